@@ -1,0 +1,256 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows. None of them compares the oracle with
+itself: the expected values come from the paper's tables, from closed forms,
+from brute force over all codewords, from numpy's independent Philox, or from
+exact invariants of the sum-product rules.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_1609_01567_gb300 import inputs as I
+
+
+# --- Tables 1-2 (Section III-B) --------------------------------------------------
+
+def test_address_iterators_match_tables_1_and_2(oracle_mod):
+    it = oracle_mod.address_iterators(I.code_14_7())
+    for number in (1, 2):
+        for name, want in I.table(number).items():
+            np.testing.assert_array_equal(it[name], want, err_msg=f"Table {number} array {name}")
+
+
+def test_code_14_7_rank_and_text_example(oracle_mod):
+    """Section II-C: v0 joins c0, c2, c3, c5 and c3 joins v0, v4, v11, v12; k = 7."""
+    code = I.code_14_7()
+    h = code.dense()
+    assert set(np.flatnonzero(h[:, 0])) == {0, 2, 3, 5}
+    assert set(np.flatnonzero(h[3])) == {0, 4, 11, 12}
+    words = oracle_mod.codewords_of(code)
+    assert words.shape == (2 ** 7, 14)
+    assert np.all(oracle_mod.syndrome_weight(code, words) == 0)
+    assert len({w.tobytes() for w in words}) == 128
+
+
+# --- syndrome and encoder (Section II-B: v is a codeword iff v H^T = 0) ----------
+
+def test_syndrome_of_unit_vectors_is_column_weight(oracle_mod):
+    code = I.small_code_n1008()
+    eye = np.eye(code.n, dtype=np.uint8)[:50]
+    colw = np.bincount(code.cols, minlength=code.n)[:50]
+    np.testing.assert_array_equal(oracle_mod.syndrome_weight(code, eye), colw)
+
+
+@pytest.mark.parametrize("which", ["n1008", "n64800"])
+def test_encoded_words_have_zero_syndrome(oracle_mod, which):
+    code = I.small_code_n1008() if which == "n1008" else I.large_code_n64800()
+    cw = I.encode_ira(code, I.random_info(6, code.k, seed=11))
+    assert np.all(oracle_mod.syndrome_weight(code, cw) == 0)
+    bad = cw.copy()
+    bad[:, 3] ^= 1
+    assert np.all(oracle_mod.syndrome_weight(code, bad) == np.bincount(code.cols, minlength=code.n)[3])
+
+
+def test_code_profiles():
+    """Workload sizes: E = 2873 at n = 1008 and E = 194399 at n = 64800."""
+    c1, c2 = I.small_code_n1008(), I.large_code_n64800()
+    assert c1.n_edges == 2873 and c2.n_edges == 194399
+    for c in (c1, c2):
+        key = c.rows.astype(np.int64) * c.n + c.cols
+        assert np.unique(key).size == key.size
+    vd = np.bincount(c2.cols, minlength=c2.n)
+    assert (vd == 8).sum() == 6480 and (vd == 3).sum() == 25920
+    cd = np.bincount(c2.rows, minlength=c2.m)
+    assert (cd == 6).sum() == 32399 and cd[0] == 5
+
+
+# --- check rule: closed forms --------------------------------------------------
+
+def test_single_parity_check_closed_form(oracle_mod):
+    """Algorithm 1 (second half) on one check equals the exact parity posterior
+    lambda_j - 2 atanh(prod_{j' != j} (-tanh(lambda_j'/2))), and brute force."""
+    rng = np.random.default_rng(3)
+    for d in (2, 3, 5, 8):
+        code = I.coo_code(1, d, [0] * d, list(range(d)))
+        lam = rng.normal(0.0, 2.5, size=(20, d))
+        out = oracle_mod.decode(code, lam, 0, early_exit=False, l_max=60.0)
+        t = -np.tanh(lam / 2.0)
+        want = np.empty_like(lam)
+        for j in range(d):
+            prod = np.prod(np.delete(t, j, axis=1), axis=1)
+            want[:, j] = lam[:, j] - 2.0 * np.arctanh(prod)
+        np.testing.assert_allclose(out["post"], want, rtol=1e-11, atol=1e-11)
+        words = oracle_mod.codewords_of(code)
+        np.testing.assert_allclose(out["post"], oracle_mod.map_llr(words, lam), rtol=1e-9, atol=1e-9)
+
+
+def test_degree_two_check_passes_clamped_message(oracle_mod):
+    """phi is an involution, so a degree-2 check forwards sign(q) * clamp(|q|,
+    phi(L_MAX), L_MAX): the saturation reading of the check rule."""
+    code = I.coo_code(1, 2, [0, 0], [0, 1])
+    lam = np.array([[0.5, 35.0], [0.5, -7.25], [-1.0, 3.0], [2.0, -50.0]])
+    out = oracle_mod.decode(code, lam, 0, early_exit=False, l_max=20.0)
+    want0 = lam[:, 0] + np.sign(lam[:, 1]) * np.minimum(np.abs(lam[:, 1]), 20.0)
+    np.testing.assert_allclose(out["post"][:, 0], want0, rtol=1e-12)
+
+
+def test_degree_one_check_and_isolated_nodes(oracle_mod):
+    """Degree-1 check: empty product, r0 = 1, so r = -L_MAX. Degree-0 variable:
+    APP = lambda; its tie APP = 0 decides 0 (Algorithm 5). Empty check: z = 0."""
+    code = I.coo_code(3, 3, [0, 1], [0, 1])  # check 2 empty, variable 2 isolated
+    lam = np.array([[1.5, -0.5, 0.0], [-3.0, 2.0, 0.25]])
+    out = oracle_mod.decode(code, lam, 0, early_exit=False, l_max=20.0)
+    np.testing.assert_allclose(out["post"], lam + np.array([-20.0, -20.0, 0.0]))
+    assert out["bits"][0, 2] == 0 and out["bits"][1, 2] == 1
+    assert np.all(out["ok"] == 1)
+
+
+# --- whole decoder on cycle-free graphs: BP is exact ---------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tree_decoder_equals_bitwise_map(oracle_mod, seed):
+    code = I.tree_code(14 + seed, seed=seed)
+    words = oracle_mod.codewords_of(code)
+    rng = np.random.default_rng(100 + seed)
+    lam = rng.normal(0.0, 2.0, size=(12, code.n))
+    out = oracle_mod.decode(code, lam, code.n, early_exit=False, l_max=60.0)
+    np.testing.assert_allclose(out["post"], oracle_mod.map_llr(words, lam), rtol=1e-9, atol=1e-9)
+
+
+def test_repetition_code_sums_llrs(oracle_mod):
+    """Checks v0 + vi = 0: every bit equals v0, so APP_j = sum of all LLRs."""
+    n = 7
+    code = I.coo_code(n - 1, n, [i - 1 for i in range(1, n)] * 2, [0] * (n - 1) + list(range(1, n)))
+    lam = np.random.default_rng(5).normal(0.3, 1.5, size=(9, n))
+    out = oracle_mod.decode(code, lam, 3, early_exit=False, l_max=60.0)
+    np.testing.assert_allclose(out["post"], np.repeat(lam.sum(axis=1, keepdims=True), n, axis=1), rtol=1e-10)
+
+
+# --- LLR rewrite vs the literal probability-domain algorithms ----------------------
+
+@pytest.mark.parametrize("which", ["14_7", "ira40"])
+def test_llr_oracle_matches_probability_domain(oracle_mod, which):
+    code = I.code_14_7() if which == "14_7" else I.ira_code(40, 20, {3: 0.6, 4: 0.4}, seed=4)
+    rng = np.random.default_rng(9)
+    sigma2 = 0.9
+    y = -1.0 + math.sqrt(sigma2) * rng.standard_normal((5, code.n))
+    lit = oracle_mod.decode_probability_domain(code, y, sigma2, 4)
+    lam = 2.0 * y / sigma2
+    r_prev = None
+    for p in range(5):
+        st = oracle_mod.sp_pass(code, lam, r_prev, l_max=60.0)
+        r_prev = st["r"]
+        r1, q1, bits, weight = lit[p]
+        np.testing.assert_allclose(st["r"], np.log(r1 / (1.0 - r1)), rtol=1e-10, atol=1e-10)
+        np.testing.assert_allclose(st["post"], np.log(q1 / (1.0 - q1)), rtol=1e-10, atol=1e-10)
+        np.testing.assert_array_equal(st["bits"], bits)
+        np.testing.assert_array_equal(st["weight"], weight)
+
+
+# --- invariants of the whole decoder ---------------------------------------------
+
+@pytest.fixture(scope="module")
+def n1008():
+    code = I.small_code_n1008()
+    cw = I.encode_ira(code, I.random_info(40, code.k, seed=21))
+    return code, cw
+
+
+def test_noiseless_codeword_decodes_in_zero_iterations(oracle_mod, n1008):
+    code, cw = n1008
+    lam = np.where(cw == 1, 40.0, -40.0)
+    out = oracle_mod.decode(code, lam, 50)
+    assert np.all(out["iters"] == 0) and np.all(out["ok"] == 1)
+    np.testing.assert_array_equal(out["bits"], cw)
+
+
+def test_all_zero_word_at_high_snr(oracle_mod, n1008):
+    code, _ = n1008
+    s2 = I.sigma2_from_ebn0(8.0, 0.5)
+    lam = oracle_mod.gen_awgn(7, 0, 40, code.n, s2)
+    out = oracle_mod.decode(code, lam, 50)
+    assert out["bits"].sum() == 0 and np.all(out["ok"] == 1)
+
+
+def test_codeword_sign_symmetry_is_exact(oracle_mod, n1008):
+    """Flipping the LLR signs on a codeword c' flips exactly those decisions
+    and negates those posteriors, with the same iteration counts."""
+    code, cw = n1008
+    s2 = I.sigma2_from_ebn0(1.5, 0.5)
+    lam = I.gaussian_llr(np.zeros_like(cw), s2, seed=3).astype(np.float64)
+    base = oracle_mod.decode(code, lam, 30)
+    flip = oracle_mod.decode(code, lam * (1.0 - 2.0 * cw), 30)
+    np.testing.assert_array_equal(flip["iters"], base["iters"])
+    np.testing.assert_array_equal(flip["ok"], base["ok"])
+    np.testing.assert_array_equal(flip["bits"], base["bits"] ^ cw)
+    np.testing.assert_array_equal(flip["post"], base["post"] * (1.0 - 2.0 * cw))
+
+
+def test_ok_iff_zero_syndrome_and_prefix_property(oracle_mod, n1008):
+    code, cw = n1008
+    s2 = I.sigma2_from_ebn0(1.25, 0.5)
+    lam = I.gaussian_llr(cw, s2, seed=8).astype(np.float64)
+    full = oracle_mod.decode(code, lam, 40)
+    np.testing.assert_array_equal(full["ok"] == 1, oracle_mod.syndrome_weight(code, full["bits"]) == 0)
+    for t in (0, 1, 3, 7):
+        part = oracle_mod.decode(code, lam, t)
+        early = full["iters"] <= t
+        np.testing.assert_array_equal(part["iters"][early & (full["ok"] == 1)], full["iters"][early & (full["ok"] == 1)])
+        assert np.all(part["iters"][~early] == t) and np.all(part["ok"][~early] == 0)
+        # fixed mode with max_iter = t runs the same passes as early exit until t
+        fixed = oracle_mod.decode(code, lam, t, early_exit=False)
+        same = ~early
+        np.testing.assert_array_equal(fixed["post"][same], part["post"][same])
+
+
+def test_bp_frame_errors_not_below_ml(oracle_mod):
+    """ML minimises the frame error rate, so FER_BP >= FER_ML (95% margin)."""
+    code = I.ira_code(18, 9, {3: 1.0}, seed=2)
+    words = oracle_mod.codewords_of(code)
+    assert words.shape[0] == 2 ** 9
+    s2 = I.sigma2_from_ebn0(1.0, 0.5)
+    rng = np.random.default_rng(17)
+    sent = words[rng.integers(0, words.shape[0], size=3000)]
+    lam = I.gaussian_llr(sent, s2, seed=18).astype(np.float64)
+    bp = oracle_mod.decode(code, lam, 50)
+    ml = oracle_mod.ml_decode(words, lam)
+    fer_bp = np.mean(np.any(bp["bits"] != sent, axis=1))
+    fer_ml = np.mean(np.any(ml != sent, axis=1))
+    margin = 1.96 * math.sqrt(fer_ml * (1 - fer_ml) / sent.shape[0] + fer_bp * (1 - fer_bp) / sent.shape[0])
+    assert fer_bp >= fer_ml - margin
+    assert fer_ml > 0.0
+
+
+# --- channel generator (BER-simulator section; Philox from Salmon et al.) -----------
+
+def test_philox_matches_numpy(oracle_mod):
+    """numpy's Philox is Philox-4x64-10; it bumps the counter before each block."""
+    for key0, key1, ctr0 in ((5, 0, 0), (2 ** 64 - 1, 12345, 77), (0x243F6A8885A308D3, 0x13198A2E03707344, 10 ** 12)):
+        bg = np.random.Philox(key=np.array([key0, key1], dtype=np.uint64),
+                              counter=np.array([ctr0, 0, 0, 0], dtype=np.uint64))
+        want = bg.random_raw(4 * 64).reshape(64, 4)
+        got = oracle_mod.philox_blocks(key0, key1, ctr0 + 1, 0, 64)
+        np.testing.assert_array_equal(got, want)
+
+
+def test_awgn_statistics(oracle_mod):
+    n, f = 4000, 40
+    s2 = I.sigma2_from_ebn0(1.0, 0.5)
+    lam = oracle_mod.gen_awgn(99, 0, f, n, s2)
+    z = (lam * s2 / 2.0 + 1.0) / math.sqrt(s2)  # back to the unit normal
+    assert abs(z.mean()) < 4.0 / math.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 0.02
+    assert stats.kstest(z.ravel(), "norm").pvalue > 1e-3
+    cw = np.ones((f, n), dtype=np.uint8)
+    lam1 = oracle_mod.gen_awgn(99, 0, f, n, s2, cw)
+    np.testing.assert_allclose(lam1 - lam, 4.0 / s2, rtol=1e-12)
+
+
+def test_awgn_frames_are_independent_of_batching(oracle_mod):
+    s2 = 0.7
+    whole = oracle_mod.gen_awgn(3, 100, 10, 37, s2)
+    part = oracle_mod.gen_awgn(3, 104, 3, 37, s2)
+    np.testing.assert_array_equal(whole[4:7], part)
