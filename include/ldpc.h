@@ -1,0 +1,219 @@
+/*
+ * ldpc.h -- C ABI of the GB300 (sm_103a) sum-product LDPC decoder.
+ *
+ * The library decodes any irregular binary LDPC code, with no bound on node
+ * degree, by the flooding sum-product (SP) algorithm of arXiv:1609.01567:
+ * a check-node update, a bit-node update, a hard decision and a parallel
+ * syndrome check per iteration, stopping a frame at its first zero syndrome
+ * or after max_iter iterations (Algorithm 2). All compute runs in the
+ * library's CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - LLRs are lambda = ln(P(bit = 1) / P(bit = 0)); a positive LLR favours
+ *     bit 1. This is the reading of Algorithms 3 and 5, which store and
+ *     decide on the probability of a one. Callers holding ln(P0/P1) negate.
+ *   - A hard decision is 1 iff the posterior LLR is > 0 (a tie gives 0, as
+ *     in Algorithm 5).
+ *   - Edges are the nonzeros of H (Section II-B, Eqs. 1-2). Edge ids are the
+ *     caller's COO entries stably sorted by column (the e array of Table 1);
+ *     the check order of edges is the edge ids stably sorted by check (the
+ *     ebar array of Table 2).
+ *   - Device pointers must be in the device memory of the code's device and
+ *     stay valid until the work enqueued on `stream` completes. `stream` is
+ *     a cudaStream_t (NULL = legacy default stream).
+ *   - Every function returns LDPC_OK (0) or a negative ldpc_status; the text
+ *     of the last error of the calling thread is ldpc_last_error(). No C++
+ *     exception crosses this ABI.
+ *   - Argument errors are reported synchronously, before anything is
+ *     enqueued. Work is asynchronous on `stream` unless a function says
+ *     otherwise.
+ */
+#ifndef LDPC_GB300_H
+#define LDPC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LDPC_OK = 0,
+    LDPC_EINVAL = -1,   /* bad argument (range, size, null pointer, wrong device) */
+    LDPC_EDUP = -2,     /* repeated (row, column) in the COO of H               */
+    LDPC_ENOMEM = -3,   /* host or device allocation failed                     */
+    LDPC_ECUDA = -4,    /* a CUDA runtime call failed                           */
+    LDPC_ETIMEOUT = -5, /* a bounded device wait ran out                        */
+    LDPC_EBUSY = -6,    /* resource in use                                      */
+    LDPC_ENODEV = -7    /* the code was created host-only (no device tables)    */
+} ldpc_status;
+
+typedef enum {
+    LDPC_MSG_F32 = 0,   /* check-to-bit messages stored as float              */
+    LDPC_MSG_F16 = 1,   /* stored as IEEE half; all node sums stay in float   */
+    LDPC_MSG_BF16 = 2   /* stored as bfloat16; all node sums stay in float    */
+} ldpc_msg_dtype;
+
+/* Opaque code handle: host tables plus their device copies. */
+typedef struct ldpc_code ldpc_code_t;
+
+typedef struct {
+    int32_t device;     /* CUDA device ordinal for the tables; -1 = host only
+                           (tables are built and can be read back with
+                           ldpc_code_tables, but decoding returns LDPC_ENODEV) */
+} ldpc_code_opts_t;
+
+typedef struct {
+    int32_t m;                   /* checks (rows of H)                       */
+    int32_t n;                   /* variables / code bits (columns of H)     */
+    int64_t n_edges;             /* E = nonzeros of H                        */
+    int32_t max_check_degree;
+    int32_t max_var_degree;
+    double mean_check_degree;    /* E / m                                    */
+    double mean_var_degree;      /* E / n                                    */
+    int32_t n_check_bins;        /* degree bins used by the check kernels    */
+    int32_t check_bin_max_degree[8]; /* upper degree bound of each bin; the
+                                        last bin of an unbounded-degree code
+                                        reports INT32_MAX                     */
+    int32_t check_bin_count[8];  /* checks in each bin                       */
+    int32_t device;              /* device of the tables, -1 for host only   */
+} ldpc_code_info_t;
+
+/*
+ * Build a code from the COO of its parity-check matrix H (m x n, nnz ones).
+ * rows/cols: host arrays of nnz int32 indices; H[rows[t]][cols[t]] = 1.
+ * The COO order defines edge ids (stable sort by column). Empty rows or
+ * columns and degree-1 nodes are accepted.
+ * Errors: LDPC_EINVAL for m, n or nnz out of range (m, n >= 0,
+ * 0 <= nnz <= 2^31 - 1) or an index outside H; LDPC_EDUP when a (row,
+ * column) pair repeats; LDPC_ENOMEM / LDPC_ECUDA on allocation or upload
+ * failure. Synchronous: the device tables are uploaded before it returns.
+ * The caller owns rows/cols; the library copies them. *out receives a handle
+ * that the caller releases with ldpc_code_destroy.
+ */
+int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t *rows, const int32_t *cols,
+                     const ldpc_code_opts_t *opts, ldpc_code_t **out);
+
+/* Release a code, its device tables and its decode workspace. Waits for
+ * the code's pending work. NULL is ignored. */
+void ldpc_code_destroy(ldpc_code_t *code);
+
+/* Sizes and degree statistics of a code. */
+int ldpc_code_info(const ldpc_code_t *code, ldpc_code_info_t *info);
+
+/*
+ * Read back the paper's address-iterator arrays (Section III-B, Tables 1-2),
+ * each of n_edges int32 entries into caller-owned host buffers; any pointer
+ * may be NULL to skip that array.
+ *   variable-sorted (edge e):  v[e] variable, c[e] check, t[e] degree of v[e],
+ *                              s[e] first edge of v[e], u[e] = e - s[e]
+ *   check-sorted (slot k):     ebar[k] edge id, vbar[k], cbar[k] its variable
+ *                              and check, tbar[k] degree of cbar[k],
+ *                              sbar[k] first slot of cbar[k], ubar[k] = k - sbar[k]
+ * Host-only; works for host-only codes.
+ */
+int ldpc_code_tables(const ldpc_code_t *code, int32_t *v, int32_t *c, int32_t *t, int32_t *s, int32_t *u,
+                     int32_t *ebar, int32_t *vbar, int32_t *cbar, int32_t *tbar, int32_t *sbar, int32_t *ubar);
+
+typedef struct {
+    int32_t early_exit; /* nonzero: a frame stops at its first zero syndrome
+                           (Algorithm 2); zero: every frame runs all max_iter
+                           iterations and reports the final syndrome        */
+    float l_max;        /* saturation L_MAX of the check rule, > 0; values
+                           <= 0 select the default 20. Check inputs and outputs
+                           are clamped to [phi(L_MAX), L_MAX] in magnitude    */
+    int32_t msg_dtype;  /* ldpc_msg_dtype of the stored check-to-bit messages */
+    int32_t profile;    /* nonzero: time every kernel launch with CUDA events
+                           on `stream` (read with ldpc_prof_read)             */
+    float *r_out;       /* optional device [n_frames][n_edges] float: the last
+                           check-to-bit messages in edge order (for checking
+                           one iteration at a time); NULL to skip            */
+} ldpc_decode_opts_t;
+
+/*
+ * Decode n_frames frames.
+ *   llr       device [n_frames][n] float channel LLRs (read only)
+ *   max_iter  >= 0 iterations after the first check pass (Algorithm 2), so at
+ *             most max_iter + 1 check passes run
+ *   opts      NULL selects {early_exit = 1, l_max = 20, F32, no profiling}
+ *   bits      device [n_frames][n] uint8 hard decisions (0/1)
+ *   iters     device [n_frames] int32: 0 when the first pass already gives a
+ *             codeword, else the iteration at which the frame stopped, or
+ *             max_iter (always max_iter without early exit)
+ *   syndrome_ok device [n_frames] uint8: 1 iff H * bits = 0
+ *   post_llr  optional device [n_frames][n] float posterior LLRs; NULL to skip
+ * The code's decode workspace (device scratch sized for the largest batch
+ * seen so far) is allocated on first use and reused; calls that share a code
+ * are serialised on the device through an event, whatever their streams.
+ * Errors: LDPC_EINVAL (bad sizes, NULL required pointer), LDPC_ENODEV,
+ * LDPC_ENOMEM, LDPC_ECUDA.
+ */
+int ldpc_decode(ldpc_code_t *code, const float *llr, int32_t n_frames, int32_t max_iter,
+                const ldpc_decode_opts_t *opts, uint8_t *bits, int32_t *iters, uint8_t *syndrome_ok,
+                float *post_llr, void *stream);
+
+/*
+ * ldpc_decode on HOST buffers (same shapes, host memory; pinned memory makes
+ * the copies asynchronous). Copies llr to the device, decodes, copies bits,
+ * iters, syndrome_ok (and post_llr when non-NULL) back, and synchronizes
+ * `stream` before returning. opts->r_out must be NULL.
+ */
+int ldpc_decode_host(ldpc_code_t *code, const float *llr_host, int32_t n_frames, int32_t max_iter,
+                     const ldpc_decode_opts_t *opts, uint8_t *bits_host, int32_t *iters_host,
+                     uint8_t *syndrome_ok_host, float *post_llr_host, void *stream);
+
+/*
+ * Channel LLRs of BPSK over AWGN (the BER simulator of Section IV, Eqs. 3-4)
+ * into device llr [n_frames][n] float.
+ * Frame f has global index frame_offset + f. Bit j of a frame uses Philox-4x64
+ * with 10 rounds (Salmon et al., SC'11), key (seed, 0) and counter
+ * (j / 4, frame_offset + f, 0, 0): words (w0, w1) drive bits 4q and 4q+1,
+ * (w2, w3) bits 4q+2 and 4q+3, through Box-Muller on 24-bit uniforms
+ * ua = ((w >> 40) + 1) 2^-24 in (0, 1], ub = (w >> 40) 2^-24 in [0, 1):
+ * z0 = sqrt(-2 ln ua) cos(2 pi ub), z1 = sqrt(-2 ln ua) sin(2 pi ub).
+ * Then x = 2c - 1, y = x + sigma z, llr = 2 y / sigma^2 (float arithmetic).
+ * codewords: device [n_frames][n] uint8, or NULL for the all-zero word.
+ * Errors: LDPC_EINVAL for negative sizes or sigma2 <= 0.
+ */
+int ldpc_gen_awgn(uint64_t seed, int64_t frame_offset, int32_t n_frames, int32_t n, float sigma2,
+                  const uint8_t *codewords, float *llr, void *stream);
+
+/* Raw Philox-4x64-10 blocks: out[i][0..3] = Philox(key (key0, key1),
+ * counter (ctr0 + i, ctr1, 0, 0)) for 0 <= i < count; out is device
+ * [count][4] uint64. */
+int ldpc_philox4x64_10(uint64_t key0, uint64_t key1, uint64_t ctr0, uint64_t ctr1, int64_t count,
+                       uint64_t *out, void *stream);
+
+/* Kernel classes reported by ldpc_prof_read. */
+enum {
+    LDPC_K_INTERLEAVE = 0, /* frame-major LLRs -> frame-interleaved layout      */
+    LDPC_K_CHECK = 1,      /* check-node update (plus syndrome of the last APP) */
+    LDPC_K_BIT = 2,        /* bit-node update: posterior LLR per variable       */
+    LDPC_K_SYNDROME = 3,   /* final syndrome pass                               */
+    LDPC_K_FINALIZE = 4,   /* hard decisions, posteriors, iteration counts      */
+    LDPC_K_OTHER = 5,      /* flag set-up, message export                       */
+    LDPC_K_COUNT = 6
+};
+
+typedef struct {
+    int64_t launches[LDPC_K_COUNT];
+    double total_ms[LDPC_K_COUNT]; /* sum of CUDA-event durations */
+} ldpc_prof_t;
+
+/* Collect the timings of profiled launches of `code` made since the last
+ * reset (synchronizes on their events), adding them into *out; reset != 0
+ * clears the record afterwards. */
+int ldpc_prof_read(ldpc_code_t *code, ldpc_prof_t *out, int32_t reset);
+
+/* Text of the calling thread's last error ("" if none). */
+const char *ldpc_last_error(void);
+
+/* Library version string. */
+const char *ldpc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPC_GB300_H */

@@ -1,0 +1,251 @@
+// Code tables: COO of H -> edge ids, CSC by variable, CSR by check, the edge
+// permutation between the two orders, and check degree bins (host side), plus
+// their upload to the device. Also the error-text plumbing of the C ABI.
+//
+// The edge numbering follows Section III-B: edge ids e are the COO entries
+// stably sorted by variable (Table 1: e, v, c with segment start s, degree t
+// and rank u); the check order is e stably sorted by check (Table 2: ebar,
+// vbar, cbar, sbar, tbar, ubar).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ldpc_internal.h"
+
+namespace ldpc {
+
+static thread_local std::string g_last_error;
+
+int set_error(int status, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+    return set_error(e == cudaErrorMemoryAllocation ? LDPC_ENOMEM : LDPC_ECUDA, "%s: %s (%s)", what,
+                     cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+}  // namespace ldpc
+
+using namespace ldpc;
+
+static void free_device_tables(ldpc_code *c) {
+    if (c->device < 0) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    cudaFree(c->d.row_ptr);
+    cudaFree(c->d.col_idx);
+    cudaFree(c->d.col_ptr);
+    cudaFree(c->d.edge_slot);
+    cudaFree(c->d.bin_checks);
+    Workspace &w = c->ws;
+    if (w.last_use) cudaEventSynchronize(w.last_use);
+    cudaFree(w.lamT);
+    cudaFree(w.app);
+    cudaFree(w.r);
+    cudaFree(w.done);
+    cudaFree(w.unsat);
+    cudaFree(w.stop_iter);
+    cudaFree(w.h_llr);
+    cudaFree(w.h_bits);
+    cudaFree(w.h_iters);
+    cudaFree(w.h_ok);
+    cudaFree(w.h_post);
+    if (w.last_use) cudaEventDestroy(w.last_use);
+    for (auto &p : c->prof) {
+        cudaEventDestroy(p.start);
+        cudaEventDestroy(p.stop);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    c->d = DeviceTables{};
+    c->ws = Workspace{};
+    if (prev >= 0) cudaSetDevice(prev);
+}
+
+template <typename T>
+static cudaError_t upload(T **dst, const std::vector<T> &src) {
+    size_t bytes = sizeof(T) * (src.empty() ? 1 : src.size());
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) return e;
+    if (!src.empty()) e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+extern "C" int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t *rows, const int32_t *cols,
+                                const ldpc_code_opts_t *opts, ldpc_code_t **out) {
+    if (!out) return set_error(LDPC_EINVAL, "ldpc_code_create: out is NULL");
+    *out = nullptr;
+    if (m < 0 || n < 0) return set_error(LDPC_EINVAL, "ldpc_code_create: negative size m=%d n=%d", m, n);
+    if (nnz < 0 || nnz > INT32_MAX)
+        return set_error(LDPC_EINVAL, "ldpc_code_create: nnz=%lld outside [0, 2^31-1]", (long long)nnz);
+    if (nnz > 0 && (!rows || !cols)) return set_error(LDPC_EINVAL, "ldpc_code_create: rows/cols is NULL");
+    int device = opts ? opts->device : 0;
+
+    ldpc_code *c = new (std::nothrow) ldpc_code();
+    if (!c) return set_error(LDPC_ENOMEM, "ldpc_code_create: out of host memory");
+    try {
+        c->m = m;
+        c->n = n;
+        c->E = nnz;
+        const int64_t E = nnz;
+        for (int64_t t = 0; t < E; ++t) {
+            if (rows[t] < 0 || rows[t] >= m || cols[t] < 0 || cols[t] >= n) {
+                delete c;
+                return set_error(LDPC_EINVAL, "ldpc_code_create: entry %lld = (%d, %d) outside H (%d x %d)",
+                                 (long long)t, rows[t], cols[t], m, n);
+            }
+        }
+        // CSC by variable; edge ids = stable sort of the COO by column.
+        c->col_ptr.assign((size_t)n + 1, 0);
+        for (int64_t t = 0; t < E; ++t) c->col_ptr[cols[t] + 1]++;
+        for (int32_t j = 0; j < n; ++j) c->col_ptr[j + 1] += c->col_ptr[j];
+        c->var_of_edge.resize(E);
+        c->chk_of_edge.resize(E);
+        {
+            std::vector<int32_t> fill(c->col_ptr.begin(), c->col_ptr.end() - 1);
+            for (int64_t t = 0; t < E; ++t) {
+                int32_t e = fill[cols[t]]++;
+                c->var_of_edge[e] = cols[t];
+                c->chk_of_edge[e] = rows[t];
+            }
+        }
+        // repeated (row, column): within one column, every check at most once
+        {
+            std::vector<int32_t> seen((size_t)m, -1);
+            for (int32_t j = 0; j < n; ++j) {
+                for (int32_t e = c->col_ptr[j]; e < c->col_ptr[j + 1]; ++e) {
+                    int32_t i = c->chk_of_edge[e];
+                    if (seen[i] == j) {
+                        delete c;
+                        return set_error(LDPC_EDUP, "ldpc_code_create: H[%d][%d] appears more than once", i, j);
+                    }
+                    seen[i] = j;
+                }
+            }
+        }
+        // CSR by check; check order = stable sort of edge ids by check.
+        c->row_ptr.assign((size_t)m + 1, 0);
+        for (int64_t e = 0; e < E; ++e) c->row_ptr[c->chk_of_edge[e] + 1]++;
+        for (int32_t i = 0; i < m; ++i) c->row_ptr[i + 1] += c->row_ptr[i];
+        c->edge_of_slot.resize(E);
+        c->col_idx.resize(E);
+        c->edge_slot.resize(E);
+        {
+            std::vector<int32_t> fill(c->row_ptr.begin(), c->row_ptr.end() - 1);
+            for (int64_t e = 0; e < E; ++e) {
+                int32_t k = fill[c->chk_of_edge[e]]++;
+                c->edge_of_slot[k] = (int32_t)e;
+                c->col_idx[k] = c->var_of_edge[e];
+                c->edge_slot[e] = k;
+            }
+        }
+        for (int32_t i = 0; i < m; ++i) c->max_cdeg = std::max(c->max_cdeg, c->row_ptr[i + 1] - c->row_ptr[i]);
+        for (int32_t j = 0; j < n; ++j) c->max_vdeg = std::max(c->max_vdeg, c->col_ptr[j + 1] - c->col_ptr[j]);
+        // check degree bins (degree-0 checks carry no message and are skipped)
+        for (int b = 0; b < kNumCheckBins; ++b) {
+            c->bin_off[b] = (int32_t)c->bin_checks.size();
+            int lo = b == 0 ? 1 : kBinMaxDegree[b - 1] + 1;
+            int hi = kBinMaxDegree[b];
+            for (int32_t i = 0; i < m; ++i) {
+                int d = c->row_ptr[i + 1] - c->row_ptr[i];
+                if (d >= lo && d <= hi) c->bin_checks.push_back(i);
+            }
+        }
+        c->bin_off[kNumCheckBins] = (int32_t)c->bin_checks.size();
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return set_error(LDPC_ENOMEM, "ldpc_code_create: out of host memory");
+    }
+
+    if (device >= 0) {
+        int count = 0;
+        cudaError_t e = cudaGetDeviceCount(&count);
+        if (e != cudaSuccess || device >= count) {
+            delete c;
+            if (e != cudaSuccess) return cuda_error(e, "ldpc_code_create: cudaGetDeviceCount");
+            return set_error(LDPC_EINVAL, "ldpc_code_create: device %d not present (%d devices)", device, count);
+        }
+        int prev = -1;
+        cudaGetDevice(&prev);
+        cudaSetDevice(device);
+        c->device = device;
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+        if ((e = upload(&c->d.row_ptr, c->row_ptr)) != cudaSuccess ||
+            (e = upload(&c->d.col_idx, c->col_idx)) != cudaSuccess ||
+            (e = upload(&c->d.col_ptr, c->col_ptr)) != cudaSuccess ||
+            (e = upload(&c->d.edge_slot, c->edge_slot)) != cudaSuccess ||
+            (e = upload(&c->d.bin_checks, c->bin_checks)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&c->ws.last_use, cudaEventDisableTiming)) != cudaSuccess) {
+            int st = cuda_error(e, "ldpc_code_create: device upload");
+            free_device_tables(c);
+            delete c;
+            if (prev >= 0) cudaSetDevice(prev);
+            return st;
+        }
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    *out = c;
+    return LDPC_OK;
+}
+
+extern "C" void ldpc_code_destroy(ldpc_code_t *code) {
+    if (!code) return;
+    free_device_tables(code);
+    delete code;
+}
+
+extern "C" int ldpc_code_info(const ldpc_code_t *c, ldpc_code_info_t *info) {
+    if (!c || !info) return set_error(LDPC_EINVAL, "ldpc_code_info: NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->m = c->m;
+    info->n = c->n;
+    info->n_edges = c->E;
+    info->max_check_degree = c->max_cdeg;
+    info->max_var_degree = c->max_vdeg;
+    info->mean_check_degree = c->m ? (double)c->E / c->m : 0.0;
+    info->mean_var_degree = c->n ? (double)c->E / c->n : 0.0;
+    info->n_check_bins = kNumCheckBins;
+    for (int b = 0; b < kNumCheckBins; ++b) {
+        info->check_bin_max_degree[b] = kBinMaxDegree[b];
+        info->check_bin_count[b] = c->bin_off[b + 1] - c->bin_off[b];
+    }
+    info->device = c->device;
+    return LDPC_OK;
+}
+
+extern "C" int ldpc_code_tables(const ldpc_code_t *c, int32_t *v, int32_t *cc, int32_t *t, int32_t *s, int32_t *u,
+                                int32_t *ebar, int32_t *vbar, int32_t *cbar, int32_t *tbar, int32_t *sbar,
+                                int32_t *ubar) {
+    if (!c) return set_error(LDPC_EINVAL, "ldpc_code_tables: code is NULL");
+    for (int64_t e = 0; e < c->E; ++e) {
+        int32_t j = c->var_of_edge[e];
+        if (v) v[e] = j;
+        if (cc) cc[e] = c->chk_of_edge[e];
+        if (t) t[e] = c->col_ptr[j + 1] - c->col_ptr[j];
+        if (s) s[e] = c->col_ptr[j];
+        if (u) u[e] = (int32_t)e - c->col_ptr[j];
+    }
+    for (int32_t i = 0; i < c->m; ++i) {
+        for (int32_t k = c->row_ptr[i]; k < c->row_ptr[i + 1]; ++k) {
+            if (ebar) ebar[k] = c->edge_of_slot[k];
+            if (vbar) vbar[k] = c->col_idx[k];
+            if (cbar) cbar[k] = i;
+            if (tbar) tbar[k] = c->row_ptr[i + 1] - c->row_ptr[i];
+            if (sbar) sbar[k] = c->row_ptr[i];
+            if (ubar) ubar[k] = k - c->row_ptr[i];
+        }
+    }
+    return LDPC_OK;
+}
+
+extern "C" const char *ldpc_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char *ldpc_version(void) { return "ldpc-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,449 @@
+// Decode driver (Algorithm 2) and the layout/flag kernels around the passes.
+//
+// One decode call of F frames runs, per chunk of frames:
+//   init flags -> interleave LLRs -> pass 0 (check on q = lambda, bit) ->
+//   passes 1..max_iter (check, fused syndrome of the previous decision,
+//   bit with the early-exit test) -> final syndrome -> results.
+// Every step is a kernel of this library on the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ldpc_internal.h"
+#include "ldpc_pass_kernels.cuh"
+
+namespace ldpc {
+
+constexpr int32_t kMaxChunkFrames = 8192;
+
+// llr [F][n] (frame-major) -> lamT [n][Fp] (frame-interleaved); padding
+// frames get lambda = 0.
+__global__ void k_interleave(const float *__restrict__ llr, float *__restrict__ lamT, int32_t n, int32_t F,
+                             int32_t Fp) {
+    __shared__ float tile[32][33];
+    const int64_t j0 = (int64_t)blockIdx.x * 32;
+    const int f0 = blockIdx.y * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        int f = f0 + yy;
+        int64_t j = j0 + threadIdx.x;
+        tile[yy][threadIdx.x] = (f < F && j < n) ? llr[(size_t)f * n + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        int64_t j = j0 + yy;
+        int f = f0 + threadIdx.x;
+        if (j < n) lamT[(size_t)j * Fp + f] = tile[threadIdx.x][yy];
+    }
+}
+
+// done bits: padding frames (f >= F) start as stopped.
+__global__ void k_init_done(uint32_t *done, int32_t F, int32_t Fp) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= Fp / 32) return;
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; ++b)
+        if (w * 32 + b >= F) bits |= 1u << b;
+    done[w] = bits;
+}
+
+// Syndrome of the hard decision of the current APP into flag row `row`
+// (Algorithm 6), one warp per check for 32 * V frames.
+template <int V>
+__global__ void __launch_bounds__(kThreads) k_syndrome(PassArgs a, uint32_t *row) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int g = blockIdx.y;
+    const int f0 = g * 32 * V + lane * V;
+    const size_t Fp = (size_t)a.Fp;
+    bool unsat[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) unsat[v] = false;
+    for (int i = blockIdx.x * (kThreads / 32) + warp; i < a.m; i += gridDim.x * (kThreads / 32)) {
+        const int b = a.row_ptr[i];
+        const int d = a.row_ptr[i + 1] - b;
+        uint32_t z[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) z[v] = 0u;
+        for (int k = 0; k < d; ++k) {
+            const int j = a.col_idx[b + k];
+            float av[V];
+            load_v<V, float>(a.app + (size_t)j * Fp + f0, av);
+#pragma unroll
+            for (int v = 0; v < V; ++v) z[v] ^= av[v] > 0.0f ? 1u : 0u;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) unsat[v] |= z[v] != 0u;
+    }
+    or_frame_bits<V>(row, g, lane, unsat);
+}
+
+// APP [n][Fp] -> bits [F][n] (1 iff APP > 0) and optional post [F][n].
+__global__ void k_finalize(const float *__restrict__ app, uint8_t *__restrict__ bits, float *__restrict__ post,
+                           int32_t n, int32_t F, int32_t Fp) {
+    __shared__ float tile[32][33];
+    const int64_t j0 = (int64_t)blockIdx.x * 32;
+    const int f0 = blockIdx.y * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        int64_t j = j0 + yy;
+        int f = f0 + threadIdx.x;
+        tile[yy][threadIdx.x] = j < n ? app[(size_t)j * Fp + f] : 0.0f;
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        int f = f0 + yy;
+        int64_t j = j0 + threadIdx.x;
+        if (f < F && j < n) {
+            float x = tile[threadIdx.x][yy];
+            bits[(size_t)f * n + j] = x > 0.0f ? 1 : 0;
+            if (post) post[(size_t)f * n + j] = x;
+        }
+    }
+}
+
+// Per-frame iteration count and syndrome status.
+__global__ void k_frame_results(const uint32_t *done, const int32_t *stop_iter, const uint32_t *final_unsat,
+                                int32_t F, int32_t max_iter, int32_t *iters, uint8_t *ok) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    bool stopped = frame_bit(done, f);
+    iters[f] = stopped ? stop_iter[f] : max_iter;
+    ok[f] = stopped ? 1 : (frame_bit(final_unsat, f) ? 0 : 1);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static int msg_size(int dtype) { return dtype == LDPC_MSG_F32 ? 4 : 2; }
+
+static void frames_layout(int32_t F, int32_t *V, int32_t *Fp) {
+    if (F > 64) {
+        *V = 4;
+        *Fp = (F + 127) / 128 * 128;
+    } else {
+        *V = 1;
+        *Fp = (F + 31) / 32 * 32;
+    }
+}
+
+template <typename T>
+static cudaError_t grow(T **p, size_t count) {
+    cudaFree(*p);
+    *p = nullptr;
+    return cudaMalloc(p, sizeof(T) * std::max<size_t>(count, 1));
+}
+
+// Device buffers for Fp frames and max_iter iterations (grown, never shrunk).
+static int ensure_workspace(ldpc_code *c, int32_t Fp, int32_t max_iter, int msg_bytes) {
+    Workspace &w = c->ws;
+    bool need_frames = Fp > w.fp_cap || msg_bytes > w.msg_bytes;
+    bool need_iters = need_frames || max_iter > w.iter_cap;
+    if (!need_frames && !need_iters) return LDPC_OK;
+    cudaError_t e = cudaEventSynchronize(w.last_use);
+    if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: waiting for the previous decode");
+    if (need_frames) {
+        int32_t cap = std::max(Fp, w.fp_cap);
+        int mb = std::max(msg_bytes, w.msg_bytes);
+        if ((e = grow(&w.lamT, (size_t)c->n * cap)) != cudaSuccess ||
+            (e = grow(&w.app, (size_t)c->n * cap)) != cudaSuccess ||
+            (e = grow(reinterpret_cast<char **>(&w.r), (size_t)c->E * cap * mb)) != cudaSuccess ||
+            (e = grow(&w.done, (size_t)cap / 32)) != cudaSuccess ||
+            (e = grow(&w.stop_iter, (size_t)cap)) != cudaSuccess) {
+            w.fp_cap = 0;
+            w.iter_cap = -1;
+            return cuda_error(e, "ldpc_decode: workspace allocation");
+        }
+        // padding frames read finite posteriors
+        if ((e = cudaMemset(w.app, 0, sizeof(float) * std::max<size_t>((size_t)c->n * cap, 1))) != cudaSuccess)
+            return cuda_error(e, "ldpc_decode: workspace init");
+        w.fp_cap = cap;
+        w.msg_bytes = mb;
+    }
+    int32_t icap = std::max(max_iter, w.iter_cap);
+    if ((e = grow(&w.unsat, (size_t)(icap + 1) * (w.fp_cap / 32))) != cudaSuccess) {
+        w.iter_cap = -1;
+        return cuda_error(e, "ldpc_decode: workspace allocation");
+    }
+    w.iter_cap = icap;
+    return LDPC_OK;
+}
+
+static cudaEvent_t take_event(ldpc_code *c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch wrapper: optional CUDA-event timing of each launch on the stream.
+struct Launcher {
+    ldpc_code *c;
+    cudaStream_t s;
+    bool profile;
+    template <typename F>
+    cudaError_t operator()(int kind, F &&fn) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (profile) {
+            a = take_event(c);
+            b = take_event(c);
+            cudaEventRecord(a, s);
+        }
+        cudaError_t e = fn();
+        if (profile) {
+            cudaEventRecord(b, s);
+            c->prof.push_back(ProfRecord{kind, a, b});
+        }
+        return e;
+    }
+};
+
+template <typename M>
+static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t max_iter, const ldpc_decode_opts_t &o,
+                             float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok, float *post, float *r_out,
+                             cudaStream_t s) {
+    Workspace &w = c->ws;
+    int32_t V, Fp;
+    frames_layout(F, &V, &Fp);
+    PassArgs a{};
+    a.row_ptr = c->d.row_ptr;
+    a.col_idx = c->d.col_idx;
+    a.col_ptr = c->d.col_ptr;
+    a.edge_slot = c->d.edge_slot;
+    a.lamT = w.lamT;
+    a.app = w.app;
+    a.r = w.r;
+    a.m = c->m;
+    a.n = c->n;
+    a.E = c->E;
+    a.Fp = Fp;
+    a.V = V;
+    a.n_frames = F;
+    a.early_exit = o.early_exit ? 1 : 0;
+    a.l_max = l_max;
+    a.phi_lmax = (float)std::log1p(2.0 / std::expm1((double)l_max));
+    a.done = w.done;
+    a.unsat = w.unsat;
+    a.stop_iter = w.stop_iter;
+    a.grid_ctas = std::max(1, c->sm_count) * 4;
+
+    Launcher L{c, s, o.profile != 0};
+    cudaError_t e;
+    const int words = Fp / 32;
+    e = L(LDPC_K_OTHER, [&] {
+        cudaError_t ee = cudaMemsetAsync(w.unsat, 0, sizeof(uint32_t) * (size_t)(max_iter + 1) * words, s);
+        if (ee != cudaSuccess) return ee;
+        k_init_done<<<(words + 127) / 128, 128, 0, s>>>(w.done, F, Fp);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    if (c->n > 0) {
+        e = L(LDPC_K_INTERLEAVE, [&] {
+            dim3 grid((unsigned)((c->n + 31) / 32), (unsigned)(Fp / 32), 1);
+            k_interleave<<<grid, dim3(32, 8, 1), 0, s>>>(llr, w.lamT, c->n, F, Fp);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+    }
+    for (int32_t t = 0; t <= max_iter; ++t) {
+        a.pass = t;
+        a.syndrome = (t > 0 && a.early_exit) ? 1 : 0;
+        for (int b = 0; b < kNumCheckBins; ++b) {
+            int32_t count = c->bin_off[b + 1] - c->bin_off[b];
+            if (count == 0) continue;
+            e = L(LDPC_K_CHECK, [&] { return launch_check_bin<M>(a, b, c->d.bin_checks + c->bin_off[b], count, s); });
+            if (e != cudaSuccess) return e;
+        }
+        if (c->n > 0) {
+            e = L(LDPC_K_BIT, [&] { return launch_bit<M>(a, s); });
+            if (e != cudaSuccess) return e;
+        }
+    }
+    uint32_t *final_row = w.unsat + (size_t)max_iter * words;
+    if (c->m > 0 && c->E > 0) {
+        e = L(LDPC_K_SYNDROME, [&] {
+            dim3 grid = pass_grid(a, c->m);
+            if (V == 4)
+                k_syndrome<4><<<grid, kThreads, 0, s>>>(a, final_row);
+            else
+                k_syndrome<1><<<grid, kThreads, 0, s>>>(a, final_row);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+    }
+    e = L(LDPC_K_FINALIZE, [&] {
+        if (c->n > 0) {
+            dim3 grid((unsigned)((c->n + 31) / 32), (unsigned)((F + 31) / 32), 1);
+            k_finalize<<<grid, dim3(32, 8, 1), 0, s>>>(w.app, bits, post, c->n, F, Fp);
+        }
+        k_frame_results<<<(F + 255) / 256, 256, 0, s>>>(w.done, w.stop_iter, final_row, F, max_iter, iters, ok);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    if (r_out) {
+        e = L(LDPC_K_OTHER, [&] { return launch_export_r<M>(a, r_out, s); });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static int check_decode_args(const ldpc_code *c, int32_t F, int32_t max_iter, const ldpc_decode_opts_t &o,
+                             float *l_max_out, const char *fn) {
+    if (!c) return set_error(LDPC_EINVAL, "%s: code is NULL", fn);
+    if (c->device < 0) return set_error(LDPC_ENODEV, "%s: the code was created without device tables", fn);
+    if (F < 0) return set_error(LDPC_EINVAL, "%s: n_frames=%d < 0", fn, F);
+    if (max_iter < 0 || max_iter > 100000) return set_error(LDPC_EINVAL, "%s: max_iter=%d outside [0, 100000]", fn, max_iter);
+    float l_max = o.l_max > 0.0f ? o.l_max : 20.0f;
+    if (!(l_max <= 80.0f)) return set_error(LDPC_EINVAL, "%s: l_max=%g outside (0, 80]", fn, (double)o.l_max);
+    if (o.msg_dtype != LDPC_MSG_F32 && o.msg_dtype != LDPC_MSG_F16 && o.msg_dtype != LDPC_MSG_BF16)
+        return set_error(LDPC_EINVAL, "%s: unknown msg_dtype %d", fn, o.msg_dtype);
+    *l_max_out = l_max;
+    return LDPC_OK;
+}
+
+static ldpc_decode_opts_t default_opts() {
+    ldpc_decode_opts_t o;
+    memset(&o, 0, sizeof(o));
+    o.early_exit = 1;
+    o.l_max = 20.0f;
+    o.msg_dtype = LDPC_MSG_F32;
+    return o;
+}
+
+// Decode with the code's lock held.
+static int decode_locked(ldpc_code *c, const float *llr, int32_t F, int32_t max_iter, const ldpc_decode_opts_t &o,
+                         float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok, float *post, cudaStream_t s) {
+    int32_t chunk = std::min(F, kMaxChunkFrames);
+    int32_t V, Fp;
+    frames_layout(chunk, &V, &Fp);
+    int st = ensure_workspace(c, Fp, max_iter, msg_size(o.msg_dtype));
+    if (st != LDPC_OK) return st;
+    cudaError_t e = cudaStreamWaitEvent(s, c->ws.last_use, 0);
+    if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: cudaStreamWaitEvent");
+    for (int32_t f0 = 0; f0 < F; f0 += chunk) {
+        int32_t fc = std::min(chunk, F - f0);
+        const float *l = llr + (size_t)f0 * c->n;
+        uint8_t *bb = bits + (size_t)f0 * c->n;
+        float *pp = post ? post + (size_t)f0 * c->n : nullptr;
+        float *rr = o.r_out ? o.r_out + (size_t)f0 * c->E : nullptr;
+        switch (o.msg_dtype) {
+        case LDPC_MSG_F16:
+            e = run_chunk<__half>(c, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
+            break;
+        case LDPC_MSG_BF16:
+            e = run_chunk<__nv_bfloat16>(c, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
+            break;
+        default:
+            e = run_chunk<float>(c, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
+            break;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: kernel launch");
+    }
+    e = cudaEventRecord(c->ws.last_use, s);
+    if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: cudaEventRecord");
+    return LDPC_OK;
+}
+
+}  // namespace ldpc
+
+using namespace ldpc;
+
+extern "C" int ldpc_decode(ldpc_code_t *c, const float *llr, int32_t F, int32_t max_iter,
+                           const ldpc_decode_opts_t *opts, uint8_t *bits, int32_t *iters, uint8_t *ok, float *post,
+                           void *stream) {
+    ldpc_decode_opts_t o = opts ? *opts : default_opts();
+    float l_max;
+    int st = check_decode_args(c, F, max_iter, o, &l_max, "ldpc_decode");
+    if (st != LDPC_OK) return st;
+    if (F == 0) return LDPC_OK;
+    if ((c->n > 0 && (!llr || !bits)) || !iters || !ok)
+        return set_error(LDPC_EINVAL, "ldpc_decode: NULL llr, bits, iters or syndrome_ok");
+    std::lock_guard<std::mutex> lock(c->mu);
+    DeviceGuard guard(c->device);
+    return decode_locked(c, llr, F, max_iter, o, l_max, bits, iters, ok, post, (cudaStream_t)stream);
+}
+
+extern "C" int ldpc_decode_host(ldpc_code_t *c, const float *llr_host, int32_t F, int32_t max_iter,
+                                const ldpc_decode_opts_t *opts, uint8_t *bits_host, int32_t *iters_host,
+                                uint8_t *ok_host, float *post_host, void *stream) {
+    ldpc_decode_opts_t o = opts ? *opts : default_opts();
+    float l_max;
+    int st = check_decode_args(c, F, max_iter, o, &l_max, "ldpc_decode_host");
+    if (st != LDPC_OK) return st;
+    if (o.r_out) return set_error(LDPC_EINVAL, "ldpc_decode_host: r_out must be NULL");
+    if (F == 0) return LDPC_OK;
+    if ((c->n > 0 && (!llr_host || !bits_host)) || !iters_host || !ok_host)
+        return set_error(LDPC_EINVAL, "ldpc_decode_host: NULL llr, bits, iters or syndrome_ok");
+    std::lock_guard<std::mutex> lock(c->mu);
+    DeviceGuard guard(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace &w = c->ws;
+    cudaError_t e;
+    if (F > w.host_cap) {
+        if ((e = cudaEventSynchronize(w.last_use)) != cudaSuccess) return cuda_error(e, "ldpc_decode_host: wait");
+        if ((e = grow(&w.h_llr, (size_t)F * c->n)) != cudaSuccess || (e = grow(&w.h_bits, (size_t)F * c->n)) != cudaSuccess ||
+            (e = grow(&w.h_iters, (size_t)F)) != cudaSuccess || (e = grow(&w.h_ok, (size_t)F)) != cudaSuccess ||
+            (e = grow(&w.h_post, (size_t)F * c->n)) != cudaSuccess) {
+            w.host_cap = 0;
+            return cuda_error(e, "ldpc_decode_host: staging allocation");
+        }
+        w.host_cap = F;
+    }
+    if ((e = cudaStreamWaitEvent(s, w.last_use, 0)) != cudaSuccess) return cuda_error(e, "ldpc_decode_host: wait");
+    size_t nf = (size_t)F * c->n;
+    if (nf && (e = cudaMemcpyAsync(w.h_llr, llr_host, sizeof(float) * nf, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_error(e, "ldpc_decode_host: copy in");
+    st = decode_locked(c, w.h_llr, F, max_iter, o, l_max, w.h_bits, w.h_iters, w.h_ok, post_host ? w.h_post : nullptr, s);
+    if (st != LDPC_OK) return st;
+    if ((nf && (e = cudaMemcpyAsync(bits_host, w.h_bits, nf, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(iters_host, w.h_iters, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(ok_host, w.h_ok, F, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (post_host && nf &&
+         (e = cudaMemcpyAsync(post_host, w.h_post, sizeof(float) * nf, cudaMemcpyDeviceToHost, s)) != cudaSuccess))
+        return cuda_error(e, "ldpc_decode_host: copy out");
+    if ((e = cudaEventRecord(w.last_use, s)) != cudaSuccess) return cuda_error(e, "ldpc_decode_host: record");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_error(e, "ldpc_decode_host: synchronize");
+    return LDPC_OK;
+}
+
+extern "C" int ldpc_prof_read(ldpc_code_t *c, ldpc_prof_t *out, int32_t reset) {
+    if (!c || !out) return set_error(LDPC_EINVAL, "ldpc_prof_read: NULL argument");
+    std::lock_guard<std::mutex> lock(c->mu);
+    if (c->device < 0) return LDPC_OK;
+    DeviceGuard guard(c->device);
+    for (auto &p : c->prof) {
+        cudaError_t e = cudaEventSynchronize(p.stop);
+        if (e != cudaSuccess) return cuda_error(e, "ldpc_prof_read: event");
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, p.start, p.stop);
+        if (e != cudaSuccess) return cuda_error(e, "ldpc_prof_read: elapsed");
+        if (p.kind >= 0 && p.kind < LDPC_K_COUNT) {
+            out->launches[p.kind] += 1;
+            out->total_ms[p.kind] += ms;
+        }
+    }
+    if (reset) {
+        for (auto &p : c->prof) {
+            c->event_pool.push_back(p.start);
+            c->event_pool.push_back(p.stop);
+        }
+        c->prof.clear();
+    }
+    return LDPC_OK;
+}

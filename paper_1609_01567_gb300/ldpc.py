@@ -1,0 +1,280 @@
+"""Thin Python binding of the C ABI in ``include/ldpc.h`` (argument marshalling only).
+
+Every function has the name of the C entry point it calls. Device buffers are
+PyTorch CUDA tensors (PyTorch provides memory and streams; all decoding runs
+in the library's kernels). The library must be built (``build.build()``); if
+it is missing or a call fails, an exception is raised -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LDPC_MSG = {"f32": 0, "f16": 1, "bf16": 2}
+KERNEL_CLASSES = ("interleave", "check", "bit", "syndrome", "finalize", "other")
+
+
+class LdpcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"ldpc status {status}: {message}")
+        self.status = status
+
+
+class ldpc_code_opts_t(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32)]
+
+
+class ldpc_code_info_t(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("n_edges", ctypes.c_int64),
+                ("max_check_degree", ctypes.c_int32), ("max_var_degree", ctypes.c_int32),
+                ("mean_check_degree", ctypes.c_double), ("mean_var_degree", ctypes.c_double),
+                ("n_check_bins", ctypes.c_int32), ("check_bin_max_degree", ctypes.c_int32 * 8),
+                ("check_bin_count", ctypes.c_int32 * 8), ("device", ctypes.c_int32)]
+
+
+class ldpc_decode_opts_t(ctypes.Structure):
+    _fields_ = [("early_exit", ctypes.c_int32), ("l_max", ctypes.c_float), ("msg_dtype", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("r_out", ctypes.c_void_p)]
+
+
+class ldpc_prof_t(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 6), ("total_ms", ctypes.c_double * 6)]
+
+
+EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
+           "ldpc_decode_host", "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
+           "ldpc_version")
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def library():
+    """The loaded C library (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = _build.library_path()
+            if not path.exists():
+                raise RuntimeError(f"libldpc_gb300 is not built ({path}); run __graft_entry__.build()")
+            lib = ctypes.CDLL(str(path))
+            vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+            lib.ldpc_code_create.argtypes = [i32, i32, i64, vp, vp, ctypes.POINTER(ldpc_code_opts_t), ctypes.POINTER(vp)]
+            lib.ldpc_code_destroy.argtypes = [vp]
+            lib.ldpc_code_destroy.restype = None
+            lib.ldpc_code_info.argtypes = [vp, ctypes.POINTER(ldpc_code_info_t)]
+            lib.ldpc_code_tables.argtypes = [vp] + [vp] * 11
+            lib.ldpc_decode.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ldpc_decode_opts_t), vp, vp, vp, vp, vp]
+            lib.ldpc_decode_host.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ldpc_decode_opts_t), vp, vp, vp, vp, vp]
+            lib.ldpc_gen_awgn.argtypes = [u64, i64, i32, i32, ctypes.c_float, vp, vp, vp]
+            lib.ldpc_philox4x64_10.argtypes = [u64, u64, u64, u64, i64, vp, vp]
+            lib.ldpc_prof_read.argtypes = [vp, ctypes.POINTER(ldpc_prof_t), i32]
+            lib.ldpc_last_error.restype = ctypes.c_char_p
+            lib.ldpc_version.restype = ctypes.c_char_p
+            for name in ("ldpc_code_create", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode", "ldpc_decode_host",
+                         "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read"):
+                getattr(lib, name).restype = ctypes.c_int
+            _LIB = lib
+        return _LIB
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise LdpcError(status, library().ldpc_last_error().decode(errors="replace"))
+
+
+def ldpc_version() -> str:
+    return library().ldpc_version().decode()
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, shape, name, device):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the code is on cuda:{device}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Code:
+    """Owner of an ``ldpc_code_t`` handle (released by :meth:`close` or GC)."""
+
+    def __init__(self, handle, m, n, n_edges, device):
+        self._h = handle
+        self.m, self.n, self.n_edges, self.device = m, n, n_edges, device
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("code is closed")
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            library().ldpc_code_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ldpc_code_create(m: int, n: int, rows, cols, device: int = 0) -> Code:
+    """Build a code from the COO of H (``rows``, ``cols``: int sequences)."""
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    if r.shape != c.shape or r.ndim != 1:
+        raise ValueError("rows and cols must be 1-D of equal length")
+    h = ctypes.c_void_p()
+    opts = ldpc_code_opts_t(device=device)
+    _check(library().ldpc_code_create(m, n, r.shape[0], r.ctypes.data_as(ctypes.c_void_p),
+                                      c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts), ctypes.byref(h)))
+    return Code(h, m, n, int(r.shape[0]), device)
+
+
+def ldpc_code_info(code: Code) -> dict:
+    info = ldpc_code_info_t()
+    _check(library().ldpc_code_info(code.handle, ctypes.byref(info)))
+    nb = info.n_check_bins
+    return {"m": info.m, "n": info.n, "n_edges": info.n_edges, "max_check_degree": info.max_check_degree,
+            "max_var_degree": info.max_var_degree, "mean_check_degree": info.mean_check_degree,
+            "mean_var_degree": info.mean_var_degree, "check_bin_max_degree": list(info.check_bin_max_degree[:nb]),
+            "check_bin_count": list(info.check_bin_count[:nb]), "device": info.device}
+
+
+TABLE_NAMES = ("v", "c", "t", "s", "u", "ebar", "vbar", "cbar", "tbar", "sbar", "ubar")
+
+
+def ldpc_code_tables(code: Code) -> dict:
+    """The address-iterator arrays of Tables 1-2 as numpy int32 arrays."""
+    arrs = {k: np.zeros(code.n_edges, dtype=np.int32) for k in TABLE_NAMES}
+    _check(library().ldpc_code_tables(code.handle, *[arrs[k].ctypes.data_as(ctypes.c_void_p) for k in TABLE_NAMES]))
+    return arrs
+
+
+def _opts(early_exit, l_max, msg_dtype, profile, r_out_ptr):
+    if msg_dtype not in LDPC_MSG:
+        raise ValueError(f"msg_dtype must be one of {sorted(LDPC_MSG)}")
+    return ldpc_decode_opts_t(early_exit=1 if early_exit else 0, l_max=float(l_max), msg_dtype=LDPC_MSG[msg_dtype],
+                              profile=1 if profile else 0, r_out=r_out_ptr)
+
+
+def ldpc_decode(code: Code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
+                msg_dtype: str = "f32", profile: bool = False, want_post: bool = True, want_r: bool = False,
+                out: dict | None = None, stream=None) -> dict:
+    """Decode ``llr`` (CUDA float32 [F, n]); returns CUDA tensors
+    ``bits`` uint8 [F, n], ``iters`` int32 [F], ``ok`` uint8 [F] and, when
+    asked, ``post`` float32 [F, n] and ``r`` float32 [F, E] (edge order)."""
+    import torch
+    f = int(llr.shape[0]) if llr.dim() == 2 else -1
+    dev = torch.device("cuda", code.device)
+    _dev_ptr(llr, torch.float32, (f, code.n), "llr", code.device)
+    o = dict(out or {})
+    if "bits" not in o:
+        o["bits"] = torch.empty((f, code.n), dtype=torch.uint8, device=dev)
+    if "iters" not in o:
+        o["iters"] = torch.empty((f,), dtype=torch.int32, device=dev)
+    if "ok" not in o:
+        o["ok"] = torch.empty((f,), dtype=torch.uint8, device=dev)
+    if want_post and "post" not in o:
+        o["post"] = torch.empty((f, code.n), dtype=torch.float32, device=dev)
+    if want_r and "r" not in o:
+        o["r"] = torch.empty((f, code.n_edges), dtype=torch.float32, device=dev)
+    r_ptr = _dev_ptr(o.get("r"), torch.float32, (f, code.n_edges), "r", code.device) if want_r else None
+    opts = _opts(early_exit, l_max, msg_dtype, profile, r_ptr.value if r_ptr else None)
+    _check(library().ldpc_decode(
+        code.handle, _dev_ptr(llr, torch.float32, (f, code.n), "llr", code.device), f, max_iter, ctypes.byref(opts),
+        _dev_ptr(o["bits"], torch.uint8, (f, code.n), "bits", code.device),
+        _dev_ptr(o["iters"], torch.int32, (f,), "iters", code.device),
+        _dev_ptr(o["ok"], torch.uint8, (f,), "ok", code.device),
+        _dev_ptr(o.get("post"), torch.float32, (f, code.n), "post", code.device) if want_post else None,
+        _stream_handle(stream)))
+    return o
+
+
+def ldpc_decode_host(code: Code, llr: np.ndarray, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
+                     msg_dtype: str = "f32", profile: bool = False, want_post: bool = False, out: dict | None = None,
+                     stream=None) -> dict:
+    """Decode host LLRs (numpy float32 [F, n], or a pinned CPU torch tensor);
+    copies in and out inside the call and returns host arrays."""
+    import torch
+    if isinstance(llr, torch.Tensor):
+        if llr.is_cuda or llr.dtype != torch.float32 or not llr.is_contiguous():
+            raise ValueError("llr must be a contiguous float32 host tensor")
+        f, n = llr.shape
+        llr_ptr = ctypes.c_void_p(llr.data_ptr())
+        mk = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=llr.is_pinned())  # noqa: E731
+        dts = (torch.uint8, torch.int32, torch.uint8, torch.float32)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    else:
+        llr = np.ascontiguousarray(llr, dtype=np.float32)
+        f, n = llr.shape
+        llr_ptr = llr.ctypes.data_as(ctypes.c_void_p)
+        mk = lambda shape, dt: np.empty(shape, dtype=dt)  # noqa: E731
+        dts = (np.uint8, np.int32, np.uint8, np.float32)
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    if n != code.n:
+        raise ValueError("llr has the wrong code length")
+    o = dict(out or {})
+    o.setdefault("bits", mk((f, n), dts[0]))
+    o.setdefault("iters", mk((f,), dts[1]))
+    o.setdefault("ok", mk((f,), dts[2]))
+    if want_post:
+        o.setdefault("post", mk((f, n), dts[3]))
+    opts = _opts(early_exit, l_max, msg_dtype, profile, None)
+    _check(library().ldpc_decode_host(code.handle, llr_ptr, f, max_iter, ctypes.byref(opts), ptr(o["bits"]),
+                                      ptr(o["iters"]), ptr(o["ok"]), ptr(o["post"]) if want_post else None,
+                                      _stream_handle(stream)))
+    return o
+
+
+def ldpc_gen_awgn(seed: int, frame_offset: int, n_frames: int, n: int, sigma2: float, codewords=None, out=None,
+                  device: int = 0, stream=None):
+    """BPSK/AWGN channel LLRs (CUDA float32 [n_frames, n]) from the on-device
+    Philox-4x64-10 generator; ``codewords`` is a CUDA uint8 [n_frames, n]
+    tensor or None (all-zero word)."""
+    import torch
+    if out is None:
+        out = torch.empty((n_frames, n), dtype=torch.float32, device=torch.device("cuda", device))
+    _check(library().ldpc_gen_awgn(seed, frame_offset, n_frames, n, float(sigma2),
+                                   _dev_ptr(codewords, torch.uint8, (n_frames, n), "codewords", None),
+                                   _dev_ptr(out, torch.float32, (n_frames, n), "out", None), _stream_handle(stream)))
+    return out
+
+
+def ldpc_philox4x64_10(key0: int, key1: int, ctr0: int, ctr1: int, count: int, device: int = 0, stream=None):
+    """Raw Philox-4x64-10 blocks as a CUDA int64 tensor [count, 4] (bit pattern of uint64)."""
+    import torch
+    out = torch.empty((count, 4), dtype=torch.int64, device=torch.device("cuda", device))
+    _check(library().ldpc_philox4x64_10(key0, key1, ctr0, ctr1, count, ctypes.c_void_p(out.data_ptr()),
+                                        _stream_handle(stream)))
+    return out
+
+
+def ldpc_prof_read(code: Code, reset: bool = True) -> dict:
+    """Per kernel class: launches and total CUDA-event milliseconds."""
+    p = ldpc_prof_t()
+    _check(library().ldpc_prof_read(code.handle, ctypes.byref(p), 1 if reset else 0))
+    return {k: {"launches": int(p.launches[i]), "total_ms": float(p.total_ms[i])} for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def code_from_inputs(code, device: int = 0) -> Code:
+    """Convenience: an ``ldpc_code_t`` from an ``inputs.Code``."""
+    return ldpc_code_create(code.m, code.n, code.rows, code.cols, device=device)

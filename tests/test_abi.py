@@ -1,0 +1,113 @@
+"""The C ABI on the CPU: symbols, host tables, argument errors (no GPU work).
+
+Codes are created host-only (device -1), which builds the tables without
+touching a GPU; decoding such a code must refuse with LDPC_ENODEV.
+"""
+import ctypes
+import re
+import subprocess
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_1609_01567_gb300 import build as lib_build
+from paper_1609_01567_gb300 import inputs as I
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module")
+def ldpc():
+    lib_build.build()
+    from paper_1609_01567_gb300 import ldpc as mod
+    return mod
+
+
+def declared_functions():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = h.read_text()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(ldpc_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(ldpc):
+    names = declared_functions()
+    assert {"ldpc_code_create", "ldpc_decode", "ldpc_gen_awgn"} <= names
+    out = subprocess.run(["nm", "-D", "--defined-only", str(lib_build.library_path())], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = names - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+    assert set(ldpc.EXPORTS) == names
+    lib = ldpc.library()
+    for n in names:
+        getattr(lib, n)
+    assert "sm_103a" in ldpc.ldpc_version()
+
+
+def test_host_tables_reproduce_tables_1_and_2(ldpc):
+    code = I.code_14_7()
+    h = ldpc.ldpc_code_create(code.m, code.n, code.rows, code.cols, device=-1)
+    got = ldpc.ldpc_code_tables(h)
+    for number in (1, 2):
+        for name, want in I.table(number).items():
+            if name == "e":
+                continue
+            np.testing.assert_array_equal(got[name], want, err_msg=f"Table {number} array {name}")
+
+
+def test_edge_ids_follow_a_stable_sort_by_column(ldpc):
+    """Shuffling the COO and reading the tables back gives the same graph,
+    with edge ids ordered by (column, position in the COO)."""
+    code = I.small_code_n1008()
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(code.n_edges)
+    rows, cols = code.rows[perm], code.cols[perm]
+    h = ldpc.ldpc_code_create(code.m, code.n, rows, cols, device=-1)
+    t = ldpc.ldpc_code_tables(h)
+    order = np.argsort(cols, kind="stable")
+    np.testing.assert_array_equal(t["v"], cols[order])
+    np.testing.assert_array_equal(t["c"], rows[order])
+    np.testing.assert_array_equal(t["ebar"], np.argsort(t["c"], kind="stable"))
+    np.testing.assert_array_equal(t["vbar"], t["v"][t["ebar"]])
+
+
+def test_code_info_and_degree_bins(ldpc):
+    code = I.large_code_n64800()
+    h = ldpc.ldpc_code_create(code.m, code.n, code.rows, code.cols, device=-1)
+    info = ldpc.ldpc_code_info(h)
+    assert info["m"] == 32400 and info["n"] == 64800 and info["n_edges"] == 194399
+    assert info["max_check_degree"] == 6 and info["max_var_degree"] == 8
+    assert info["check_bin_count"] == [0, 32400, 0, 0, 0]
+    assert info["device"] == -1
+    big = I.ira_code(8192, 6144, {3: 0.7, 4: 0.3}, seed=3, var_degree_overrides={0: 64},
+                     check_h1_overrides={5: 94})
+    hb = ldpc.ldpc_code_create(big.m, big.n, big.rows, big.cols, device=-1)
+    ib = ldpc.ldpc_code_info(hb)
+    assert ib["max_check_degree"] == 96 and ib["max_var_degree"] == 64
+    assert ib["check_bin_count"][4] == 1
+
+
+def test_argument_errors(ldpc):
+    with pytest.raises(ldpc.LdpcError) as e:
+        ldpc.ldpc_code_create(2, 2, [0, 0], [1, 1], device=-1)
+    assert e.value.status == -2 and "more than once" in str(e.value)
+    with pytest.raises(ldpc.LdpcError) as e:
+        ldpc.ldpc_code_create(2, 2, [0, 2], [1, 1], device=-1)
+    assert e.value.status == -1
+    with pytest.raises(ldpc.LdpcError) as e:
+        ldpc.ldpc_code_create(-1, 2, [], [], device=-1)
+    assert e.value.status == -1
+    empty = ldpc.ldpc_code_create(3, 4, [], [], device=-1)
+    assert ldpc.ldpc_code_info(empty)["n_edges"] == 0
+    lib = ldpc.library()
+    h = ldpc.ldpc_code_create(1, 2, [0, 0], [0, 1], device=-1)
+    st = lib.ldpc_decode(h.handle, None, 1, 5, None, None, None, None, None, None)
+    assert st == -7
+    assert lib.ldpc_gen_awgn(1, 0, 1, 4, ctypes.c_float(0.0), None, None, None) == -1
+    assert lib.ldpc_gen_awgn(1, 0, -1, 4, ctypes.c_float(1.0), None, None, None) == -1
+    assert lib.ldpc_philox4x64_10(0, 0, 0, 0, -1, None, None) == -1
