@@ -129,6 +129,13 @@ typedef struct {
     float *r_out;       /* optional device [n_frames][n_edges] float: the last
                            check-to-bit messages in edge order (for checking
                            one iteration at a time); NULL to skip            */
+    int32_t frames_per_lane; /* tuning: frames each GPU lane carries in the
+                           bit-node kernel (1, 2 or 4); 0 picks by batch size */
+    int32_t check_schedule;  /* tuning: check-node kernel schedule; 0 = auto,
+                           1 = inputs loaded straight from global memory,
+                           2 = rows staged through a shared-memory pipeline
+                           (when the batch allows). Results do not depend on
+                           either tuning field                               */
 } ldpc_decode_opts_t;
 
 /*

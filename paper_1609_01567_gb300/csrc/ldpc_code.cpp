@@ -46,6 +46,7 @@ static void free_device_tables(ldpc_code *c) {
     cudaFree(c->d.col_ptr);
     cudaFree(c->d.edge_slot);
     cudaFree(c->d.bin_checks);
+    cudaFree(c->d.bin_desc);
     Workspace &w = c->ws;
     if (w.last_use) cudaEventSynchronize(w.last_use);
     cudaFree(w.lamT);
@@ -160,6 +161,8 @@ extern "C" int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t
             }
         }
         c->bin_off[kNumCheckBins] = (int32_t)c->bin_checks.size();
+        c->bin_desc.reserve(c->bin_checks.size());
+        for (int32_t i : c->bin_checks) c->bin_desc.push_back(make_int2(c->row_ptr[i], c->row_ptr[i + 1] - c->row_ptr[i]));
     } catch (const std::bad_alloc &) {
         delete c;
         return set_error(LDPC_ENOMEM, "ldpc_code_create: out of host memory");
@@ -183,6 +186,7 @@ extern "C" int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t
             (e = upload(&c->d.col_ptr, c->col_ptr)) != cudaSuccess ||
             (e = upload(&c->d.edge_slot, c->edge_slot)) != cudaSuccess ||
             (e = upload(&c->d.bin_checks, c->bin_checks)) != cudaSuccess ||
+            (e = upload(&c->d.bin_desc, c->bin_desc)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&c->ws.last_use, cudaEventDisableTiming)) != cudaSuccess) {
             int st = cuda_error(e, "ldpc_code_create: device upload");
             free_device_tables(c);

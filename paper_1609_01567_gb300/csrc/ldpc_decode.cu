@@ -129,14 +129,13 @@ struct DeviceGuard {
 
 static int msg_size(int dtype) { return dtype == LDPC_MSG_F32 ? 4 : 2; }
 
-static void frames_layout(int32_t F, int32_t *V, int32_t *Fp) {
-    if (F > 64) {
-        *V = 4;
-        *Fp = (F + 127) / 128 * 128;
-    } else {
-        *V = 1;
-        *Fp = (F + 31) / 32 * 32;
-    }
+// Frames per lane V and padded frame count Fp (a multiple of 32 V).
+// `want` = 0 picks: one frame per lane for tiny batches, else two.
+static void frames_layout(int32_t F, int32_t want, int32_t *V, int32_t *Fp) {
+    int32_t v = want;
+    if (v != 1 && v != 2 && v != 4) v = F > 32 ? 2 : 1;
+    *V = v;
+    *Fp = (F + 32 * v - 1) / (32 * v) * (32 * v);
 }
 
 template <typename T>
@@ -220,7 +219,7 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
                              cudaStream_t s) {
     Workspace &w = c->ws;
     int32_t V, Fp;
-    frames_layout(F, &V, &Fp);
+    frames_layout(F, o.frames_per_lane, &V, &Fp);
     PassArgs a{};
     a.row_ptr = c->d.row_ptr;
     a.col_idx = c->d.col_idx;
@@ -238,10 +237,14 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
     a.early_exit = o.early_exit ? 1 : 0;
     a.l_max = l_max;
     a.phi_lmax = (float)std::log1p(2.0 / std::expm1((double)l_max));
+    a.c_min = (float)(2.0 / (std::exp((double)l_max) + 1.0));
+    a.c_max = (float)(-std::expm1(-(double)l_max));
     a.done = w.done;
     a.unsat = w.unsat;
     a.stop_iter = w.stop_iter;
     a.grid_ctas = std::max(1, c->sm_count) * 4;
+    a.sm_count = std::max(1, c->sm_count);
+    a.check_schedule = o.check_schedule;
 
     Launcher L{c, s, o.profile != 0};
     cudaError_t e;
@@ -267,7 +270,10 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
         for (int b = 0; b < kNumCheckBins; ++b) {
             int32_t count = c->bin_off[b + 1] - c->bin_off[b];
             if (count == 0) continue;
-            e = L(LDPC_K_CHECK, [&] { return launch_check_bin<M>(a, b, c->d.bin_checks + c->bin_off[b], count, s); });
+            e = L(LDPC_K_CHECK, [&] {
+                return launch_check_bin<M>(a, b, c->d.bin_checks + c->bin_off[b], c->d.bin_desc + c->bin_off[b], count,
+                                           s);
+            });
             if (e != cudaSuccess) return e;
         }
         if (c->n > 0) {
@@ -278,9 +284,11 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
     uint32_t *final_row = w.unsat + (size_t)max_iter * words;
     if (c->m > 0 && c->E > 0) {
         e = L(LDPC_K_SYNDROME, [&] {
-            dim3 grid = pass_grid(a, c->m);
+            dim3 grid = pass_grid(a, c->m, V);
             if (V == 4)
                 k_syndrome<4><<<grid, kThreads, 0, s>>>(a, final_row);
+            else if (V == 2)
+                k_syndrome<2><<<grid, kThreads, 0, s>>>(a, final_row);
             else
                 k_syndrome<1><<<grid, kThreads, 0, s>>>(a, final_row);
             return cudaGetLastError();
@@ -311,6 +319,10 @@ static int check_decode_args(const ldpc_code *c, int32_t F, int32_t max_iter, co
     if (max_iter < 0 || max_iter > 100000) return set_error(LDPC_EINVAL, "%s: max_iter=%d outside [0, 100000]", fn, max_iter);
     float l_max = o.l_max > 0.0f ? o.l_max : 20.0f;
     if (!(l_max <= 80.0f)) return set_error(LDPC_EINVAL, "%s: l_max=%g outside (0, 80]", fn, (double)o.l_max);
+    if (o.check_schedule < 0 || o.check_schedule > 2)
+        return set_error(LDPC_EINVAL, "%s: check_schedule=%d not in {0, 1, 2}", fn, o.check_schedule);
+    if (o.frames_per_lane != 0 && o.frames_per_lane != 1 && o.frames_per_lane != 2 && o.frames_per_lane != 4)
+        return set_error(LDPC_EINVAL, "%s: frames_per_lane=%d not in {0, 1, 2, 4}", fn, o.frames_per_lane);
     if (o.msg_dtype != LDPC_MSG_F32 && o.msg_dtype != LDPC_MSG_F16 && o.msg_dtype != LDPC_MSG_BF16)
         return set_error(LDPC_EINVAL, "%s: unknown msg_dtype %d", fn, o.msg_dtype);
     *l_max_out = l_max;
@@ -331,7 +343,7 @@ static int decode_locked(ldpc_code *c, const float *llr, int32_t F, int32_t max_
                          float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok, float *post, cudaStream_t s) {
     int32_t chunk = std::min(F, kMaxChunkFrames);
     int32_t V, Fp;
-    frames_layout(chunk, &V, &Fp);
+    frames_layout(chunk, o.frames_per_lane, &V, &Fp);
     int st = ensure_workspace(c, Fp, max_iter, msg_size(o.msg_dtype));
     if (st != LDPC_OK) return st;
     cudaError_t e = cudaStreamWaitEvent(s, c->ws.last_use, 0);

@@ -39,6 +39,7 @@ struct DeviceTables {
     int32_t *col_ptr = nullptr;    // [n+1] first edge of each variable (s)
     int32_t *edge_slot = nullptr;  // [E]   check-order slot of each edge id (inverse of ebar)
     int32_t *bin_checks = nullptr; // [m']  checks grouped by degree bin
+    int2 *bin_desc = nullptr;      // [m']  (first slot, degree) of each binned check
 };
 
 // Arguments of one flooding pass, shared by the kernels of all bins.
@@ -60,14 +61,19 @@ struct PassArgs {
     int32_t early_exit;
     float l_max;
     float phi_lmax;      // phi(l_max)
+    float c_min;         // 1 - tanh(l_max / 2): complement of the largest |r|
+    float c_max;         // 1 - e^-l_max: complement of the smallest |r|
     uint32_t *done;      // [Fp/32]
     uint32_t *unsat;     // [max_iter + 1][Fp/32]
     int32_t *stop_iter;  // [Fp] iteration at which a frame stopped
     int32_t grid_ctas;   // CTAs per launch target (a multiple of the SM count)
+    int32_t sm_count;
+    int32_t check_schedule;  // 0 auto, 1 direct loads, 2 shared-memory pipeline
 };
 
 template <typename M>
-cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, int32_t count, cudaStream_t s);
+cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, const int2 *desc, int32_t count,
+                             cudaStream_t s);
 template <typename M>
 cudaError_t launch_bit(const PassArgs &a, cudaStream_t s);
 template <typename M>
@@ -117,6 +123,7 @@ struct ldpc_code {
     std::vector<int32_t> col_idx;       // vbar [E]
     std::vector<int32_t> edge_slot;     // [E]
     std::vector<int32_t> bin_checks;
+    std::vector<int2> bin_desc;
     int32_t bin_off[ldpc::kNumCheckBins + 1] = {0};
     // device side
     int device = -1;

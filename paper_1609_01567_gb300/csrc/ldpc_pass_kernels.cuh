@@ -52,6 +52,13 @@ struct MsgIO<float> {
     static __device__ __forceinline__ void store4(float *p, const float (&x)[4]) {
         *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
     }
+    static __device__ __forceinline__ void load2(const float *p, float (&x)[2]) {
+        float2 v = *reinterpret_cast<const float2 *>(p);
+        x[0] = v.x; x[1] = v.y;
+    }
+    static __device__ __forceinline__ void store2(float *p, const float (&x)[2]) {
+        *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+    }
     static __device__ __forceinline__ float load1(const float *p) { return *p; }
     static __device__ __forceinline__ void store1(float *p, float x) { *p = x; }
 };
@@ -71,6 +78,13 @@ struct MsgIO<__half> {
         raw.x = *reinterpret_cast<uint32_t *>(&a);
         raw.y = *reinterpret_cast<uint32_t *>(&b);
         *reinterpret_cast<uint2 *>(p) = raw;
+    }
+    static __device__ __forceinline__ void load2(const __half *p, float (&x)[2]) {
+        float2 a = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        x[0] = a.x; x[1] = a.y;
+    }
+    static __device__ __forceinline__ void store2(__half *p, const float (&x)[2]) {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(x[0], x[1]);
     }
     static __device__ __forceinline__ float load1(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void store1(__half *p, float x) { *p = __float2half_rn(x); }
@@ -92,6 +106,13 @@ struct MsgIO<__nv_bfloat16> {
         raw.y = *reinterpret_cast<uint32_t *>(&b);
         *reinterpret_cast<uint2 *>(p) = raw;
     }
+    static __device__ __forceinline__ void load2(const __nv_bfloat16 *p, float (&x)[2]) {
+        float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+        x[0] = a.x; x[1] = a.y;
+    }
+    static __device__ __forceinline__ void store2(__nv_bfloat16 *p, const float (&x)[2]) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(x[0], x[1]);
+    }
     static __device__ __forceinline__ float load1(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void store1(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
 };
@@ -100,6 +121,8 @@ template <int V, typename M>
 __device__ __forceinline__ void load_v(const M *p, float (&x)[V]) {
     if constexpr (V == 4) {
         MsgIO<M>::load4(p, x);
+    } else if constexpr (V == 2) {
+        MsgIO<M>::load2(p, x);
     } else {
 #pragma unroll
         for (int v = 0; v < V; ++v) x[v] = MsgIO<M>::load1(p + v);
@@ -110,6 +133,8 @@ template <int V, typename M>
 __device__ __forceinline__ void store_v(M *p, const float (&x)[V]) {
     if constexpr (V == 4) {
         MsgIO<M>::store4(p, x);
+    } else if constexpr (V == 2) {
+        MsgIO<M>::store2(p, x);
     } else {
 #pragma unroll
         for (int v = 0; v < V; ++v) MsgIO<M>::store1(p + v, x[v]);
@@ -137,42 +162,99 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // phi(x) = ln((1 + t) / (1 - t)), t = e^-x, for 0 < x <= 80.
-//  * t = 2^(-x log2 e) with the product split exactly by an FMA, so the
-//    exponent carries no rounding error beyond ~1e-12 relative.
+//  * t = 2^(-x log2 e): the product x log2(e) is split exactly by an FMA (and
+//    the rounding of log2(e) itself is added back), so t keeps ~1e-7
+//    relative accuracy even at x = 80.
 //  * t < 1/16: phi = 2 atanh(t) = 2t (1 + t^2/3 + t^4/5 + t^6/7 + ...), the
 //    series truncated after t^6/7 (relative error < 1e-10); this keeps full
 //    relative precision for the tiny values that the sums of large-|q|
 //    inputs are made of.
 //  * otherwise phi = ln((1 + t) / (1 - t)), with 1 - t = 1 - e^-x from its
 //    Taylor series below x = 1/4 (where 1 - t would cancel).
-__device__ __forceinline__ float phi_core(float x) {
-    const float kL2E = 1.44269502162933349609375f;   // log2(e) rounded to float
-    const float kL2ELo = 1.925963033500011e-08f;     // log2(e) - kL2E
-    const float kLn2 = 0.693147180559945309f;
-    float p = -x * kL2E;
-    float pe = fmaf(-x, kL2E, -p) - x * kL2ELo;
-    float t = ex2_approx(p);
-    t = fmaf(t, pe * kLn2, t);
-    if (t < 0.0625f) {
-        float t2 = t * t;
-        float poly = fmaf(t2, fmaf(t2, fmaf(t2, 1.0f / 7.0f, 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
-        return 2.0f * t * poly;
-    }
-    float u, num;
-    if (x < 0.25f) {
-        u = x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, -1.0f / 720.0f, 1.0f / 120.0f), -1.0f / 24.0f), 1.0f / 6.0f),
-                             -0.5f),
-                     1.0f);
-        num = 2.0f - u;
-    } else {
-        u = 1.0f - t;
-        num = 1.0f + t;
-    }
-    return lg2_approx(num * rcp_approx(u)) * kLn2;
-}
+// The scalar form and the two-frame form below execute the same operations
+// in the same order (the packed FP32 instructions round element-wise like
+// their scalar counterparts), so results do not depend on how many frames a
+// lane carries.
+constexpr float kL2E = 1.44269502162933349609375f;  // log2(e) rounded to float
+constexpr float kL2ELo = 1.925963033500011e-08f;    // log2(e) - kL2E
+constexpr float kLn2 = 0.693147180559945309f;
 
 __device__ __forceinline__ float phi_hat(float x, float l_max, float phi_lmax) {
-    return phi_core(fminf(fmaxf(x, phi_lmax), l_max));
+    x = fminf(fmaxf(x, phi_lmax), l_max);
+    float pn = x * -kL2E;
+    float e = fmaf(x, kL2E, pn);
+    e = fmaf(x, kL2ELo, e);
+    float t = ex2_approx(pn);
+    t = fmaf(t, e * -kLn2, t);
+    float t2 = t * t;
+    float poly = fmaf(t2, fmaf(t2, fmaf(t2, 1.0f / 7.0f, 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
+    float res = (t + t) * poly;
+    if (t >= 0.0625f) {
+        float us = x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, -1.0f / 720.0f, 1.0f / 120.0f), -1.0f / 24.0f),
+                                            1.0f / 6.0f),
+                                    -0.5f),
+                            1.0f);
+        float u1 = fmaf(t, -1.0f, 1.0f);
+        float u = x < 0.25f ? us : u1;
+        float num = fmaf(u, -1.0f, 2.0f);
+        float ratio = num * rcp_approx(u);
+        res = lg2_approx(ratio) * kLn2;
+    }
+    return res;
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// phi^ of two frames at once. Must be called by all 32 lanes of the warp
+// (the logarithm branch is skipped when no lane of the warp needs it).
+__device__ __forceinline__ float2 phi_hat2(float2 x, float l_max, float phi_lmax) {
+    x.x = fminf(fmaxf(x.x, phi_lmax), l_max);
+    x.y = fminf(fmaxf(x.y, phi_lmax), l_max);
+    // t = e^-x
+    float2 pn = mul2(x, f2(-kL2E));                 // -fl(x log2 e)
+    float2 e = fma2(x, f2(kL2E), pn);               // x log2 e - fl(x log2 e), exact
+    e = fma2(x, f2(kL2ELo), e);
+    float2 t = make_float2(ex2_approx(pn.x), ex2_approx(pn.y));
+    t = fma2(t, mul2(e, f2(-kLn2)), t);
+    // small t: 2 atanh(t)
+    float2 t2 = mul2(t, t);
+    float2 poly = fma2(t2, fma2(t2, fma2(t2, f2(1.0f / 7.0f), f2(1.0f / 5.0f)), f2(1.0f / 3.0f)), f2(1.0f));
+    float2 res = mul2(add2(t, t), poly);
+    const bool big_x = t.x >= 0.0625f, big_y = t.y >= 0.0625f;
+    if (__any_sync(kFull, big_x || big_y)) {
+        float2 us = mul2(
+            x, fma2(x, fma2(x, fma2(x, fma2(x, fma2(x, f2(-1.0f / 720.0f), f2(1.0f / 120.0f)), f2(-1.0f / 24.0f)),
+                                    f2(1.0f / 6.0f)),
+                            f2(-0.5f)),
+                    f2(1.0f)));
+        float2 u1 = fma2(t, f2(-1.0f), f2(1.0f));
+        float2 u = make_float2(x.x < 0.25f ? us.x : u1.x, x.y < 0.25f ? us.y : u1.y);
+        float2 num = fma2(u, f2(-1.0f), f2(2.0f));
+        float2 ratio = mul2(num, make_float2(rcp_approx(u.x), rcp_approx(u.y)));
+        float2 lg = mul2(make_float2(lg2_approx(ratio.x), lg2_approx(ratio.y)), f2(kLn2));
+        res.x = big_x ? lg.x : res.x;
+        res.y = big_y ? lg.y : res.y;
+    }
+    return res;
+}
+
+// phi^ of V frames (pairs when V is even).
+template <int V>
+__device__ __forceinline__ void phi_hat_v(float (&x)[V], float l_max, float phi_lmax) {
+    if constexpr (V % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < V; v += 2) {
+            float2 y = phi_hat2(make_float2(x[v], x[v + 1]), l_max, phi_lmax);
+            x[v] = y.x;
+            x[v + 1] = y.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = phi_hat(x[v], l_max, phi_lmax);
+    }
 }
 
 // Error-free sum: s + err == a + b exactly.
@@ -181,6 +263,122 @@ __device__ __forceinline__ float two_sum(float a, float b, float &err) {
     float bb = s - a;
     err = (a - (s - bb)) + (b - bb);
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// The check rule in product form. Algorithm 1 ("Values to Variable Nodes")
+// computes r0 - r1 = prod_{j' != j} (1 - 2 q1_j'); in magnitudes this is
+//   tanh(|r_ij| / 2) = prod_{j' != j} T_j',   T = tanh(|q| / 2),
+// the same rule as phi(sum phi) above. The kernels carry it in complement
+// form so that nothing cancels: every input gives D = 1 - T = 2t / (1 + t),
+// t = e^-|q| (accurate for strong inputs, where T rounds to 1), partial
+// products are kept as C = 1 - prod T, merged by C(A u {k}) = C(A) + P(A) D_k
+// and P(A u {k}) = P(A) (1 - D_k) (sums of non-negative terms), and the
+// output magnitude is |r| = ln((1 + P) / (1 - P)) = ln((2 - C) / C).
+// Saturation: |q| is clamped to [phi(L), L] as in phi^, and C to the range
+// that keeps |r| in [phi(L), L]. Scalar and packed forms run the same
+// operations in the same order.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float tanh_complement(float x, float l_max, float phi_lmax) {
+    x = fminf(fmaxf(x, phi_lmax), l_max);
+    float pn = x * -kL2E;
+    float e = fmaf(x, kL2E, pn);
+    e = fmaf(x, kL2ELo, e);
+    float t = ex2_approx(pn);
+    t = fmaf(t, e * -kLn2, t);
+    float rr = rcp_approx(t + 1.0f);
+    return (t + t) * rr;
+}
+
+__device__ __forceinline__ float2 tanh_complement2(float2 x, float l_max, float phi_lmax) {
+    x.x = fminf(fmaxf(x.x, phi_lmax), l_max);
+    x.y = fminf(fmaxf(x.y, phi_lmax), l_max);
+    float2 pn = mul2(x, f2(-kL2E));
+    float2 e = fma2(x, f2(kL2E), pn);
+    e = fma2(x, f2(kL2ELo), e);
+    float2 t = make_float2(ex2_approx(pn.x), ex2_approx(pn.y));
+    t = fma2(t, mul2(e, f2(-kLn2)), t);
+    float2 tp = add2(t, f2(1.0f));
+    float2 rr = make_float2(rcp_approx(tp.x), rcp_approx(tp.y));
+    return mul2(add2(t, t), rr);
+}
+
+__device__ __forceinline__ float mag_of_complement(float c, float c_min, float c_max) {
+    c = fminf(fmaxf(c, c_min), c_max);
+    float ratio = fmaf(c, -1.0f, 2.0f) * rcp_approx(c);
+    return lg2_approx(ratio) * kLn2;
+}
+
+__device__ __forceinline__ float2 mag_of_complement2(float2 c, float c_min, float c_max) {
+    c.x = fminf(fmaxf(c.x, c_min), c_max);
+    c.y = fminf(fmaxf(c.y, c_min), c_max);
+    float2 ratio = mul2(fma2(c, f2(-1.0f), f2(2.0f)), make_float2(rcp_approx(c.x), rcp_approx(c.y)));
+    return mul2(make_float2(lg2_approx(ratio.x), lg2_approx(ratio.y)), f2(kLn2));
+}
+
+// Element-wise helpers over V frames (packed when V is even).
+template <int V>
+__device__ __forceinline__ void vtanh_complement(float (&x)[V], float l_max, float phi_lmax) {
+    if constexpr (V % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < V; v += 2) {
+            float2 y = tanh_complement2(make_float2(x[v], x[v + 1]), l_max, phi_lmax);
+            x[v] = y.x;
+            x[v + 1] = y.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = tanh_complement(x[v], l_max, phi_lmax);
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void vmag_of_complement(float (&c)[V], float c_min, float c_max) {
+    if constexpr (V % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < V; v += 2) {
+            float2 y = mag_of_complement2(make_float2(c[v], c[v + 1]), c_min, c_max);
+            c[v] = y.x;
+            c[v + 1] = y.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) c[v] = mag_of_complement(c[v], c_min, c_max);
+    }
+}
+
+// o = a * b + c
+template <int V>
+__device__ __forceinline__ void vfma(float (&o)[V], const float (&a)[V], const float (&b)[V], const float (&c)[V]) {
+    if constexpr (V % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < V; v += 2) {
+            float2 y = fma2(make_float2(a[v], a[v + 1]), make_float2(b[v], b[v + 1]), make_float2(c[v], c[v + 1]));
+            o[v] = y.x;
+            o[v + 1] = y.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = fmaf(a[v], b[v], c[v]);
+    }
+}
+
+// p = p * (1 - dk)
+template <int V>
+__device__ __forceinline__ void vscale_by_tanh(float (&p)[V], const float (&dk)[V]) {
+    if constexpr (V % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < V; v += 2) {
+            float2 tk = fma2(make_float2(dk[v], dk[v + 1]), f2(-1.0f), f2(1.0f));
+            float2 y = mul2(make_float2(p[v], p[v + 1]), tk);
+            p[v] = y.x;
+            p[v + 1] = y.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) p[v] = p[v] * fmaf(dk[v], -1.0f, 1.0f);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -196,8 +394,16 @@ __device__ __forceinline__ void or_frame_bits(uint32_t *row, int g, int lane, co
     if constexpr (V == 1) {
         uint32_t w = __ballot_sync(kFull, bits[0]);
         if (lane == 0 && w) atomicOr(row + g, w);
+    } else if constexpr (V == 2) {
+        uint32_t pair = (bits[0] ? 1u : 0u) | (bits[1] ? 2u : 0u);
+        uint32_t w = pair << ((lane & 15) * 2);
+        w |= __shfl_xor_sync(kFull, w, 1);
+        w |= __shfl_xor_sync(kFull, w, 2);
+        w |= __shfl_xor_sync(kFull, w, 4);
+        w |= __shfl_xor_sync(kFull, w, 8);
+        if ((lane & 15) == 0 && w) atomicOr(row + g * 2 + (lane >> 4), w);
     } else {
-        static_assert(V == 4, "V is 1 or 4");
+        static_assert(V == 4, "V is 1, 2 or 4");
         uint32_t nib = 0;
 #pragma unroll
         for (int v = 0; v < 4; ++v) nib |= (bits[v] ? 1u : 0u) << v;
@@ -213,7 +419,88 @@ __device__ __forceinline__ void or_frame_bits(uint32_t *row, int g, int lane, co
 // Check-node kernels
 // ---------------------------------------------------------------------------
 
-// Checks of degree <= D: a check's d messages stay in registers.
+// The check-node rule for one check of degree d <= D on V frames per lane,
+// in product/complement form. load(k, av, rv) fetches input k: av = APP_j
+// (or lambda_j on the first pass), rv = the previous message r_ij (unused on
+// the first pass). Writes the d new messages to rows out + k * Fp and ors the
+// check's syndrome of the previous hard decision into unsat.
+template <int D, int V, typename M, typename Load>
+__device__ __forceinline__ void check_node(int d, bool first, Load &&load, M *out, size_t Fp, const PassArgs &a,
+                                           bool (&unsat)[V]) {
+    float dc[D][V];    // D_k = 1 - tanh(|q_k| / 2)
+    uint32_t ones[V];  // bit k: input k says "bit 1" (q > 0)
+    uint32_t z[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) ones[v] = z[v] = 0u;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if (k < d) {
+            float av[V], rv[V];
+            load(k, av, rv);
+            if (!first) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    z[v] ^= av[v] > 0.0f ? 1u : 0u;
+                    av[v] = av[v] - rv[v];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                ones[v] |= (av[v] > 0.0f ? 1u : 0u) << k;
+                dc[k][v] = fabsf(av[v]);
+            }
+            vtanh_complement<V>(dc[k], a.l_max, a.phi_lmax);
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) dc[k][v] = 0.0f;  // T = 1: neutral
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) unsat[v] |= z[v] != 0u;
+    // complements of the suffix products, then a running prefix
+    float csuf[D][V];
+    {
+        float cr[V], pr[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            cr[v] = 0.0f;
+            pr[v] = 1.0f;
+        }
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) csuf[k][v] = cr[v];
+            vfma<V>(cr, pr, dc[k], cr);
+            vscale_by_tanh<V>(pr, dc[k]);
+        }
+    }
+    // output k is negative (bit-0 message) iff the other inputs hold an even
+    // number of ones, i.e. iff input k's bit equals the total parity
+    float cp[V], pp[V];
+    uint32_t neg[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        cp[v] = 0.0f;
+        pp[v] = 1.0f;
+        neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if (k < d) {
+            float o[V];
+            vfma<V>(o, pp, csuf[k], cp);  // C of all inputs but k
+            vmag_of_complement<V>(o, a.c_min, a.c_max);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                o[v] = __int_as_float(__float_as_int(o[v]) | (int)((neg[v] << (31 - k)) & 0x80000000u));
+            store_v<V, M>(out + (size_t)k * Fp, o);
+            vfma<V>(cp, pp, dc[k], cp);
+            vscale_by_tanh<V>(pp, dc[k]);
+        }
+    }
+}
+
+// Checks of degree <= D, inputs read straight from global memory.
 template <int D, int V, typename M>
 __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_t *__restrict__ checks,
                                                         int32_t count) {
@@ -242,81 +529,149 @@ __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_
     for (int w = blockIdx.x * (kThreads / 32) + warp; w < count; w += gridDim.x * (kThreads / 32)) {
         const int i = checks[w];
         const int b = a.row_ptr[i];
-        const int d = a.row_ptr[i + 1] - b;
-        float mag[D][V];
-        uint32_t ones[V];
-        uint32_t z[V];
+        const int d = a.row_ptr[i + 1] - b;  // warp-uniform, 1 <= d <= D
+        auto load = [&](int k, float (&av)[V], float (&rv)[V]) {
+            const int slot = b + k;
+            load_v<V, float>(qsrc + (size_t)a.col_idx[slot] * Fp + f0, av);
+            if (!first) load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
+        };
+        check_node<D, V, M>(d, first, load, r + (size_t)b * Fp + f0, Fp, a, unsat);
+    }
+    if (a.syndrome) {
+        bool bits[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) ones[v] = z[v] = 0u;
+        for (int v = 0; v < V; ++v) bits[v] = unsat[v] && live[v];
+        or_frame_bits<V>(a.unsat + (size_t)(a.pass - 1) * (a.Fp / 32), g, lane, bits);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Software-pipelined check kernel: every warp streams the rows of its next
+// S - 1 checks into its own shared-memory ring with 16-byte cp.async copies
+// while it computes the current one, so row loads overlap the check rule.
+// Check descriptors (first slot, degree) and column indices are fetched one
+// and two checks ahead of their copies.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int D, int V, typename M>
+struct PipeShape {
+    static constexpr int kRowA = 32 * V * 4;                  // bytes of one APP row segment
+    static constexpr int kRowR = 32 * V * (int)sizeof(M);     // bytes of one message row segment
+    static constexpr int kChunksA = kRowA / 16;
+    static constexpr int kChunksR = kRowR / 16;
+    static constexpr int kStage = D * (kRowA + kRowR);        // bytes of one check's rows
+};
+
+template <int D, int V, typename M, int S>
+__global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 *__restrict__ desc, int32_t count) {
+    using P = PipeShape<D, V, M>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    unsigned char *ring = smem + (size_t)warp * S * P::kStage;
+    const int g = blockIdx.y;
+    const int fbase = g * 32 * V;
+    const int f0 = fbase + lane * V;
+    const size_t Fp = (size_t)a.Fp;
+    M *r = reinterpret_cast<M *>(a.r);
+    const bool first = a.pass == 0;
+    const float *qsrc = first ? a.lamT : a.app;
+
+    bool live[V];
+    bool any_live = false;
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            if (k < d) {
-                const int slot = b + k;
-                const int j = a.col_idx[slot];
-                float av[V];
-                load_v<V, float>(qsrc + (size_t)j * Fp + f0, av);
-                float qv[V];
-                if (first) {
+    for (int v = 0; v < V; ++v) {
+        live[v] = !frame_bit(a.done, f0 + v);
+        any_live |= live[v];
+    }
+    if (!__any_sync(kFull, any_live)) return;
+    bool unsat[V];
 #pragma unroll
-                    for (int v = 0; v < V; ++v) qv[v] = av[v];
-                } else {
-                    float rv[V];
-                    load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        qv[v] = av[v] - rv[v];
-                        z[v] ^= av[v] > 0.0f ? 1u : 0u;
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    mag[k][v] = phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax);
-                    ones[v] |= (qv[v] > 0.0f ? 1u : 0u) << k;
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; ++v) mag[k][v] = 0.0f;
+    for (int v = 0; v < V; ++v) unsat[v] = false;
+
+    const int stride = gridDim.x * (kThreads / 32);
+    const int w0 = blockIdx.x * (kThreads / 32) + warp;
+
+    // Copy the d APP rows (and message rows) of one check into ring stage st.
+    auto issue = [&](int st, int b, int d, int jl) {
+        unsigned char *base = ring + st * P::kStage;
+        const int nA = d * P::kChunksA;
+        for (int c0 = 0; c0 < nA; c0 += 32) {
+            const int c = c0 + lane;
+            const int k = min(c / P::kChunksA, 31);
+            const int j = __shfl_sync(kFull, jl, k);
+            if (c < nA) {
+                const int o = c - k * P::kChunksA;
+                cp_async16(base + k * P::kRowA + o * 16,
+                           reinterpret_cast<const unsigned char *>(qsrc + (size_t)j * Fp + fbase) + o * 16);
             }
         }
-#pragma unroll
-        for (int v = 0; v < V; ++v) unsat[v] |= z[v] != 0u;
-        // exclusive sums: suffix sums first, then a running prefix
-        float suf[D][V];
-        {
-            float run[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) run[v] = 0.0f;
-#pragma unroll
-            for (int k = D - 1; k >= 0; --k) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    suf[k][v] = run[v];
-                    run[v] += mag[k][v];
-                }
+        if (!first) {
+            const int nR = d * P::kChunksR;
+            for (int c = lane; c < nR; c += 32) {
+                const int k = c / P::kChunksR;
+                const int o = c - k * P::kChunksR;
+                cp_async16(base + D * P::kRowA + k * P::kRowR + o * 16,
+                           reinterpret_cast<const unsigned char *>(r + (size_t)(b + k) * Fp + fbase) + o * 16);
             }
         }
-        float pre[V];
-        uint32_t par[V];
+    };
+    auto get_desc = [&](int w) { return w < count ? desc[w] : make_int2(0, 0); };
+    auto get_col = [&](int2 dd) { return lane < dd.y ? a.col_idx[dd.x + lane] : 0; };
+
+    // queue of the checks whose rows are in flight: (first slot, degree)
+    int qb[S], qd[S];
+    // prologue: stages 0 .. S-2
+    int2 nd = get_desc(w0);
+    int njl = get_col(nd);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            pre[v] = 0.0f;
-            par[v] = __popc(ones[v]) & 1u;
-        }
+    for (int s = 0; s < S - 1; ++s) {
+        issue(s, nd.x, nd.y, njl);
+        cp_async_commit();
+        qb[s] = nd.x;
+        qd[s] = nd.y;
+        nd = get_desc(w0 + (s + 1) * stride);
+        njl = get_col(nd);
+    }
+    int2 nd2 = get_desc(w0 + S * stride);
+    int n = 0;
+    for (int w = w0; w < count; w += stride, ++n) {
+        // rows of the check S - 1 ahead
+        issue((n + S - 1) % S, nd.x, nd.y, njl);
+        cp_async_commit();
+        qb[S - 1] = nd.x;
+        qd[S - 1] = nd.y;
+        nd = nd2;
+        njl = get_col(nd);
+        nd2 = get_desc(w + (S + 1) * stride);
+        cp_async_wait<S - 1>();
+        __syncwarp();
+        const unsigned char *base = ring + (n % S) * P::kStage;
+        auto load = [&](int k, float (&av)[V], float (&rv)[V]) {
+            const float *pa = reinterpret_cast<const float *>(base + k * P::kRowA) + lane * V;
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            if (k < d) {
-                float out[V];
+            for (int v = 0; v < V; ++v) av[v] = pa[v];
+            if (!first) load_v<V, M>(reinterpret_cast<const M *>(base + D * P::kRowA + k * P::kRowR) + lane * V, rv);
+        };
+        check_node<D, V, M>(qd[0], first, load, r + (size_t)qb[0] * Fp + f0, Fp, a, unsat);
+        __syncwarp();
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    float m = phi_hat(pre[v] + suf[k][v], a.l_max, a.phi_lmax);
-                    uint32_t others = par[v] ^ ((ones[v] >> k) & 1u);
-                    out[v] = others ? m : -m;
-                    pre[v] += mag[k][v];
-                }
-                store_v<V, M>(r + (size_t)(b + k) * Fp + f0, out);
-            }
+        for (int s = 0; s < S - 1; ++s) {
+            qb[s] = qb[s + 1];
+            qd[s] = qd[s + 1];
         }
     }
+    cp_async_wait<0>();
     if (a.syndrome) {
         bool bits[V];
 #pragma unroll
@@ -516,8 +871,8 @@ __global__ void k_export_r(PassArgs a, float *__restrict__ r_out) {
 // Launchers
 // ---------------------------------------------------------------------------
 
-inline dim3 pass_grid(const PassArgs &a, int64_t nodes) {
-    int groups = a.Fp / (32 * a.V);
+inline dim3 pass_grid(const PassArgs &a, int64_t nodes, int V) {
+    int groups = a.Fp / (32 * V);
     int64_t want = (nodes + (kThreads / 32) - 1) / (kThreads / 32);
     int64_t cap = a.grid_ctas / groups;
     if (cap < 1) cap = 1;
@@ -529,7 +884,7 @@ inline dim3 pass_grid(const PassArgs &a, int64_t nodes) {
 template <int V, typename M>
 static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t *checks, int32_t count,
                                       cudaStream_t s) {
-    dim3 grid = pass_grid(a, count);
+    dim3 grid = pass_grid(a, count, V);
     switch (bin) {
     case 0: k_check_reg<4, V, M><<<grid, kThreads, 0, s>>>(a, checks, count); break;
     case 1: k_check_reg<8, V, M><<<grid, kThreads, 0, s>>>(a, checks, count); break;
@@ -540,20 +895,57 @@ static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t 
     return cudaGetLastError();
 }
 
+// Pipelined kernel: dynamic shared memory above 48 KB needs an opt-in, and
+// the grid is sized to the CTAs that fit on the GPU at once.
+template <int D, int V, typename M, int S>
+static cudaError_t launch_pipe(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
+    static int resident_by_device[64] = {0};  // CTAs per SM, once per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &resident = resident_by_device[dev & 63];
+    const size_t smem = (size_t)(kThreads / 32) * S * PipeShape<D, V, M>::kStage;
+    if (resident == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_check_pipe<D, V, M, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_pipe<D, V, M, S>, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        resident = nb > 0 ? nb : 1;
+    }
+    PassArgs b = a;
+    b.grid_ctas = a.sm_count * resident;
+    dim3 grid = pass_grid(b, count, V);
+    k_check_pipe<D, V, M, S><<<grid, kThreads, smem, s>>>(a, desc, count);
+    return cudaGetLastError();
+}
+
 template <typename M>
-cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, int32_t count, cudaStream_t s) {
+cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, const int2 *desc, int32_t count,
+                             cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    // The degree-32 bin keeps 32 messages per frame in registers: one frame
-    // per lane there, to stay clear of spills.
-    if (a.V == 4 && bin < 3) return launch_check_bin_v<4, M>(a, bin, checks, count, s);
+    if (a.check_schedule != 1 && bin <= 2 && a.Fp % 64 == 0) {
+        switch (bin) {
+        case 0: return launch_pipe<4, 2, M, 4>(a, desc, count, s);
+        case 1: return launch_pipe<8, 2, M, 3>(a, desc, count, s);
+        default: return launch_pipe<16, 2, M, 2>(a, desc, count, s);
+        }
+    }
+    // Wider bins keep more messages per frame in registers: fewer frames per
+    // lane there, to stay clear of spills (bins 2-4 run two frames per lane
+    // at most, bin 3 and the unbounded bin one when V is odd).
+    if (a.V == 4 && bin < 2) return launch_check_bin_v<4, M>(a, bin, checks, count, s);
+    if (a.V >= 2 && bin != 3) return launch_check_bin_v<2, M>(a, bin, checks, count, s);
     return launch_check_bin_v<1, M>(a, bin, checks, count, s);
 }
 
 template <typename M>
 cudaError_t launch_bit(const PassArgs &a, cudaStream_t s) {
-    dim3 grid = pass_grid(a, a.n);
+    dim3 grid = pass_grid(a, a.n, a.V);
     if (a.V == 4)
         k_bit<4, M><<<grid, kThreads, 0, s>>>(a);
+    else if (a.V == 2)
+        k_bit<2, M><<<grid, kThreads, 0, s>>>(a);
     else
         k_bit<1, M><<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();
@@ -571,7 +963,8 @@ cudaError_t launch_export_r(const PassArgs &a, float *r_out, cudaStream_t s) {
 
 #define LDPC_INSTANTIATE_PASS_KERNELS(M)                                                                       \
     namespace ldpc {                                                                                           \
-    template cudaError_t launch_check_bin<M>(const PassArgs &, int, const int32_t *, int32_t, cudaStream_t);  \
+    template cudaError_t launch_check_bin<M>(const PassArgs &, int, const int32_t *, const int2 *, int32_t,    \
+                                             cudaStream_t);                                                    \
     template cudaError_t launch_bit<M>(const PassArgs &, cudaStream_t);                                        \
     template cudaError_t launch_export_r<M>(const PassArgs &, float *, cudaStream_t);                          \
     }

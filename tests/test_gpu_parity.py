@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_1609_01567_gb300 import inputs as I
-from tests.parity import ATOL, RTOL, close, compare_decodes
+from tests.parity import ATOL, RTOL, close, compare_decodes, near_zero_frames
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -125,18 +125,29 @@ def n1008():
 
 
 def test_n1008_full_decode_matches_oracle(ldpc, oracle_mod, n1008):
+    """The n = 1008 workload end to end: decisions, iteration counts and
+    syndrome flags of every frame equal the oracle's (frames with a posterior
+    within tolerance of 0 are logged instead), and posteriors match within
+    the stated tolerance on frames that stop within 20 iterations. Longer
+    trajectories accumulate FP32 rounding over many passes; they are checked
+    pass by pass in test_lock_step_every_pass_n1008."""
     code, cw, llr = n1008
     h = ldpc.code_from_inputs(code)
     got = gpu_decode(ldpc, h, llr, 50)
     ref = oracle_mod.decode(code, llr.astype(np.float64), 50, n_threads=8)
-    bad, exempt = compare_decodes(got, ref)
-    conv = ref["ok"] == 1
-    # every converged frame matches; frames that never converge are chaotic
-    # and are checked one pass at a time in the lock-step test
-    bad_conv = [f for f in bad if conv[f]]
-    assert not bad_conv, f"converged frames off the oracle: {bad_conv[:10]} (exempt near-zero: {exempt.size})"
-    assert np.array_equal(got["ok"], ref["ok"])
-    assert conv.mean() > 0.8
+    same = (got["bits"] == ref["bits"]).all(axis=1) & (got["iters"] == ref["iters"]) & (got["ok"] == ref["ok"])
+    exempt = near_zero_frames(ref["post"])
+    diff = np.flatnonzero(~same & ~exempt)
+    detail = [(int(f), int(got["iters"][f]), int(ref["iters"][f]), int(got["ok"][f]),
+               int((got["bits"][f] != ref["bits"][f]).sum())) for f in diff[:10]]
+    assert diff.size == 0, f"frames off the oracle (f, it_gpu, it_orc, ok_gpu, dbits): {detail}"
+    short = ref["iters"] <= 20
+    post_ok = close(got["post"], ref["post"]).all(axis=1)
+    bad = np.flatnonzero(short & ~post_ok & ~exempt)
+    assert bad.size == 0, [(int(f), float(np.abs(got["post"][f] - ref["post"][f]).max())) for f in bad[:10]]
+    assert (ref["ok"] == 1).mean() > 0.8 and short.mean() > 0.8
+    print(f"n1008: {len(same)} frames, {int(exempt.sum())} exempt (posterior near 0), "
+          f"{int((~short).sum())} longer than 20 iterations")
 
 
 @pytest.mark.parametrize("n_frames", [1, 31, 33, 64, 65, 129, 1000])
@@ -150,19 +161,29 @@ def test_n1008_ragged_batches(ldpc, oracle_mod, n1008, n_frames):
     assert bad.size == 0, bad[:10]
 
 
-def test_lock_step_passes_n1008(ldpc, oracle_mod, n1008):
-    """One pass at a time from the GPU's own messages: every frame, converging
-    or not, follows Algorithm 2's pass within tolerance."""
+def test_lock_step_every_pass_n1008(ldpc, oracle_mod, n1008):
+    """Every pass of every frame (51 passes, 1000 frames), each started from
+    the GPU's own messages of the previous pass, equals the oracle's pass.
+
+    Messages r get atol 1e-4: the GPU forms q = APP - r from its FP32
+    posterior, whose rounding (up to ~1.5e-5 at |APP| ~ 200) reaches every
+    output of a check through a rule that is 1-Lipschitz in each input."""
     code, cw, llr = n1008
     h = ldpc.code_from_inputs(code)
-    sub = llr[:200]
     prev_r = None
-    for t in range(6):
-        got = gpu_decode(ldpc, h, sub, t, early_exit=False, want_r=True)
-        ref = oracle_mod.sp_pass(code, sub.astype(np.float64), prev_r, n_threads=8)
-        assert close(got["post"], ref["post"]).all(), (t, np.abs(got["post"] - ref["post"]).max())
-        assert close(got["r"], ref["r"], atol=1e-4).all(), (t, np.abs(got["r"] - ref["r"]).max())
+    lam = llr.astype(np.float64)
+    worst_post = worst_r = 0.0
+    for t in range(51):
+        got = gpu_decode(ldpc, h, llr, t, early_exit=False, want_r=True)
+        ref = oracle_mod.sp_pass(code, lam, prev_r, n_threads=8)
+        okp = close(got["post"], ref["post"])
+        okr = close(got["r"], ref["r"], atol=1e-4)
+        assert okp.all(), (t, np.argwhere(~okp)[:5].tolist(), float(np.abs(got["post"] - ref["post"]).max()))
+        assert okr.all(), (t, float(np.abs(got["r"] - ref["r"]).max()))
+        worst_post = max(worst_post, float(np.abs(got["post"] - ref["post"]).max()))
+        worst_r = max(worst_r, float(np.abs(got["r"] - ref["r"]).max()))
         prev_r = got["r"].astype(np.float64)
+    print(f"lock-step: worst |dpost| {worst_post:.2e}, worst |dr| {worst_r:.2e}")
 
 
 def test_prefix_property_and_symmetry_on_gpu(ldpc, n1008):
@@ -177,6 +198,18 @@ def test_prefix_property_and_symmetry_on_gpu(ldpc, n1008):
     np.testing.assert_array_equal(flip["iters"], full["iters"])
     np.testing.assert_array_equal(flip["bits"], full["bits"] ^ cw)
     np.testing.assert_array_equal(flip["post"], full["post"] * (1 - 2 * cw.astype(np.float32)))
+
+
+@pytest.mark.parametrize("msg", ["f32", "f16", "bf16"])
+def test_schedules_do_not_change_results(ldpc, n1008, msg):
+    """Frames per lane and the check-kernel schedule are tuning knobs only."""
+    code, cw, llr = n1008
+    h = ldpc.code_from_inputs(code)
+    base = gpu_decode(ldpc, h, llr[:300], 15, frames_per_lane=1, check_schedule=1, msg_dtype=msg)
+    for v, sched in ((2, 1), (4, 1), (2, 2), (4, 2), (0, 0)):
+        other = gpu_decode(ldpc, h, llr[:300], 15, frames_per_lane=v, check_schedule=sched, msg_dtype=msg)
+        for k in ("bits", "iters", "ok", "post"):
+            np.testing.assert_array_equal(other[k], base[k], err_msg=f"V={v} schedule={sched} {k}")
 
 
 def test_host_entry_point_matches_device_entry_point(ldpc, n1008):
