@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the sum-product LDPC decoder on GB300.
+
+Workload: the seeded n = 64800, k = 32400 (rate 1/2) IRA code with info-bit
+degrees {8: 0.2, 3: 0.8} (E = 194,399 edges), a batch of 256 random
+codewords per GPU, BPSK over AWGN at Eb/N0 = 1.0 dB (LLRs from the on-device
+Philox generator), flooding sum-product with max_iter = 10 fixed (11 check
+passes), FP32 messages. One step = one ldpc_decode call on the batch
+(interleave, 11 check + 11 bit passes, final syndrome, results).
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
+on the same workload instead (bounded samples per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+if str(ROOT) not in sys.path:
+    sys.path.insert(0, str(ROOT))
+
+METRIC = "decoded Gbit/s and edge-updates/s at n=64800, 10 iters; HBM roofline %; p50/p99"
+UNIT = "Gbit/s"
+N_BITS, K_BITS = 64800, 32400
+PROFILE_DIR = ROOT / "profiles"
+HOT_SOURCES = ("ldpc_pass_kernels.cuh", "ldpc_decode.cu", "ldpc_internal.h")
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--frames", type=int, default=256, help="frames per GPU per step")
+    p.add_argument("--max-iter", type=int, default=10)
+    p.add_argument("--ebn0", type=float, default=1.0)
+    p.add_argument("--msg", choices=("f32", "f16", "bf16"), default="f32")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=50)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(args, world):
+    return {
+        "workload": (f"IRA LDPC n={N_BITS} k={K_BITS} (rate 1/2, info degrees 8:0.2/3:0.8, E=194399), "
+                     f"{args.frames} frames/GPU, BPSK/AWGN Eb/N0={args.ebn0} dB, sum-product flooding, "
+                     f"max_iter={args.max_iter} fixed ({args.max_iter + 1} check passes), {args.msg} messages"),
+        "n": N_BITS, "k": K_BITS, "edges": 194399, "frames_per_gpu": args.frames, "global_frames": args.frames * world,
+        "max_iter": args.max_iter, "early_exit": False, "ebn0_db": args.ebn0, "msg_dtype": args.msg,
+        "l_max": 20.0, "llr": "on-device Philox-4x64-10 BPSK/AWGN, random codewords",
+        "l2": "decode working set (messages + posteriors + LLRs) >= 331 MB > 129 MB L2; "
+              "input LLRs rotated over 4 buffers",
+    }
+
+
+def measured_hbm_peak():
+    path = ROOT / "MEASURED_PEAKS.json"
+    try:
+        data = json.loads(path.read_text())
+        return float(data["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s recipe figure)"
+
+
+def hot_source_hash():
+    h = hashlib.sha256()
+    for name in HOT_SOURCES:
+        h.update((ROOT / "paper_1609_01567_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(msg):
+    """DRAM bytes per check launch from the committed ncu summary, if it was
+    taken on the current kernel sources."""
+    path = PROFILE_DIR / f"check_kernel_n64800_f256_{msg}.md"
+    if not path.exists():
+        return None, None
+    fields = {}
+    for line in path.read_text().splitlines():
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("source_hash") != hot_source_hash():
+        return None, f"{path.name} (stale: kernel changed since the capture)"
+    try:
+        return float(fields["dram_bytes_per_launch"]), path.name
+    except (KeyError, ValueError):
+        return None, None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(code, info_cw, args, budget_s, max_frames):
+    """Time the FP64 oracle on a bounded sample of the workload's frames."""
+    from oracle import oracle
+    from paper_1609_01567_gb300 import inputs
+
+    cores = os.cpu_count() or 1
+    sigma2 = inputs.sigma2_from_ebn0(args.ebn0, code.rate)
+    lam1 = oracle.gen_awgn(11, 0, 1, code.n, sigma2, info_cw[:1])
+    t0 = time.perf_counter()
+    oracle.decode(code, lam1, args.max_iter, early_exit=False, want_post=False, n_threads=1)
+    t_frame = time.perf_counter() - t0
+    frames = max(1, min(max_frames, int(budget_s / max(t_frame, 1e-6))))
+    frames = max(min(cores, max_frames), (frames // cores) * cores) if frames >= cores else frames
+    threads = min(cores, frames)
+    lam = oracle.gen_awgn(11, 0, frames, code.n, sigma2, info_cw[:frames])
+    t0 = time.perf_counter()
+    oracle.decode(code, lam, args.max_iter, early_exit=False, want_post=False, n_threads=threads)
+    wall = time.perf_counter() - t0
+    return frames, threads, wall, t_frame
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1609_01567_gb300 import inputs
+
+    code = inputs.large_code_n64800()
+    cw = inputs.encode_ira(code, inputs.random_info(min(args.frames, 256), code.k, seed=1000))
+    cores = os.cpu_count() or 1
+    # per step: one frame per host core (the oracle runs frames in parallel)
+    frames_per_step = min(cores, cw.shape[0])
+    from oracle import oracle
+    sigma2 = inputs.sigma2_from_ebn0(args.ebn0, code.rate)
+    lam = oracle.gen_awgn(11, 0, frames_per_step, code.n, sigma2, cw[:frames_per_step])
+    for _ in range(args.warmup):
+        oracle.decode(code, lam, args.max_iter, early_exit=False, want_post=False, n_threads=frames_per_step)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.decode(code, lam, args.max_iter, early_exit=False, want_post=False, n_threads=frames_per_step)
+        times.append(time.perf_counter() - t0)
+    step_s = sum(times) / len(times)
+    value = frames_per_step * K_BITS / step_s / 1e9
+    sample = (f"{frames_per_step} frames of the {args.frames}-frame batch per step, FP64 oracle, "
+              f"max_iter={args.max_iter} fixed, {frames_per_step} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": frames_per_step, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "p50_ms": statistics.median(times) * 1e3,
+        "p99_ms": sorted(times)[min(len(times) - 1, int(math.ceil(0.99 * len(times))) - 1)] * 1e3,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    else:
+        dist = None
+
+    from paper_1609_01567_gb300 import build, inputs, ldpc
+
+    build.build()
+    code = inputs.large_code_n64800()
+    h = ldpc.code_from_inputs(code, device=local)
+    F = args.frames
+    info = inputs.random_info(F, code.k, seed=1000 + rank)
+    cw_host = inputs.encode_ira(code, info)
+    cw = torch.from_numpy(cw_host).to(dev)
+    sigma2 = inputs.sigma2_from_ebn0(args.ebn0, code.rate)
+    n_buf = 4
+    llrs = [ldpc.ldpc_gen_awgn(17 + b, rank * F, F, code.n, sigma2, cw, device=local) for b in range(n_buf)]
+    out = None
+    kw = dict(early_exit=False, msg_dtype=args.msg)
+    for i in range(args.warmup):
+        out = ldpc.ldpc_decode(h, llrs[i % n_buf], args.max_iter, out=out, **kw)
+    torch.cuda.synchronize()
+    ldpc.ldpc_prof_read(h, reset=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    stream = torch.cuda.current_stream()
+    events[0].record(stream)
+    for i in range(args.steps):
+        out = ldpc.ldpc_decode(h, llrs[i % n_buf], args.max_iter, out=out, profile=True, **kw)
+        events[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = events[0].elapsed_time(events[-1])
+    step_ms = [events[i].elapsed_time(events[i + 1]) for i in range(args.steps)]
+    prof = ldpc.ldpc_prof_read(h, reset=True)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    passes = args.max_iter + 1
+    E = code.n_edges
+    value = world * F * K_BITS / (ms_per_step * 1e-3) / 1e9
+    # decode quality of the last step (same noise realisation as buffer (steps-1) % 4)
+    last = (args.steps - 1) % n_buf
+    ref_bits = ldpc.ldpc_decode(h, llrs[last], args.max_iter, **kw)
+    bit_err = int((ref_bits["bits"] != cw).sum().item())
+    frame_err = int((ref_bits["bits"] != cw).any(dim=1).sum().item())
+
+    # roofline of the dominant kernel (check-node pass)
+    s = 4 if args.msg == "f32" else 2
+    n = code.n
+    check_bytes = ((passes - 1) * (2 * s * E + 4 * n) + (s * E + 4 * n)) * F / passes
+    bit_bytes = (s * E + 8 * n) * F
+    kern = {k: v for k, v in prof.items() if isinstance(v, dict) and v["launches"]}
+    check_ms = kern["check"]["total_ms"] / kern["check"]["launches"]
+    bit_ms = kern["bit"]["total_ms"] / kern["bit"]["launches"]
+    peak, peak_src = measured_hbm_peak()
+    achieved = check_bytes / (check_ms * 1e-3) / 1e9
+    traffic, traffic_src = recorded_traffic(args.msg)
+    step_kernel_ms = sum(v["total_ms"] for v in kern.values()) / args.steps
+    shares = {k: v["total_ms"] / args.steps / step_kernel_ms for k, v in kern.items()}
+    model_bytes_step = passes * (3 * s * E + 12.125 * n) * F
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.msg, "data": "synthetic", "config": workload_config(args, world),
+        "edge_updates_per_s": world * E * passes * F / (ms_per_step * 1e-3),
+        "coded_gbps": world * F * N_BITS / (ms_per_step * 1e-3) / 1e9,
+        "p50_ms": statistics.median(step_ms), "p99_ms": sorted(step_ms)[min(len(step_ms) - 1,
+                                                                           int(math.ceil(0.99 * len(step_ms))) - 1)],
+        "model_bytes_per_step": model_bytes_step,
+        "model_hbm_frac": model_bytes_step / (ms_per_step * 1e-3) / 1e9 / peak,
+        "roofline": {"bound": "hbm", "kernel": "check-node pass", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "traffic_source": traffic_src, "algorithmic_bytes_per_launch": check_bytes,
+                     "avg_launch_ms": check_ms},
+        "kernel_ms": {k: v["total_ms"] / v["launches"] for k, v in kern.items()},
+        "kernel_share": shares,
+        "bit_kernel": {"achieved_gbs": bit_bytes / (bit_ms * 1e-3) / 1e9, "avg_launch_ms": bit_ms},
+        "gpu_launches": prof["kernels"],
+        "clocks": clk,
+        "quality": {"frames": F, "frame_errors": frame_err, "bit_errors": bit_err, "ebn0_db": args.ebn0},
+    }
+
+    # end to end through the host entry point (pinned buffers, copies inside)
+    llr_host = [llrs[b].cpu().pin_memory() for b in range(n_buf)]
+    host_out = {"bits": torch.empty((F, n), dtype=torch.uint8, pin_memory=True),
+                "iters": torch.empty((F,), dtype=torch.int32, pin_memory=True),
+                "ok": torch.empty((F,), dtype=torch.uint8, pin_memory=True)}
+    for i in range(3):
+        ldpc.ldpc_decode_host(h, llr_host[i % n_buf], args.max_iter, out=host_out, **kw)
+    if dist:
+        dist.barrier()
+    k_e2e = max(1, min(args.e2e_steps, args.steps))
+    t0 = time.perf_counter()
+    for i in range(k_e2e):
+        ldpc.ldpc_decode_host(h, llr_host[i % n_buf], args.max_iter, out=host_out, **kw)
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    line["e2e"] = {"value": world * F * K_BITS / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": F * n * 4,
+                   "d2h_bytes_per_step": F * n + 4 * F + F, "steps": k_e2e, "ms_per_step": e2e_s * 1e3,
+                   "entry_point": "ldpc_decode_host"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        frames, threads, wall, t_frame = oracle_sample(code, cw_host, args, args.cpu_seconds, F)
+        cpu_value = frames * K_BITS / wall / 1e9
+        line["cpu_baseline"] = {
+            "value": cpu_value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{frames} of the {F} frames, FP64 oracle, max_iter={args.max_iter} fixed, "
+                      f"{threads} threads, {wall:.1f} s wall ({t_frame:.2f} s per frame on one core)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

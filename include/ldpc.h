@@ -206,11 +206,14 @@ enum {
 typedef struct {
     int64_t launches[LDPC_K_COUNT];
     double total_ms[LDPC_K_COUNT]; /* sum of CUDA-event durations */
+    int64_t kernels;               /* library kernels enqueued by this code,
+                                      profiled or not                      */
 } ldpc_prof_t;
 
 /* Collect the timings of profiled launches of `code` made since the last
- * reset (synchronizes on their events), adding them into *out; reset != 0
- * clears the record afterwards. */
+ * reset (synchronizes on their events) and the count of all library kernels
+ * enqueued for the code since then, adding them into *out (zero it first);
+ * reset != 0 clears the record afterwards. */
 int ldpc_prof_read(ldpc_code_t *code, ldpc_prof_t *out, int32_t reset);
 
 /* Text of the calling thread's last error ("" if none). */

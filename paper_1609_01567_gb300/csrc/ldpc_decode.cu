@@ -130,10 +130,11 @@ struct DeviceGuard {
 static int msg_size(int dtype) { return dtype == LDPC_MSG_F32 ? 4 : 2; }
 
 // Frames per lane V and padded frame count Fp (a multiple of 32 V).
-// `want` = 0 picks: one frame per lane for tiny batches, else two.
+// `want` = 0 picks by batch size: four frames per lane (the widest rows,
+// best for the bandwidth-bound bit kernel) once the padding stays small.
 static void frames_layout(int32_t F, int32_t want, int32_t *V, int32_t *Fp) {
     int32_t v = want;
-    if (v != 1 && v != 2 && v != 4) v = F > 32 ? 2 : 1;
+    if (v != 1 && v != 2 && v != 4) v = F > 64 ? 4 : (F > 32 ? 2 : 1);
     *V = v;
     *Fp = (F + 32 * v - 1) / (32 * v) * (32 * v);
 }
@@ -197,7 +198,8 @@ struct Launcher {
     cudaStream_t s;
     bool profile;
     template <typename F>
-    cudaError_t operator()(int kind, F &&fn) {
+    cudaError_t operator()(int kind, int n_kernels, F &&fn) {
+        c->kernels_launched += n_kernels;
         cudaEvent_t a = nullptr, b = nullptr;
         if (profile) {
             a = take_event(c);
@@ -249,7 +251,7 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
     Launcher L{c, s, o.profile != 0};
     cudaError_t e;
     const int words = Fp / 32;
-    e = L(LDPC_K_OTHER, [&] {
+    e = L(LDPC_K_OTHER, 1, [&] {
         cudaError_t ee = cudaMemsetAsync(w.unsat, 0, sizeof(uint32_t) * (size_t)(max_iter + 1) * words, s);
         if (ee != cudaSuccess) return ee;
         k_init_done<<<(words + 127) / 128, 128, 0, s>>>(w.done, F, Fp);
@@ -257,7 +259,7 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
     });
     if (e != cudaSuccess) return e;
     if (c->n > 0) {
-        e = L(LDPC_K_INTERLEAVE, [&] {
+        e = L(LDPC_K_INTERLEAVE, 1, [&] {
             dim3 grid((unsigned)((c->n + 31) / 32), (unsigned)(Fp / 32), 1);
             k_interleave<<<grid, dim3(32, 8, 1), 0, s>>>(llr, w.lamT, c->n, F, Fp);
             return cudaGetLastError();
@@ -270,20 +272,20 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
         for (int b = 0; b < kNumCheckBins; ++b) {
             int32_t count = c->bin_off[b + 1] - c->bin_off[b];
             if (count == 0) continue;
-            e = L(LDPC_K_CHECK, [&] {
+            e = L(LDPC_K_CHECK, 1, [&] {
                 return launch_check_bin<M>(a, b, c->d.bin_checks + c->bin_off[b], c->d.bin_desc + c->bin_off[b], count,
                                            s);
             });
             if (e != cudaSuccess) return e;
         }
         if (c->n > 0) {
-            e = L(LDPC_K_BIT, [&] { return launch_bit<M>(a, s); });
+            e = L(LDPC_K_BIT, 1, [&] { return launch_bit<M>(a, s); });
             if (e != cudaSuccess) return e;
         }
     }
     uint32_t *final_row = w.unsat + (size_t)max_iter * words;
     if (c->m > 0 && c->E > 0) {
-        e = L(LDPC_K_SYNDROME, [&] {
+        e = L(LDPC_K_SYNDROME, 1, [&] {
             dim3 grid = pass_grid(a, c->m, V);
             if (V == 4)
                 k_syndrome<4><<<grid, kThreads, 0, s>>>(a, final_row);
@@ -295,7 +297,7 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
         });
         if (e != cudaSuccess) return e;
     }
-    e = L(LDPC_K_FINALIZE, [&] {
+    e = L(LDPC_K_FINALIZE, c->n > 0 ? 2 : 1, [&] {
         if (c->n > 0) {
             dim3 grid((unsigned)((c->n + 31) / 32), (unsigned)((F + 31) / 32), 1);
             k_finalize<<<grid, dim3(32, 8, 1), 0, s>>>(w.app, bits, post, c->n, F, Fp);
@@ -305,7 +307,7 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
     });
     if (e != cudaSuccess) return e;
     if (r_out) {
-        e = L(LDPC_K_OTHER, [&] { return launch_export_r<M>(a, r_out, s); });
+        e = L(LDPC_K_OTHER, 1, [&] { return launch_export_r<M>(a, r_out, s); });
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -450,7 +452,9 @@ extern "C" int ldpc_prof_read(ldpc_code_t *c, ldpc_prof_t *out, int32_t reset) {
             out->total_ms[p.kind] += ms;
         }
     }
+    out->kernels += c->kernels_launched;
     if (reset) {
+        c->kernels_launched = 0;
         for (auto &p : c->prof) {
             c->event_pool.push_back(p.start);
             c->event_pool.push_back(p.stop);

@@ -133,4 +133,5 @@ struct ldpc_code {
     std::mutex mu;
     std::vector<ldpc::ProfRecord> prof;
     std::vector<cudaEvent_t> event_pool;
+    int64_t kernels_launched = 0;  // library kernels enqueued since the last profile reset
 };

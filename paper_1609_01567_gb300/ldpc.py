@@ -44,7 +44,7 @@ class ldpc_decode_opts_t(ctypes.Structure):
 
 
 class ldpc_prof_t(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 6), ("total_ms", ctypes.c_double * 6)]
+    _fields_ = [("launches", ctypes.c_int64 * 6), ("total_ms", ctypes.c_double * 6), ("kernels", ctypes.c_int64)]
 
 
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
@@ -272,10 +272,13 @@ def ldpc_philox4x64_10(key0: int, key1: int, ctr0: int, ctr1: int, count: int, d
 
 
 def ldpc_prof_read(code: Code, reset: bool = True) -> dict:
-    """Per kernel class: launches and total CUDA-event milliseconds."""
+    """Per kernel class: profiled launches and total CUDA-event milliseconds;
+    ``kernels``: all library kernels enqueued for the code since the last reset."""
     p = ldpc_prof_t()
     _check(library().ldpc_prof_read(code.handle, ctypes.byref(p), 1 if reset else 0))
-    return {k: {"launches": int(p.launches[i]), "total_ms": float(p.total_ms[i])} for i, k in enumerate(KERNEL_CLASSES)}
+    out = {k: {"launches": int(p.launches[i]), "total_ms": float(p.total_ms[i])} for i, k in enumerate(KERNEL_CLASSES)}
+    out["kernels"] = int(p.kernels)
+    return out
 
 
 def code_from_inputs(code, device: int = 0) -> Code:
