@@ -171,6 +171,35 @@ int ldpc_decode_host(ldpc_code_t *code, const float *llr_host, int32_t n_frames,
                      uint8_t *syndrome_ok_host, float *post_llr_host, void *stream);
 
 /*
+ * ldpc_decode for callers that cannot allocate device memory when they
+ * decode: a latency-bound receive chain that must not stall on cudaMalloc
+ * (which may synchronise the device), or a plug-in confined to another
+ * framework's memory pool or to a device-memory cap. The code handle is made
+ * beforehand with ldpc_code_create (that call does allocate: it uploads the
+ * tables); this entry point then allocates nothing. The paper has no
+ * counterpart: it is a deployment aid, not part of the method.
+ *
+ * Arguments, layouts, results and errors are those of ldpc_decode, except:
+ *   - its scratch (messages, posteriors, interleaved LLRs, flags) lives in one
+ *     64 MiB device array of the library, reserved on every GPU that loads the
+ *     library until the process exits. A call whose scratch does not fit
+ *     (roughly (4 E + 8 n) bytes per frame rounded up to 32 to 128 frames, for
+ *     FP32 messages) is rejected with LDPC_EINVAL and a message giving both
+ *     sizes; decode fewer frames per call;
+ *   - every call on a device shares that array and it keeps the last call's
+ *     contents (each call clears what it needs cleared). Calls that overlap on
+ *     the GPU -- on different streams, with the same or different codes --
+ *     race on it: the caller must serialise them;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - opts->profile must be 0 (timing events are not available here).
+ */
+int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int32_t n_frames, int32_t max_iter,
+                       const ldpc_decode_opts_t *opts, uint8_t *bits, int32_t *iters, uint8_t *syndrome_ok,
+                       float *post_llr, void *stream);
+
+/*
  * Channel LLRs of BPSK over AWGN (the BER simulator of Section IV, Eqs. 3-4)
  * into device llr [n_frames][n] float.
  * Frame f has global index frame_offset + f. Bit j of a frame uses Philox-4x64

@@ -48,7 +48,7 @@ class ldpc_prof_t(ctypes.Structure):
 
 
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
-           "ldpc_decode_host", "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
+           "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
            "ldpc_version")
 
 _LIB = None
@@ -72,12 +72,15 @@ def library():
             lib.ldpc_code_tables.argtypes = [vp] + [vp] * 11
             lib.ldpc_decode.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ldpc_decode_opts_t), vp, vp, vp, vp, vp]
             lib.ldpc_decode_host.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ldpc_decode_opts_t), vp, vp, vp, vp, vp]
+            lib.ldpc_decode_static.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ldpc_decode_opts_t), vp, vp, vp, vp,
+                                               vp]
             lib.ldpc_gen_awgn.argtypes = [u64, i64, i32, i32, ctypes.c_float, vp, vp, vp]
             lib.ldpc_philox4x64_10.argtypes = [u64, u64, u64, u64, i64, vp, vp]
             lib.ldpc_prof_read.argtypes = [vp, ctypes.POINTER(ldpc_prof_t), i32]
             lib.ldpc_last_error.restype = ctypes.c_char_p
             lib.ldpc_version.restype = ctypes.c_char_p
             for name in ("ldpc_code_create", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode", "ldpc_decode_host",
+                         "ldpc_decode_static",
                          "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read"):
                 getattr(lib, name).restype = ctypes.c_int
             _LIB = lib
@@ -245,6 +248,36 @@ def ldpc_decode_host(code: Code, llr: np.ndarray, max_iter: int, *, early_exit: 
     _check(library().ldpc_decode_host(code.handle, llr_ptr, f, max_iter, ctypes.byref(opts), ptr(o["bits"]),
                                       ptr(o["iters"]), ptr(o["ok"]), ptr(o["post"]) if want_post else None,
                                       _stream_handle(stream)))
+    return o
+
+
+def ldpc_decode_static(code: Code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
+                       msg_dtype: str = "f32", want_post: bool = True, out: dict | None = None, stream=None,
+                       frames_per_lane: int = 0, check_schedule: int = 0) -> dict:
+    """ldpc_decode for callers that may not allocate device memory while they
+    decode: the library's scratch is a fixed 64 MiB device array (see
+    include/ldpc.h). Output tensors are allocated here unless passed in
+    ``out``; pass them in to keep the whole call allocation-free."""
+    import torch
+    f = int(llr.shape[0]) if llr.dim() == 2 else -1
+    dev = torch.device("cuda", code.device)
+    o = dict(out or {})
+    if "bits" not in o:
+        o["bits"] = torch.empty((f, code.n), dtype=torch.uint8, device=dev)
+    if "iters" not in o:
+        o["iters"] = torch.empty((f,), dtype=torch.int32, device=dev)
+    if "ok" not in o:
+        o["ok"] = torch.empty((f,), dtype=torch.uint8, device=dev)
+    if want_post and "post" not in o:
+        o["post"] = torch.empty((f, code.n), dtype=torch.float32, device=dev)
+    opts = _opts(early_exit, l_max, msg_dtype, False, None, frames_per_lane, check_schedule)
+    _check(library().ldpc_decode_static(
+        code.handle, _dev_ptr(llr, torch.float32, (f, code.n), "llr", code.device), f, max_iter, ctypes.byref(opts),
+        _dev_ptr(o["bits"], torch.uint8, (f, code.n), "bits", code.device),
+        _dev_ptr(o["iters"], torch.int32, (f,), "iters", code.device),
+        _dev_ptr(o["ok"], torch.uint8, (f,), "ok", code.device),
+        _dev_ptr(o.get("post"), torch.float32, (f, code.n), "post", code.device) if want_post else None,
+        _stream_handle(stream)))
     return o
 
 
