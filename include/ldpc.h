@@ -130,12 +130,18 @@ typedef struct {
                            check-to-bit messages in edge order (for checking
                            one iteration at a time); NULL to skip            */
     int32_t frames_per_lane; /* tuning: frames each GPU lane carries in the
-                           bit-node kernel (1, 2 or 4); 0 picks by batch size */
+                           bit-node kernel (1, 2, 4 or 8); 0 picks by batch
+                           size                                              */
     int32_t check_schedule;  /* tuning: check-node kernel schedule; 0 = auto,
                            1 = inputs loaded straight from global memory,
                            2 = rows staged through a shared-memory pipeline
-                           (when the batch allows). Results do not depend on
-                           either tuning field                               */
+                           (when the batch allows)                           */
+    int32_t streams;    /* tuning: 1 = all passes on `stream`; 2 = the two
+                           halves of the batch on two library streams, half a
+                           pass apart, so that the check pass of one half
+                           overlaps the bit pass of the other; 0 = 2 when the
+                           batch splits evenly. Results do not depend on any
+                           tuning field                                      */
 } ldpc_decode_opts_t;
 
 /*
@@ -229,7 +235,9 @@ enum {
     LDPC_K_SYNDROME = 3,   /* final syndrome pass                               */
     LDPC_K_FINALIZE = 4,   /* hard decisions, posteriors, iteration counts      */
     LDPC_K_OTHER = 5,      /* flag set-up, message export                       */
-    LDPC_K_COUNT = 6
+    LDPC_K_PASSES = 6,     /* the whole pass region (all check and bit passes,
+                              on one or two streams), timed on `stream`       */
+    LDPC_K_COUNT = 7
 };
 
 typedef struct {

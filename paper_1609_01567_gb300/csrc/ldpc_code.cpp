@@ -61,6 +61,12 @@ static void free_device_tables(ldpc_code *c) {
     cudaFree(w.h_ok);
     cudaFree(w.h_post);
     if (w.last_use) cudaEventDestroy(w.last_use);
+    for (int h = 0; h < 2; ++h) {
+        if (w.half_stream[h]) cudaStreamDestroy(w.half_stream[h]);
+        if (w.join[h]) cudaEventDestroy(w.join[h]);
+    }
+    if (w.fork) cudaEventDestroy(w.fork);
+    if (w.phase) cudaEventDestroy(w.phase);
     for (auto &p : c->prof) {
         cudaEventDestroy(p.start);
         cudaEventDestroy(p.stop);

@@ -134,7 +134,7 @@ static int msg_size(int dtype) { return dtype == LDPC_MSG_F32 ? 4 : 2; }
 // best for the bandwidth-bound bit kernel) once the padding stays small.
 static void frames_layout(int32_t F, int32_t want, int32_t *V, int32_t *Fp) {
     int32_t v = want;
-    if (v != 1 && v != 2 && v != 4) v = F > 64 ? 4 : (F > 32 ? 2 : 1);
+    if (v != 1 && v != 2 && v != 4 && v != 8) v = F > 64 ? 4 : (F > 32 ? 2 : 1);
     *V = v;
     *Fp = (F + 32 * v - 1) / (32 * v) * (32 * v);
 }
@@ -189,6 +189,19 @@ static cudaEvent_t take_event(ldpc_code *c) {
     }
     cudaEvent_t e = nullptr;
     cudaEventCreate(&e);
+    return e;
+}
+
+// The two library streams (non-blocking) and their fork/phase/join events.
+static cudaError_t ensure_half_streams(ldpc_code *c) {
+    Workspace &w = c->ws;
+    cudaError_t e = cudaSuccess;
+    for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
+        if (!w.half_stream[h]) e = cudaStreamCreateWithFlags(&w.half_stream[h], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !w.join[h]) e = cudaEventCreateWithFlags(&w.join[h], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && !w.fork) e = cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !w.phase) e = cudaEventCreateWithFlags(&w.phase, cudaEventDisableTiming);
     return e;
 }
 
@@ -247,6 +260,8 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
     a.grid_ctas = std::max(1, c->sm_count) * 4;
     a.sm_count = std::max(1, c->sm_count);
     a.check_schedule = o.check_schedule;
+    a.f_begin = 0;
+    a.f_count = Fp;
 
     Launcher L{c, s, o.profile != 0};
     cudaError_t e;
@@ -266,28 +281,72 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
         });
         if (e != cudaSuccess) return e;
     }
+    // The passes: on `s`, or split over the two library streams, each running
+    // one half of the frame range, the second starting when the first has
+    // finished its first check pass, so the (arithmetic-bound) check pass of
+    // one half overlaps the (bandwidth-bound) bit pass of the other.
+    cudaEvent_t region_start = nullptr;
+    if (o.profile) {
+        region_start = take_event(c);
+        cudaEventRecord(region_start, s);
+    }
+    const int32_t vmax = std::max(V, 2);
+    const bool split = o.streams != 1 && Fp % (64 * vmax) == 0 && (o.streams == 2 || Fp >= 256);
+    int nh = 1;
+    PassArgs half[2] = {a, a};
+    cudaStream_t hs[2] = {s, s};
+    if (split) {
+        if ((e = ensure_half_streams(c)) != cudaSuccess) return e;
+        nh = 2;
+        half[0].f_count = half[1].f_count = Fp / 2;
+        half[1].f_begin = Fp / 2;
+        hs[0] = w.half_stream[0];
+        hs[1] = w.half_stream[1];
+        if ((e = cudaEventRecord(w.fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(hs[0], w.fork, 0)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(hs[1], w.fork, 0)) != cudaSuccess) return e;
+    }
     for (int32_t t = 0; t <= max_iter; ++t) {
-        a.pass = t;
-        a.syndrome = (t > 0 && a.early_exit) ? 1 : 0;
-        for (int b = 0; b < kNumCheckBins; ++b) {
-            int32_t count = c->bin_off[b + 1] - c->bin_off[b];
-            if (count == 0) continue;
-            e = L(LDPC_K_CHECK, 1, [&] {
-                return launch_check_bin<M>(a, b, c->d.bin_checks + c->bin_off[b], c->d.bin_desc + c->bin_off[b], count,
-                                           s);
-            });
-            if (e != cudaSuccess) return e;
+        for (int h = 0; h < nh; ++h) {
+            PassArgs &ah = half[h];
+            Launcher Lh{c, hs[h], o.profile != 0};
+            ah.pass = t;
+            ah.syndrome = (t > 0 && ah.early_exit) ? 1 : 0;
+            for (int b = 0; b < kNumCheckBins; ++b) {
+                int32_t count = c->bin_off[b + 1] - c->bin_off[b];
+                if (count == 0) continue;
+                e = Lh(LDPC_K_CHECK, 1, [&] {
+                    return launch_check_bin<M>(ah, b, c->d.bin_checks + c->bin_off[b], c->d.bin_desc + c->bin_off[b],
+                                               count, hs[h]);
+                });
+                if (e != cudaSuccess) return e;
+            }
+            if (split && t == 0 && h == 0) {
+                if ((e = cudaEventRecord(w.phase, hs[0])) != cudaSuccess) return e;
+                if ((e = cudaStreamWaitEvent(hs[1], w.phase, 0)) != cudaSuccess) return e;
+            }
+            if (c->n > 0) {
+                e = Lh(LDPC_K_BIT, 1, [&] { return launch_bit<M>(ah, hs[h]); });
+                if (e != cudaSuccess) return e;
+            }
         }
-        if (c->n > 0) {
-            e = L(LDPC_K_BIT, 1, [&] { return launch_bit<M>(a, s); });
-            if (e != cudaSuccess) return e;
+    }
+    if (split) {
+        for (int h = 0; h < 2; ++h) {
+            if ((e = cudaEventRecord(w.join[h], hs[h])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, w.join[h], 0)) != cudaSuccess) return e;
         }
+    }
+    if (o.profile) {
+        cudaEvent_t region_stop = take_event(c);
+        cudaEventRecord(region_stop, s);
+        c->prof.push_back(ProfRecord{LDPC_K_PASSES, region_start, region_stop});
     }
     uint32_t *final_row = w.unsat + (size_t)max_iter * words;
     if (c->m > 0 && c->E > 0) {
         e = L(LDPC_K_SYNDROME, 1, [&] {
-            dim3 grid = pass_grid(a, c->m, V);
-            if (V == 4)
+            dim3 grid = pass_grid(a, c->m, std::min(V, 4));
+            if (V >= 4)
                 k_syndrome<4><<<grid, kThreads, 0, s>>>(a, final_row);
             else if (V == 2)
                 k_syndrome<2><<<grid, kThreads, 0, s>>>(a, final_row);
@@ -323,8 +382,10 @@ static int check_decode_args(const ldpc_code *c, int32_t F, int32_t max_iter, co
     if (!(l_max <= 80.0f)) return set_error(LDPC_EINVAL, "%s: l_max=%g outside (0, 80]", fn, (double)o.l_max);
     if (o.check_schedule < 0 || o.check_schedule > 2)
         return set_error(LDPC_EINVAL, "%s: check_schedule=%d not in {0, 1, 2}", fn, o.check_schedule);
-    if (o.frames_per_lane != 0 && o.frames_per_lane != 1 && o.frames_per_lane != 2 && o.frames_per_lane != 4)
-        return set_error(LDPC_EINVAL, "%s: frames_per_lane=%d not in {0, 1, 2, 4}", fn, o.frames_per_lane);
+    if (o.frames_per_lane != 0 && o.frames_per_lane != 1 && o.frames_per_lane != 2 && o.frames_per_lane != 4 &&
+        o.frames_per_lane != 8)
+        return set_error(LDPC_EINVAL, "%s: frames_per_lane=%d not in {0, 1, 2, 4, 8}", fn, o.frames_per_lane);
+    if (o.streams < 0 || o.streams > 2) return set_error(LDPC_EINVAL, "%s: streams=%d not in {0, 1, 2}", fn, o.streams);
     if (o.msg_dtype != LDPC_MSG_F32 && o.msg_dtype != LDPC_MSG_F16 && o.msg_dtype != LDPC_MSG_BF16)
         return set_error(LDPC_EINVAL, "%s: unknown msg_dtype %d", fn, o.msg_dtype);
     *l_max_out = l_max;

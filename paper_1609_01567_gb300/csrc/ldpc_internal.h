@@ -69,6 +69,8 @@ struct PassArgs {
     int32_t grid_ctas;   // CTAs per launch target (a multiple of the SM count)
     int32_t sm_count;
     int32_t check_schedule;  // 0 auto, 1 direct loads, 2 shared-memory pipeline
+    int32_t f_begin;     // first frame of the range this launch covers (a multiple of 32 V)
+    int32_t f_count;     // frames in that range (a multiple of 32 V)
 };
 
 template <typename M>
@@ -97,6 +99,9 @@ struct Workspace {
     uint8_t *h_ok = nullptr;
     float *h_post = nullptr;
     cudaEvent_t last_use = nullptr;  // end of the last decode that used the buffers
+    // two library streams that run the two halves of a batch half a pass apart
+    cudaStream_t half_stream[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, phase = nullptr, join[2] = {nullptr, nullptr};
 };
 
 struct ProfRecord {

@@ -119,7 +119,16 @@ struct MsgIO<__nv_bfloat16> {
 
 template <int V, typename M>
 __device__ __forceinline__ void load_v(const M *p, float (&x)[V]) {
-    if constexpr (V == 4) {
+    if constexpr (V == 8) {
+        float lo[4], hi[4];
+        MsgIO<M>::load4(p, lo);
+        MsgIO<M>::load4(p + 4, hi);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            x[v] = lo[v];
+            x[v + 4] = hi[v];
+        }
+    } else if constexpr (V == 4) {
         MsgIO<M>::load4(p, x);
     } else if constexpr (V == 2) {
         MsgIO<M>::load2(p, x);
@@ -131,7 +140,11 @@ __device__ __forceinline__ void load_v(const M *p, float (&x)[V]) {
 
 template <int V, typename M>
 __device__ __forceinline__ void store_v(M *p, const float (&x)[V]) {
-    if constexpr (V == 4) {
+    if constexpr (V == 8) {
+        float lo[4] = {x[0], x[1], x[2], x[3]}, hi[4] = {x[4], x[5], x[6], x[7]};
+        MsgIO<M>::store4(p, lo);
+        MsgIO<M>::store4(p + 4, hi);
+    } else if constexpr (V == 4) {
         MsgIO<M>::store4(p, x);
     } else if constexpr (V == 2) {
         MsgIO<M>::store2(p, x);
@@ -402,8 +415,16 @@ __device__ __forceinline__ void or_frame_bits(uint32_t *row, int g, int lane, co
         w |= __shfl_xor_sync(kFull, w, 4);
         w |= __shfl_xor_sync(kFull, w, 8);
         if ((lane & 15) == 0 && w) atomicOr(row + g * 2 + (lane >> 4), w);
+    } else if constexpr (V == 8) {
+        uint32_t byte = 0;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) byte |= (bits[v] ? 1u : 0u) << v;
+        uint32_t w = byte << ((lane & 3) * 8);
+        w |= __shfl_xor_sync(kFull, w, 1);
+        w |= __shfl_xor_sync(kFull, w, 2);
+        if ((lane & 3) == 0 && w) atomicOr(row + g * 8 + (lane >> 2), w);
     } else {
-        static_assert(V == 4, "V is 1, 2 or 4");
+        static_assert(V == 4, "V is 1, 2, 4 or 8");
         uint32_t nib = 0;
 #pragma unroll
         for (int v = 0; v < 4; ++v) nib |= (bits[v] ? 1u : 0u) << v;
@@ -425,8 +446,8 @@ __device__ __forceinline__ void or_frame_bits(uint32_t *row, int g, int lane, co
 // the first pass). Writes the d new messages to rows out + k * Fp and ors the
 // check's syndrome of the previous hard decision into unsat.
 template <int D, int V, typename M, typename Load>
-__device__ __forceinline__ void check_node(int d, bool first, Load &&load, M *out, size_t Fp, const PassArgs &a,
-                                           bool (&unsat)[V]) {
+__device__ __forceinline__ void check_node(int d, bool first, bool syn, Load &&load, M *out, size_t Fp,
+                                           const PassArgs &a, bool (&unsat)[V]) {
     float dc[D][V];    // D_k = 1 - tanh(|q_k| / 2)
     uint32_t ones[V];  // bit k: input k says "bit 1" (q > 0)
     uint32_t z[V];
@@ -437,12 +458,13 @@ __device__ __forceinline__ void check_node(int d, bool first, Load &&load, M *ou
         if (k < d) {
             float av[V], rv[V];
             load(k, av, rv);
+            if (syn) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) z[v] ^= av[v] > 0.0f ? 1u : 0u;
+            }
             if (!first) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    z[v] ^= av[v] > 0.0f ? 1u : 0u;
-                    av[v] = av[v] - rv[v];
-                }
+                for (int v = 0; v < V; ++v) av[v] = av[v] - rv[v];
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
@@ -500,17 +522,116 @@ __device__ __forceinline__ void check_node(int d, bool first, Load &&load, M *ou
     }
 }
 
+// The same rule with frames kept in packed pairs (V = 2P frames per lane):
+// every value lives in a float2 register pair, so the packed FP32
+// instructions need no repacking. Same operations, same order, same results
+// as check_node.
+template <typename M, int P>
+__device__ __forceinline__ void store_pairs(M *p, const float2 (&o)[P]) {
+    float x[2 * P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        x[2 * q] = o[q].x;
+        x[2 * q + 1] = o[q].y;
+    }
+    store_v<2 * P, M>(p, x);
+}
+
+template <int D, int P, typename M, typename Load>
+__device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Load &&load, M *out, size_t Fp,
+                                                 const PassArgs &a, bool (&unsat)[2 * P]) {
+    float2 dc[D][P];       // D_k = 1 - tanh(|q_k| / 2), two frames per entry
+    uint32_t ones[2 * P];  // bit k: input k says "bit 1" (q > 0)
+    uint32_t z[2 * P];
+#pragma unroll
+    for (int v = 0; v < 2 * P; ++v) ones[v] = z[v] = 0u;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if (k < d) {
+            float2 av[P], rv[P];
+            load(k, av, rv);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                if (syn) {
+                    z[2 * q] ^= av[q].x > 0.0f ? 1u : 0u;
+                    z[2 * q + 1] ^= av[q].y > 0.0f ? 1u : 0u;
+                }
+                if (!first) av[q] = fma2(rv[q], f2(-1.0f), av[q]);
+                ones[2 * q] |= (av[q].x > 0.0f ? 1u : 0u) << k;
+                ones[2 * q + 1] |= (av[q].y > 0.0f ? 1u : 0u) << k;
+                dc[k][q] = tanh_complement2(make_float2(fabsf(av[q].x), fabsf(av[q].y)), a.l_max, a.phi_lmax);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < P; ++q) dc[k][q] = f2(0.0f);  // T = 1: neutral
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 2 * P; ++v) unsat[v] |= z[v] != 0u;
+    float2 csuf[D][P];
+    {
+        float2 cr[P], pr[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            cr[q] = f2(0.0f);
+            pr[q] = f2(1.0f);
+        }
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                csuf[k][q] = cr[q];
+                cr[q] = fma2(pr[q], dc[k][q], cr[q]);
+                pr[q] = mul2(pr[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
+            }
+        }
+    }
+    float2 cp[P], pp[P];
+    uint32_t neg[2 * P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        cp[q] = f2(0.0f);
+        pp[q] = f2(1.0f);
+    }
+#pragma unroll
+    for (int v = 0; v < 2 * P; ++v) neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if (k < d) {
+            float2 o[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                o[q] = mag_of_complement2(fma2(pp[q], csuf[k][q], cp[q]), a.c_min, a.c_max);
+                o[q].x = __int_as_float(__float_as_int(o[q].x) | (int)((neg[2 * q] << (31 - k)) & 0x80000000u));
+                o[q].y = __int_as_float(__float_as_int(o[q].y) | (int)((neg[2 * q + 1] << (31 - k)) & 0x80000000u));
+                cp[q] = fma2(pp[q], dc[k][q], cp[q]);
+                pp[q] = mul2(pp[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
+            }
+            store_pairs<M, P>(out + (size_t)k * Fp, o);
+        }
+    }
+}
+
+template <int V, typename M>
+__device__ __forceinline__ void load_pairs(const M *p, float2 (&x)[V / 2]) {
+    float t[V];
+    load_v<V, M>(p, t);
+#pragma unroll
+    for (int q = 0; q < V / 2; ++q) x[q] = make_float2(t[2 * q], t[2 * q + 1]);
+}
+
 // Checks of degree <= D, inputs read straight from global memory.
 template <int D, int V, typename M>
 __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_t *__restrict__ checks,
                                                         int32_t count) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int g = blockIdx.y;
+    const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
     const int f0 = g * 32 * V + lane * V;
     const size_t Fp = (size_t)a.Fp;
     M *r = reinterpret_cast<M *>(a.r);
     const bool first = a.pass == 0;
+    const bool syn = a.syndrome != 0;
     const float *qsrc = first ? a.lamT : a.app;
 
     bool live[V];
@@ -530,12 +651,21 @@ __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_
         const int i = checks[w];
         const int b = a.row_ptr[i];
         const int d = a.row_ptr[i + 1] - b;  // warp-uniform, 1 <= d <= D
-        auto load = [&](int k, float (&av)[V], float (&rv)[V]) {
-            const int slot = b + k;
-            load_v<V, float>(qsrc + (size_t)a.col_idx[slot] * Fp + f0, av);
-            if (!first) load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
-        };
-        check_node<D, V, M>(d, first, load, r + (size_t)b * Fp + f0, Fp, a, unsat);
+        if constexpr (V % 2 == 0) {
+            auto load = [&](int k, float2 (&av)[V / 2], float2 (&rv)[V / 2]) {
+                const int slot = b + k;
+                load_pairs<V, float>(qsrc + (size_t)a.col_idx[slot] * Fp + f0, av);
+                if (!first) load_pairs<V, M>(r + (size_t)slot * Fp + f0, rv);
+            };
+            check_node_pairs<D, V / 2, M>(d, first, syn, load, r + (size_t)b * Fp + f0, Fp, a, unsat);
+        } else {
+            auto load = [&](int k, float (&av)[V], float (&rv)[V]) {
+                const int slot = b + k;
+                load_v<V, float>(qsrc + (size_t)a.col_idx[slot] * Fp + f0, av);
+                if (!first) load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
+            };
+            check_node<D, V, M>(d, first, syn, load, r + (size_t)b * Fp + f0, Fp, a, unsat);
+        }
     }
     if (a.syndrome) {
         bool bits[V];
@@ -572,19 +702,22 @@ struct PipeShape {
     static constexpr int kStage = D * (kRowA + kRowR);        // bytes of one check's rows
 };
 
-template <int D, int V, typename M, int S>
+template <int D, int V, typename M, int S, int MODE>
 __global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 *__restrict__ desc, int32_t count) {
     using P = PipeShape<D, V, M>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char *ring = smem + (size_t)warp * S * P::kStage;
-    const int g = blockIdx.y;
+    const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
     const int fbase = g * 32 * V;
     const int f0 = fbase + lane * V;
     const size_t Fp = (size_t)a.Fp;
     M *r = reinterpret_cast<M *>(a.r);
-    const bool first = a.pass == 0;
+    // MODE: 0 = first pass (q = lambda), 1 = later pass, 2 = later pass that
+    // also tests the previous hard decision (compile-time, no per-edge tests)
+    constexpr bool first = MODE == 0;
+    constexpr bool syn = MODE == 2;
     const float *qsrc = first ? a.lamT : a.app;
 
     bool live[V];
@@ -657,13 +790,15 @@ __global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 
         cp_async_wait<S - 1>();
         __syncwarp();
         const unsigned char *base = ring + (n % S) * P::kStage;
-        auto load = [&](int k, float (&av)[V], float (&rv)[V]) {
-            const float *pa = reinterpret_cast<const float *>(base + k * P::kRowA) + lane * V;
+        static_assert(V % 2 == 0, "the pipelined kernel runs frame pairs");
+        auto load = [&](int k, float2 (&av)[V / 2], float2 (&rv)[V / 2]) {
+            const float2 *pa = reinterpret_cast<const float2 *>(base + k * P::kRowA) + lane * (V / 2);
 #pragma unroll
-            for (int v = 0; v < V; ++v) av[v] = pa[v];
-            if (!first) load_v<V, M>(reinterpret_cast<const M *>(base + D * P::kRowA + k * P::kRowR) + lane * V, rv);
+            for (int q = 0; q < V / 2; ++q) av[q] = pa[q];
+            if (!first)
+                load_pairs<V, M>(reinterpret_cast<const M *>(base + D * P::kRowA + k * P::kRowR) + lane * V, rv);
         };
-        check_node<D, V, M>(qd[0], first, load, r + (size_t)qb[0] * Fp + f0, Fp, a, unsat);
+        check_node_pairs<D, V / 2, M>(qd[0], first, syn, load, r + (size_t)qb[0] * Fp + f0, Fp, a, unsat);
         __syncwarp();
 #pragma unroll
         for (int s = 0; s < S - 1; ++s) {
@@ -690,7 +825,7 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
                                                         int32_t count) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int g = blockIdx.y;
+    const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
     const int f0 = g * 32 * V + lane * V;
     const size_t Fp = (size_t)a.Fp;
     M *r = reinterpret_cast<M *>(a.r);
@@ -791,7 +926,7 @@ template <int V, typename M>
 __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int g = blockIdx.y;
+    const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
     const int f0 = g * 32 * V + lane * V;
     const size_t Fp = (size_t)a.Fp;
     const M *r = reinterpret_cast<const M *>(a.r);
@@ -803,7 +938,8 @@ __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
     // give the same answer, since it is set exactly when that frame's
     // previous syndrome was zero, which they test as well.
     if (exit_test && blockIdx.x == 0 && blockIdx.y == 0) {
-        for (int f = threadIdx.x; f < a.n_frames; f += blockDim.x) {
+        const int f_end = min(a.f_begin + a.f_count, a.n_frames);
+        for (int f = a.f_begin + threadIdx.x; f < f_end; f += blockDim.x) {
             if (!frame_bit(a.done, f) && !frame_bit(unsat_prev, f)) {
                 atomicOr(a.done + (f >> 5), 1u << (f & 31));
                 a.stop_iter[f] = a.pass - 1;
@@ -872,7 +1008,7 @@ __global__ void k_export_r(PassArgs a, float *__restrict__ r_out) {
 // ---------------------------------------------------------------------------
 
 inline dim3 pass_grid(const PassArgs &a, int64_t nodes, int V) {
-    int groups = a.Fp / (32 * V);
+    int groups = a.f_count / (32 * V);
     int64_t want = (nodes + (kThreads / 32) - 1) / (kThreads / 32);
     int64_t cap = a.grid_ctas / groups;
     if (cap < 1) cap = 1;
@@ -897,34 +1033,43 @@ static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t 
 
 // Pipelined kernel: dynamic shared memory above 48 KB needs an opt-in, and
 // the grid is sized to the CTAs that fit on the GPU at once.
-template <int D, int V, typename M, int S>
-static cudaError_t launch_pipe(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
+template <int D, int V, typename M, int S, int MODE>
+static cudaError_t launch_pipe_mode(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
     static int resident_by_device[64] = {0};  // CTAs per SM, once per device
     int dev = 0;
     cudaGetDevice(&dev);
     int &resident = resident_by_device[dev & 63];
     const size_t smem = (size_t)(kThreads / 32) * S * PipeShape<D, V, M>::kStage;
     if (resident == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_check_pipe<D, V, M, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_check_pipe<D, V, M, S, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_pipe<D, V, M, S>, kThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_pipe<D, V, M, S, MODE>, kThreads, smem);
         if (e != cudaSuccess) return e;
         resident = nb > 0 ? nb : 1;
     }
     PassArgs b = a;
     b.grid_ctas = a.sm_count * resident;
     dim3 grid = pass_grid(b, count, V);
-    k_check_pipe<D, V, M, S><<<grid, kThreads, smem, s>>>(a, desc, count);
+    k_check_pipe<D, V, M, S, MODE><<<grid, kThreads, smem, s>>>(a, desc, count);
     return cudaGetLastError();
+}
+
+// Pipelined kernel: dynamic shared memory above 48 KB needs an opt-in, and
+// the grid is sized to the CTAs that fit on the GPU at once.
+template <int D, int V, typename M, int S>
+static cudaError_t launch_pipe(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
+    if (a.pass == 0) return launch_pipe_mode<D, V, M, S, 0>(a, desc, count, s);
+    if (a.syndrome) return launch_pipe_mode<D, V, M, S, 2>(a, desc, count, s);
+    return launch_pipe_mode<D, V, M, S, 1>(a, desc, count, s);
 }
 
 template <typename M>
 cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, const int2 *desc, int32_t count,
                              cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    if (a.check_schedule != 1 && bin <= 2 && a.Fp % 64 == 0) {
+    if (a.check_schedule != 1 && bin <= 2 && a.f_count % 64 == 0 && a.f_begin % 64 == 0) {
         switch (bin) {
         case 0: return launch_pipe<4, 2, M, 4>(a, desc, count, s);
         case 1: return launch_pipe<8, 2, M, 3>(a, desc, count, s);
@@ -942,7 +1087,9 @@ cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, 
 template <typename M>
 cudaError_t launch_bit(const PassArgs &a, cudaStream_t s) {
     dim3 grid = pass_grid(a, a.n, a.V);
-    if (a.V == 4)
+    if (a.V == 8)
+        k_bit<8, M><<<grid, kThreads, 0, s>>>(a);
+    else if (a.V == 4)
         k_bit<4, M><<<grid, kThreads, 0, s>>>(a);
     else if (a.V == 2)
         k_bit<2, M><<<grid, kThreads, 0, s>>>(a);

@@ -173,6 +173,8 @@ cudaError_t run_static(ldpc_code *c, unsigned char *scratch, const float *llr, i
     a.grid_ctas = std::max(1, c->sm_count) * 4;
     a.sm_count = std::max(1, c->sm_count);
     a.check_schedule = o.check_schedule;
+    a.f_begin = 0;
+    a.f_count = Fp;
 
     // what must start at zero: the syndrome flag rows, and posteriors (the
     // padding frames' columns are read but never written)
