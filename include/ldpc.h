@@ -140,8 +140,12 @@ typedef struct {
                            halves of the batch on two library streams, half a
                            pass apart, so that the check pass of one half
                            overlaps the bit pass of the other; 0 = 2 when the
-                           batch splits evenly. Results do not depend on any
-                           tuning field                                      */
+                           batch splits evenly                              */
+    int32_t tile_frames; /* tuning: run all passes of tile_frames frames at a
+                           time (rounded up to the kernels' frame group; tiles
+                           alternate between the two streams), so that one
+                           tile's working set can stay in L2; 0 = one tile per
+                           stream. Results do not depend on any tuning field */
 } ldpc_decode_opts_t;
 
 /*

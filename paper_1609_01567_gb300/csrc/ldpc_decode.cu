@@ -290,48 +290,55 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
         region_start = take_event(c);
         cudaEventRecord(region_start, s);
     }
-    const int32_t vmax = std::max(V, 2);
-    const bool split = o.streams != 1 && Fp % (64 * vmax) == 0 && (o.streams == 2 || Fp >= 256);
-    int nh = 1;
-    PassArgs half[2] = {a, a};
+    // Tiles: frame ranges that run all their passes back to back. By default
+    // there is one tile per stream; smaller tiles keep one tile's working set
+    // (messages, posteriors, LLRs) within L2 while it iterates. With two
+    // streams, consecutive tiles alternate between them and the second stream
+    // starts when the first has finished its first check pass.
+    const int32_t unit = 32 * std::max(V, 2);
+    const bool split = o.streams != 1 && Fp % (2 * unit) == 0 && (o.streams == 2 || Fp >= 256);
+    int32_t tile = o.tile_frames > 0 ? (o.tile_frames + unit - 1) / unit * unit : 0;
+    if (tile <= 0 || tile >= Fp || Fp % tile != 0) tile = split ? Fp / 2 : Fp;
+    const int32_t ntiles = Fp / tile;
+    const int nstreams = split && ntiles >= 2 ? 2 : 1;
     cudaStream_t hs[2] = {s, s};
-    if (split) {
+    if (nstreams == 2) {
         if ((e = ensure_half_streams(c)) != cudaSuccess) return e;
-        nh = 2;
-        half[0].f_count = half[1].f_count = Fp / 2;
-        half[1].f_begin = Fp / 2;
         hs[0] = w.half_stream[0];
         hs[1] = w.half_stream[1];
         if ((e = cudaEventRecord(w.fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(hs[0], w.fork, 0)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(hs[1], w.fork, 0)) != cudaSuccess) return e;
     }
-    for (int32_t t = 0; t <= max_iter; ++t) {
-        for (int h = 0; h < nh; ++h) {
-            PassArgs &ah = half[h];
-            Launcher Lh{c, hs[h], o.profile != 0};
-            ah.pass = t;
-            ah.syndrome = (t > 0 && ah.early_exit) ? 1 : 0;
+    for (int32_t ti = 0; ti < ntiles; ++ti) {
+        const int h = ti % nstreams;
+        PassArgs at = a;
+        at.f_begin = ti * tile;
+        at.f_count = tile;
+        Launcher Lh{c, hs[h], o.profile != 0};
+        for (int32_t t = 0; t <= max_iter; ++t) {
+            at.pass = t;
+            at.syndrome = (t > 0 && at.early_exit) ? 1 : 0;
             for (int b = 0; b < kNumCheckBins; ++b) {
                 int32_t count = c->bin_off[b + 1] - c->bin_off[b];
                 if (count == 0) continue;
                 e = Lh(LDPC_K_CHECK, 1, [&] {
-                    return launch_check_bin<M>(ah, b, c->d.bin_checks + c->bin_off[b], c->d.bin_desc + c->bin_off[b],
+                    return launch_check_bin<M>(at, b, c->d.bin_checks + c->bin_off[b], c->d.bin_desc + c->bin_off[b],
                                                count, hs[h]);
                 });
                 if (e != cudaSuccess) return e;
             }
-            if (split && t == 0 && h == 0) {
+            if (nstreams == 2 && ti == 0 && t == 0) {
                 if ((e = cudaEventRecord(w.phase, hs[0])) != cudaSuccess) return e;
                 if ((e = cudaStreamWaitEvent(hs[1], w.phase, 0)) != cudaSuccess) return e;
             }
             if (c->n > 0) {
-                e = Lh(LDPC_K_BIT, 1, [&] { return launch_bit<M>(ah, hs[h]); });
+                e = Lh(LDPC_K_BIT, 1, [&] { return launch_bit<M>(at, hs[h]); });
                 if (e != cudaSuccess) return e;
             }
         }
     }
-    if (split) {
+    if (nstreams == 2) {
         for (int h = 0; h < 2; ++h) {
             if ((e = cudaEventRecord(w.join[h], hs[h])) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(s, w.join[h], 0)) != cudaSuccess) return e;
@@ -386,6 +393,7 @@ static int check_decode_args(const ldpc_code *c, int32_t F, int32_t max_iter, co
         o.frames_per_lane != 8)
         return set_error(LDPC_EINVAL, "%s: frames_per_lane=%d not in {0, 1, 2, 4, 8}", fn, o.frames_per_lane);
     if (o.streams < 0 || o.streams > 2) return set_error(LDPC_EINVAL, "%s: streams=%d not in {0, 1, 2}", fn, o.streams);
+    if (o.tile_frames < 0) return set_error(LDPC_EINVAL, "%s: tile_frames=%d < 0", fn, o.tile_frames);
     if (o.msg_dtype != LDPC_MSG_F32 && o.msg_dtype != LDPC_MSG_F16 && o.msg_dtype != LDPC_MSG_BF16)
         return set_error(LDPC_EINVAL, "%s: unknown msg_dtype %d", fn, o.msg_dtype);
     *l_max_out = l_max;

@@ -40,7 +40,7 @@ class ldpc_code_info_t(ctypes.Structure):
 class ldpc_decode_opts_t(ctypes.Structure):
     _fields_ = [("early_exit", ctypes.c_int32), ("l_max", ctypes.c_float), ("msg_dtype", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("r_out", ctypes.c_void_p), ("frames_per_lane", ctypes.c_int32),
-                ("check_schedule", ctypes.c_int32), ("streams", ctypes.c_int32)]
+                ("check_schedule", ctypes.c_int32), ("streams", ctypes.c_int32), ("tile_frames", ctypes.c_int32)]
 
 
 class ldpc_prof_t(ctypes.Structure):
@@ -173,18 +173,19 @@ def ldpc_code_tables(code: Code) -> dict:
     return arrs
 
 
-def _opts(early_exit, l_max, msg_dtype, profile, r_out_ptr, frames_per_lane=0, check_schedule=0, streams=0):
+def _opts(early_exit, l_max, msg_dtype, profile, r_out_ptr, frames_per_lane=0, check_schedule=0, streams=0,
+          tile_frames=0):
     if msg_dtype not in LDPC_MSG:
         raise ValueError(f"msg_dtype must be one of {sorted(LDPC_MSG)}")
     return ldpc_decode_opts_t(early_exit=1 if early_exit else 0, l_max=float(l_max), msg_dtype=LDPC_MSG[msg_dtype],
                               profile=1 if profile else 0, r_out=r_out_ptr, frames_per_lane=int(frames_per_lane),
-                              check_schedule=int(check_schedule), streams=int(streams))
+                              check_schedule=int(check_schedule), streams=int(streams), tile_frames=int(tile_frames))
 
 
 def ldpc_decode(code: Code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
                 msg_dtype: str = "f32", profile: bool = False, want_post: bool = True, want_r: bool = False,
                 out: dict | None = None, stream=None, frames_per_lane: int = 0, check_schedule: int = 0,
-                streams: int = 0) -> dict:
+                streams: int = 0, tile_frames: int = 0) -> dict:
     """Decode ``llr`` (CUDA float32 [F, n]); returns CUDA tensors
     ``bits`` uint8 [F, n], ``iters`` int32 [F], ``ok`` uint8 [F] and, when
     asked, ``post`` float32 [F, n] and ``r`` float32 [F, E] (edge order)."""
@@ -205,7 +206,7 @@ def ldpc_decode(code: Code, llr, max_iter: int, *, early_exit: bool = True, l_ma
         o["r"] = torch.empty((f, code.n_edges), dtype=torch.float32, device=dev)
     r_ptr = _dev_ptr(o.get("r"), torch.float32, (f, code.n_edges), "r", code.device) if want_r else None
     opts = _opts(early_exit, l_max, msg_dtype, profile, r_ptr.value if r_ptr else None, frames_per_lane,
-                 check_schedule, streams)
+                 check_schedule, streams, tile_frames)
     _check(library().ldpc_decode(
         code.handle, _dev_ptr(llr, torch.float32, (f, code.n), "llr", code.device), f, max_iter, ctypes.byref(opts),
         _dev_ptr(o["bits"], torch.uint8, (f, code.n), "bits", code.device),
@@ -218,7 +219,8 @@ def ldpc_decode(code: Code, llr, max_iter: int, *, early_exit: bool = True, l_ma
 
 def ldpc_decode_host(code: Code, llr: np.ndarray, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
                      msg_dtype: str = "f32", profile: bool = False, want_post: bool = False, out: dict | None = None,
-                     stream=None, frames_per_lane: int = 0, check_schedule: int = 0, streams: int = 0) -> dict:
+                     stream=None, frames_per_lane: int = 0, check_schedule: int = 0, streams: int = 0,
+                     tile_frames: int = 0) -> dict:
     """Decode host LLRs (numpy float32 [F, n], or a pinned CPU torch tensor);
     copies in and out inside the call and returns host arrays."""
     import torch
@@ -245,7 +247,7 @@ def ldpc_decode_host(code: Code, llr: np.ndarray, max_iter: int, *, early_exit: 
     o.setdefault("ok", mk((f,), dts[2]))
     if want_post:
         o.setdefault("post", mk((f, n), dts[3]))
-    opts = _opts(early_exit, l_max, msg_dtype, profile, None, frames_per_lane, check_schedule, streams)
+    opts = _opts(early_exit, l_max, msg_dtype, profile, None, frames_per_lane, check_schedule, streams, tile_frames)
     _check(library().ldpc_decode_host(code.handle, llr_ptr, f, max_iter, ctypes.byref(opts), ptr(o["bits"]),
                                       ptr(o["iters"]), ptr(o["ok"]), ptr(o["post"]) if want_post else None,
                                       _stream_handle(stream)))

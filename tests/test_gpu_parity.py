@@ -202,16 +202,18 @@ def test_prefix_property_and_symmetry_on_gpu(ldpc, n1008):
 
 @pytest.mark.parametrize("msg", ["f32", "f16", "bf16"])
 def test_schedules_do_not_change_results(ldpc, n1008, msg):
-    """Frames per lane, the check-kernel schedule and the two-stream split are
-    tuning knobs only: results are bit-identical."""
+    """Frames per lane, the check-kernel schedule, the two-stream split and the
+    frame tiles are tuning knobs only: results are bit-identical."""
     code, cw, llr = n1008
     h = ldpc.code_from_inputs(code)
     base = gpu_decode(ldpc, h, llr, 15, frames_per_lane=1, check_schedule=1, streams=1, msg_dtype=msg)
-    for v, sched, nst in ((2, 1, 1), (4, 1, 1), (2, 2, 1), (4, 2, 1), (4, 2, 2), (8, 2, 2), (8, 1, 1), (2, 2, 2),
-                          (0, 0, 0)):
-        other = gpu_decode(ldpc, h, llr, 15, frames_per_lane=v, check_schedule=sched, streams=nst, msg_dtype=msg)
+    for v, sched, nst, tile in ((2, 1, 1, 0), (4, 1, 1, 0), (2, 2, 1, 0), (4, 2, 1, 0), (4, 2, 2, 0), (8, 2, 2, 0),
+                                (8, 1, 1, 0), (2, 2, 2, 0), (4, 2, 2, 256), (2, 2, 1, 64), (4, 2, 2, 128), (0, 0, 0, 0)):
+        other = gpu_decode(ldpc, h, llr, 15, frames_per_lane=v, check_schedule=sched, streams=nst, tile_frames=tile,
+                           msg_dtype=msg)
         for k in ("bits", "iters", "ok", "post"):
-            np.testing.assert_array_equal(other[k], base[k], err_msg=f"V={v} schedule={sched} streams={nst} {k}")
+            np.testing.assert_array_equal(other[k], base[k],
+                                          err_msg=f"V={v} schedule={sched} streams={nst} tile={tile} {k}")
 
 
 def test_host_entry_point_matches_device_entry_point(ldpc, n1008):
