@@ -225,6 +225,18 @@ int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int32_t n_fram
 int ldpc_gen_awgn(uint64_t seed, int64_t frame_offset, int32_t n_frames, int32_t n, float sigma2,
                   const uint8_t *codewords, float *llr, void *stream);
 
+/*
+ * Error counts of the BER simulator (Section IV): for decoded words bits
+ * [n_frames][n] and the transmitted words ref [n_frames][n] (NULL = the
+ * all-zero word, enough by the code's linearity), adds to device counts[0]
+ * the bit errors, counts[1] the frames with at least one error, counts[2]
+ * the sum of iters (device [n_frames], optional) and counts[3] the frames
+ * with syndrome_ok == 0 (device [n_frames], optional). counts is device
+ * int64 [4], accumulated (zero it first). Asynchronous on `stream`.
+ */
+int ldpc_count_errors(const uint8_t *bits, const uint8_t *ref, int32_t n_frames, int32_t n, const int32_t *iters,
+                      const uint8_t *syndrome_ok, int64_t *counts, void *stream);
+
 /* Raw Philox-4x64-10 blocks: out[i][0..3] = Philox(key (key0, key1),
  * counter (ctr0 + i, ctr1, 0, 0)) for 0 <= i < count; out is device
  * [count][4] uint64. */

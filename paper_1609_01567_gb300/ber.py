@@ -1,0 +1,107 @@
+"""BER/FER simulation on the GPU (the BER simulator of Section IV).
+
+Every batch runs three library calls on one stream: the Philox BPSK/AWGN
+generator (all-zero codeword, enough by linearity, or random codewords),
+the decoder, and the on-device error count. Counters stay on the device
+until the end. Frame noise depends only on (seed, global frame index), so
+runs split across batches or ranks see the same channel.
+
+    python -m paper_1609_01567_gb300.ber --code n64800 --ebn0 1.0 1.2 1.4 \
+        --frames 1000000 --batch 1024 --msg f32 f16 bf16
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+from . import inputs
+from .shard import Counts
+
+
+def wilson(k: int, n: int, z: float = 1.96) -> tuple[float, float]:
+    """Wilson score interval of a binomial proportion k / n."""
+    if n == 0:
+        return 0.0, 1.0
+    p = k / n
+    den = 1 + z * z / n
+    mid = (p + z * z / (2 * n)) / den
+    half = z * math.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / den
+    return max(0.0, mid - half), min(1.0, mid + half)
+
+
+def simulate(handle, code, ebn0_db: float, n_frames: int, *, batch: int = 1024, max_iter: int = 50,
+             early_exit: bool = True, msg_dtype: str = "f32", seed: int = 1, frame_offset: int = 0,
+             codewords=None, stream=None, **decode_kw) -> Counts:
+    """Decode n_frames noisy frames; returns summed Counts.
+
+    codewords: None for the all-zero word, else a CUDA uint8 tensor
+    [n_frames, n] of transmitted codewords.
+    """
+    import torch
+
+    from . import ldpc
+
+    dev = torch.device("cuda", handle.device)
+    sigma2 = inputs.sigma2_from_ebn0(ebn0_db, code.rate)
+    counts = torch.zeros(4, dtype=torch.int64, device=dev)
+    llr = torch.empty((batch, code.n), dtype=torch.float32, device=dev)
+    out = None
+    done = 0
+    while done < n_frames:
+        b = min(batch, n_frames - done)
+        cw = None if codewords is None else codewords[done:done + b]
+        lb = llr[:b]
+        ldpc.ldpc_gen_awgn(seed, frame_offset + done, b, code.n, sigma2, cw, out=lb, device=handle.device,
+                           stream=stream)
+        if out is None or out["bits"].shape[0] != b:
+            out = None
+        out = ldpc.ldpc_decode(handle, lb, max_iter, early_exit=early_exit, msg_dtype=msg_dtype, want_post=False,
+                               out=out, stream=stream, **decode_kw)
+        ldpc.ldpc_count_errors(out["bits"], cw, out["iters"], out["ok"], counts=counts, stream=stream)
+        done += b
+    torch.cuda.synchronize(dev)
+    v = counts.cpu().tolist()
+    return Counts(frames=n_frames, bit_errors=v[0], frame_errors=v[1], iterations=v[2], unsatisfied=v[3])
+
+
+def summary(c: Counts, n: int) -> dict:
+    fer_lo, fer_hi = wilson(c.frame_errors, c.frames)
+    ber_lo, ber_hi = wilson(c.bit_errors, c.frames * n)
+    return {"frames": c.frames, "frame_errors": c.frame_errors, "bit_errors": c.bit_errors,
+            "fer": c.frame_errors / max(c.frames, 1), "fer_ci95": [fer_lo, fer_hi],
+            "ber": c.bit_errors / max(c.frames * n, 1), "ber_ci95": [ber_lo, ber_hi],
+            "mean_iters": c.iterations / max(c.frames, 1)}
+
+
+CODES = {"n1008": inputs.small_code_n1008, "n64800": inputs.large_code_n64800}
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description="GPU BER/FER simulation")
+    p.add_argument("--code", choices=sorted(CODES), default="n64800")
+    p.add_argument("--ebn0", type=float, nargs="+", default=[1.0, 1.2, 1.4])
+    p.add_argument("--frames", type=int, default=100000)
+    p.add_argument("--batch", type=int, default=1024)
+    p.add_argument("--max-iter", type=int, default=50)
+    p.add_argument("--msg", nargs="+", default=["f32", "f16", "bf16"])
+    p.add_argument("--seed", type=int, default=1)
+    args = p.parse_args(argv)
+
+    from . import ldpc
+
+    code = CODES[args.code]()
+    h = ldpc.code_from_inputs(code)
+    for eb in args.ebn0:
+        for msg in args.msg:
+            t0 = time.perf_counter()
+            c = simulate(h, code, eb, args.frames, batch=args.batch, max_iter=args.max_iter, msg_dtype=msg,
+                         seed=args.seed)
+            line = {"code": args.code, "ebn0_db": eb, "msg_dtype": msg, "max_iter": args.max_iter,
+                    "seconds": time.perf_counter() - t0, **summary(c, code.n)}
+            print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -48,7 +48,7 @@ class ldpc_prof_t(ctypes.Structure):
 
 
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
-           "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
+           "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_count_errors", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
            "ldpc_version")
 
 _LIB = None
@@ -76,12 +76,13 @@ def library():
                                                vp]
             lib.ldpc_gen_awgn.argtypes = [u64, i64, i32, i32, ctypes.c_float, vp, vp, vp]
             lib.ldpc_philox4x64_10.argtypes = [u64, u64, u64, u64, i64, vp, vp]
+            lib.ldpc_count_errors.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
             lib.ldpc_prof_read.argtypes = [vp, ctypes.POINTER(ldpc_prof_t), i32]
             lib.ldpc_last_error.restype = ctypes.c_char_p
             lib.ldpc_version.restype = ctypes.c_char_p
             for name in ("ldpc_code_create", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode", "ldpc_decode_host",
                          "ldpc_decode_static",
-                         "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read"):
+                         "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_count_errors"):
                 getattr(lib, name).restype = ctypes.c_int
             _LIB = lib
         return _LIB
@@ -296,6 +297,20 @@ def ldpc_gen_awgn(seed: int, frame_offset: int, n_frames: int, n: int, sigma2: f
                                    _dev_ptr(codewords, torch.uint8, (n_frames, n), "codewords", None),
                                    _dev_ptr(out, torch.float32, (n_frames, n), "out", None), _stream_handle(stream)))
     return out
+
+
+def ldpc_count_errors(bits, ref=None, iters=None, ok=None, counts=None, stream=None):
+    """Accumulate [bit errors, frame errors, sum of iterations, unsatisfied
+    frames] of decoded words into a CUDA int64 tensor [4] (returned)."""
+    import torch
+    f, n = bits.shape
+    if counts is None:
+        counts = torch.zeros(4, dtype=torch.int64, device=bits.device)
+    _check(library().ldpc_count_errors(
+        _dev_ptr(bits, torch.uint8, (f, n), "bits", None), _dev_ptr(ref, torch.uint8, (f, n), "ref", None), f, n,
+        _dev_ptr(iters, torch.int32, (f,), "iters", None), _dev_ptr(ok, torch.uint8, (f,), "ok", None),
+        _dev_ptr(counts, torch.int64, (4,), "counts", None), _stream_handle(stream)))
+    return counts
 
 
 def ldpc_philox4x64_10(key0: int, key1: int, ctr0: int, ctr1: int, count: int, device: int = 0, stream=None):
