@@ -181,6 +181,43 @@ int ldpc_decode_host(ldpc_code_t *code, const float *llr_host, int32_t n_frames,
                      uint8_t *syndrome_ok_host, float *post_llr_host, void *stream);
 
 /*
+ * Mixed-code batches. A batch holds several (code, frame count) items, all on
+ * one device, each with its own decode workspace (allocated here) and
+ * stream. ldpc_batch_run decodes every item's frames; the items run as
+ * parallel branches forked from and joined into `stream`. The first run
+ * launches the kernels directly; later runs replay one CUDA graph captured
+ * from that sequence (re-captured when any buffer pointer changes). Results
+ * equal ldpc_decode's for each item with the same options.
+ *   codes, n_frames: n_items entries (1 <= n_frames[i] <= 8192); opts as in
+ *   ldpc_decode (NULL = defaults; profile and r_out must be 0/NULL; the
+ *   stream split and tiles are not used inside a batch).
+ * Runs of one batch are serialised on the device. The batch borrows the code
+ * handles: destroy the batch before its codes.
+ */
+typedef struct ldpc_batch ldpc_batch_t;
+
+int ldpc_batch_create(int32_t n_items, ldpc_code_t *const *codes, const int32_t *n_frames, int32_t max_iter,
+                      const ldpc_decode_opts_t *opts, ldpc_batch_t **out);
+
+/* Decode every item: llr[i] device [n_frames[i]][n_i] float, outputs as in
+ * ldpc_decode (post_llr may be NULL, or hold NULL entries). Asynchronous. */
+int ldpc_batch_run(ldpc_batch_t *batch, const float *const *llr, uint8_t *const *bits, int32_t *const *iters,
+                   uint8_t *const *syndrome_ok, float *const *post_llr, void *stream);
+
+/* Autotune each item's kernel schedule (frames per lane in {1, 2, 4, 8} with
+ * padding at most a quarter of the frames, direct or pipelined check
+ * kernel) by timing decodes of the given device LLRs; keeps the fastest.
+ * Synchronous; allocates temporary outputs. */
+int ldpc_batch_tune(ldpc_batch_t *batch, const float *const *llr, void *stream);
+
+/* The schedule picked for one item and the kernels one graph replay runs. */
+int ldpc_batch_info(const ldpc_batch_t *batch, int32_t item, int32_t *frames_per_lane, int32_t *check_schedule,
+                    int64_t *kernels_per_run);
+
+/* Waits for the batch's pending work and releases it. NULL is ignored. */
+void ldpc_batch_destroy(ldpc_batch_t *batch);
+
+/*
  * ldpc_decode for callers that cannot allocate device memory when they
  * decode: a latency-bound receive chain that must not stall on cudaMalloc
  * (which may synchronise the device), or a plug-in confined to another

@@ -47,26 +47,7 @@ static void free_device_tables(ldpc_code *c) {
     cudaFree(c->d.edge_slot);
     cudaFree(c->d.bin_checks);
     cudaFree(c->d.bin_desc);
-    Workspace &w = c->ws;
-    if (w.last_use) cudaEventSynchronize(w.last_use);
-    cudaFree(w.lamT);
-    cudaFree(w.app);
-    cudaFree(w.r);
-    cudaFree(w.done);
-    cudaFree(w.unsat);
-    cudaFree(w.stop_iter);
-    cudaFree(w.h_llr);
-    cudaFree(w.h_bits);
-    cudaFree(w.h_iters);
-    cudaFree(w.h_ok);
-    cudaFree(w.h_post);
-    if (w.last_use) cudaEventDestroy(w.last_use);
-    for (int h = 0; h < 2; ++h) {
-        if (w.half_stream[h]) cudaStreamDestroy(w.half_stream[h]);
-        if (w.join[h]) cudaEventDestroy(w.join[h]);
-    }
-    if (w.fork) cudaEventDestroy(w.fork);
-    if (w.phase) cudaEventDestroy(w.phase);
+    free_workspace(c->ws);
     for (auto &p : c->prof) {
         cudaEventDestroy(p.start);
         cudaEventDestroy(p.stop);

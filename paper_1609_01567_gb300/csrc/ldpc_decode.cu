@@ -147,8 +147,7 @@ static cudaError_t grow(T **p, size_t count) {
 }
 
 // Device buffers for Fp frames and max_iter iterations (grown, never shrunk).
-static int ensure_workspace(ldpc_code *c, int32_t Fp, int32_t max_iter, int msg_bytes) {
-    Workspace &w = c->ws;
+static int ensure_workspace(ldpc_code *c, Workspace &w, int32_t Fp, int32_t max_iter, int msg_bytes) {
     bool need_frames = Fp > w.fp_cap || msg_bytes > w.msg_bytes;
     bool need_iters = need_frames || max_iter > w.iter_cap;
     if (!need_frames && !need_iters) return LDPC_OK;
@@ -193,8 +192,7 @@ static cudaEvent_t take_event(ldpc_code *c) {
 }
 
 // The two library streams (non-blocking) and their fork/phase/join events.
-static cudaError_t ensure_half_streams(ldpc_code *c) {
-    Workspace &w = c->ws;
+static cudaError_t ensure_half_streams(Workspace &w) {
     cudaError_t e = cudaSuccess;
     for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
         if (!w.half_stream[h]) e = cudaStreamCreateWithFlags(&w.half_stream[h], cudaStreamNonBlocking);
@@ -229,10 +227,9 @@ struct Launcher {
 };
 
 template <typename M>
-static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t max_iter, const ldpc_decode_opts_t &o,
-                             float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok, float *post, float *r_out,
-                             cudaStream_t s) {
-    Workspace &w = c->ws;
+static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32_t F, int32_t max_iter,
+                             const ldpc_decode_opts_t &o, float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok,
+                             float *post, float *r_out, cudaStream_t s) {
     int32_t V, Fp;
     frames_layout(F, o.frames_per_lane, &V, &Fp);
     PassArgs a{};
@@ -303,7 +300,7 @@ static cudaError_t run_chunk(ldpc_code *c, const float *llr, int32_t F, int32_t 
     const int nstreams = split && ntiles >= 2 ? 2 : 1;
     cudaStream_t hs[2] = {s, s};
     if (nstreams == 2) {
-        if ((e = ensure_half_streams(c)) != cudaSuccess) return e;
+        if ((e = ensure_half_streams(w)) != cudaSuccess) return e;
         hs[0] = w.half_stream[0];
         hs[1] = w.half_stream[1];
         if ((e = cudaEventRecord(w.fork, s)) != cudaSuccess) return e;
@@ -415,7 +412,7 @@ static int decode_locked(ldpc_code *c, const float *llr, int32_t F, int32_t max_
     int32_t chunk = std::min(F, kMaxChunkFrames);
     int32_t V, Fp;
     frames_layout(chunk, o.frames_per_lane, &V, &Fp);
-    int st = ensure_workspace(c, Fp, max_iter, msg_size(o.msg_dtype));
+    int st = ensure_workspace(c, c->ws, Fp, max_iter, msg_size(o.msg_dtype));
     if (st != LDPC_OK) return st;
     cudaError_t e = cudaStreamWaitEvent(s, c->ws.last_use, 0);
     if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: cudaStreamWaitEvent");
@@ -427,13 +424,13 @@ static int decode_locked(ldpc_code *c, const float *llr, int32_t F, int32_t max_
         float *rr = o.r_out ? o.r_out + (size_t)f0 * c->E : nullptr;
         switch (o.msg_dtype) {
         case LDPC_MSG_F16:
-            e = run_chunk<__half>(c, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
+            e = run_chunk<__half>(c, c->ws, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
             break;
         case LDPC_MSG_BF16:
-            e = run_chunk<__nv_bfloat16>(c, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
+            e = run_chunk<__nv_bfloat16>(c, c->ws, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
             break;
         default:
-            e = run_chunk<float>(c, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
+            e = run_chunk<float>(c, c->ws, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
             break;
         }
         if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: kernel launch");
@@ -530,5 +527,308 @@ extern "C" int ldpc_prof_read(ldpc_code_t *c, ldpc_prof_t *out, int32_t reset) {
         }
         c->prof.clear();
     }
+    return LDPC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-code batches: the decodes of several codes (each with its own frame
+// count) as parallel branches of one CUDA graph, launched once per batch.
+// ---------------------------------------------------------------------------
+
+namespace ldpc {
+
+void free_workspace(Workspace &w) {
+    if (w.last_use) cudaEventSynchronize(w.last_use);
+    cudaFree(w.lamT);
+    cudaFree(w.app);
+    cudaFree(w.r);
+    cudaFree(w.done);
+    cudaFree(w.unsat);
+    cudaFree(w.stop_iter);
+    cudaFree(w.h_llr);
+    cudaFree(w.h_bits);
+    cudaFree(w.h_iters);
+    cudaFree(w.h_ok);
+    cudaFree(w.h_post);
+    if (w.last_use) cudaEventDestroy(w.last_use);
+    for (int h = 0; h < 2; ++h) {
+        if (w.half_stream[h]) cudaStreamDestroy(w.half_stream[h]);
+        if (w.join[h]) cudaEventDestroy(w.join[h]);
+    }
+    if (w.fork) cudaEventDestroy(w.fork);
+    if (w.phase) cudaEventDestroy(w.phase);
+    w = Workspace{};
+}
+
+struct BatchItem {
+    ldpc_code *code = nullptr;
+    int32_t F = 0;
+    ldpc_decode_opts_t opts{};
+    Workspace ws;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+static cudaError_t enqueue_item(BatchItem &it, int32_t max_iter, float l_max, const float *llr, uint8_t *bits,
+                                int32_t *iters, uint8_t *ok, float *post, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(it.code->mu);
+    switch (it.opts.msg_dtype) {
+    case LDPC_MSG_F16:
+        return run_chunk<__half>(it.code, it.ws, llr, it.F, max_iter, it.opts, l_max, bits, iters, ok, post, nullptr, s);
+    case LDPC_MSG_BF16:
+        return run_chunk<__nv_bfloat16>(it.code, it.ws, llr, it.F, max_iter, it.opts, l_max, bits, iters, ok, post,
+                                        nullptr, s);
+    default:
+        return run_chunk<float>(it.code, it.ws, llr, it.F, max_iter, it.opts, l_max, bits, iters, ok, post, nullptr, s);
+    }
+}
+
+}  // namespace ldpc
+
+struct ldpc_batch {
+    int device = 0;
+    int32_t max_iter = 0;
+    float l_max = 20.0f;
+    std::vector<ldpc::BatchItem> items;
+    cudaStream_t capture = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t last_run = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool warmed = false;
+    std::vector<const void *> key;  // the pointers the graph was captured with
+    int64_t kernels_per_run = 0;
+    std::mutex mu;
+};
+
+static void batch_free(ldpc_batch *b) {
+    DeviceGuard guard(b->device);
+    if (b->last_run) cudaEventSynchronize(b->last_run);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto &it : b->items) {
+        free_workspace(it.ws);
+        if (it.stream) cudaStreamDestroy(it.stream);
+        if (it.done) cudaEventDestroy(it.done);
+    }
+    if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->last_run) cudaEventDestroy(b->last_run);
+    delete b;
+}
+
+extern "C" int ldpc_batch_create(int32_t n_items, ldpc_code_t *const *codes, const int32_t *n_frames, int32_t max_iter,
+                                 const ldpc_decode_opts_t *opts, ldpc_batch_t **out) {
+    if (!out) return set_error(LDPC_EINVAL, "ldpc_batch_create: out is NULL");
+    *out = nullptr;
+    if (n_items <= 0 || !codes || !n_frames) return set_error(LDPC_EINVAL, "ldpc_batch_create: empty batch");
+    ldpc_decode_opts_t o = opts ? *opts : default_opts();
+    float l_max;
+    for (int32_t i = 0; i < n_items; ++i) {
+        int st = check_decode_args(codes[i], n_frames[i], max_iter, o, &l_max, "ldpc_batch_create");
+        if (st != LDPC_OK) return st;
+        if (n_frames[i] <= 0 || n_frames[i] > kMaxChunkFrames)
+            return set_error(LDPC_EINVAL, "ldpc_batch_create: item %d has %d frames, outside [1, %d]", i, n_frames[i],
+                             kMaxChunkFrames);
+        if (codes[i]->device != codes[0]->device)
+            return set_error(LDPC_EINVAL, "ldpc_batch_create: items on different devices");
+    }
+    if (o.profile || o.r_out) return set_error(LDPC_EINVAL, "ldpc_batch_create: profile and r_out are not available");
+    ldpc_batch *b = new (std::nothrow) ldpc_batch();
+    if (!b) return set_error(LDPC_ENOMEM, "ldpc_batch_create: out of host memory");
+    b->device = codes[0]->device;
+    b->max_iter = max_iter;
+    b->l_max = l_max;
+    DeviceGuard guard(b->device);
+    cudaError_t e = cudaSuccess;
+    b->items.resize(n_items);
+    for (int32_t i = 0; i < n_items && e == cudaSuccess; ++i) {
+        BatchItem &it = b->items[i];
+        it.code = codes[i];
+        it.F = n_frames[i];
+        it.opts = o;
+        it.opts.streams = 1;      // one branch per item; items overlap each other
+        it.opts.tile_frames = 0;
+        e = cudaStreamCreateWithFlags(&it.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&it.ws.last_use, cudaEventDisableTiming);
+        if (e == cudaSuccess) {
+            // room for the widest frame layout the tuner may pick (8 frames per lane)
+            int32_t Fp = (it.F + 255) / 256 * 256;
+            int st = ensure_workspace(it.code, it.ws, Fp, max_iter, msg_size(o.msg_dtype));
+            if (st != LDPC_OK) {
+                batch_free(b);
+                return st;
+            }
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->last_run, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        int st = cuda_error(e, "ldpc_batch_create");
+        batch_free(b);
+        return st;
+    }
+    *out = b;
+    return LDPC_OK;
+}
+
+extern "C" void ldpc_batch_destroy(ldpc_batch_t *b) {
+    if (b) batch_free(b);
+}
+
+// Enqueue every item on its own stream, forked from and joined into `s`.
+static cudaError_t batch_enqueue(ldpc_batch *b, const float *const *llr, uint8_t *const *bits, int32_t *const *iters,
+                                 uint8_t *const *ok, float *const *post, cudaStream_t s) {
+    cudaError_t e = cudaEventRecord(b->fork, s);
+    for (size_t i = 0; i < b->items.size() && e == cudaSuccess; ++i) {
+        BatchItem &it = b->items[i];
+        e = cudaStreamWaitEvent(it.stream, b->fork, 0);
+        if (e == cudaSuccess)
+            e = enqueue_item(it, b->max_iter, b->l_max, llr[i], bits[i], iters[i], ok[i], post ? post[i] : nullptr,
+                             it.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(it.done, it.stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, it.done, 0);
+    }
+    return e;
+}
+
+extern "C" int ldpc_batch_run(ldpc_batch_t *b, const float *const *llr, uint8_t *const *bits, int32_t *const *iters,
+                              uint8_t *const *syndrome_ok, float *const *post_llr, void *stream) {
+    if (!b || !llr || !bits || !iters || !syndrome_ok) return set_error(LDPC_EINVAL, "ldpc_batch_run: NULL argument");
+    for (size_t i = 0; i < b->items.size(); ++i)
+        if (!llr[i] || !bits[i] || !iters[i] || !syndrome_ok[i])
+            return set_error(LDPC_EINVAL, "ldpc_batch_run: NULL buffer for item %zu", i);
+    std::lock_guard<std::mutex> lock(b->mu);
+    DeviceGuard guard(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamWaitEvent(s, b->last_run, 0);
+    if (e != cudaSuccess) return cuda_error(e, "ldpc_batch_run: wait");
+    std::vector<const void *> key;
+    for (size_t i = 0; i < b->items.size(); ++i) {
+        key.push_back(llr[i]);
+        key.push_back(bits[i]);
+        key.push_back(iters[i]);
+        key.push_back(syndrome_ok[i]);
+        key.push_back(post_llr ? post_llr[i] : nullptr);
+    }
+    if (!b->warmed) {
+        // first run: direct launches (also performs every kernel's one-time set-up)
+        e = batch_enqueue(b, llr, bits, iters, syndrome_ok, post_llr, s);
+        if (e != cudaSuccess) return cuda_error(e, "ldpc_batch_run: launch");
+        b->warmed = true;
+    } else {
+        if (!b->exec || key != b->key) {
+            int64_t before = 0, after = 0;
+            for (auto &it : b->items) before += it.code->kernels_launched;
+            e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) e = batch_enqueue(b, llr, bits, iters, syndrome_ok, post_llr, b->capture);
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
+            if (e == cudaSuccess) e = e2;
+            if (e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return cuda_error(e, "ldpc_batch_run: graph capture");
+            }
+            for (auto &it : b->items) after += it.code->kernels_launched;
+            b->kernels_per_run = after - before;
+            if (b->exec) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(b->exec, g, &info) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(b->exec);
+                    b->exec = nullptr;
+                }
+            }
+            if (!b->exec && (e = cudaGraphInstantiate(&b->exec, g, 0)) != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return cuda_error(e, "ldpc_batch_run: graph instantiate");
+            }
+            if (b->graph) cudaGraphDestroy(b->graph);
+            b->graph = g;
+            b->key = key;
+        }
+        if ((e = cudaGraphLaunch(b->exec, s)) != cudaSuccess) return cuda_error(e, "ldpc_batch_run: graph launch");
+    }
+    if ((e = cudaEventRecord(b->last_run, s)) != cudaSuccess) return cuda_error(e, "ldpc_batch_run: record");
+    return LDPC_OK;
+}
+
+extern "C" int ldpc_batch_tune(ldpc_batch_t *b, const float *const *llr, void *stream) {
+    if (!b || !llr) return set_error(LDPC_EINVAL, "ldpc_batch_tune: NULL argument");
+    std::lock_guard<std::mutex> lock(b->mu);
+    DeviceGuard guard(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b->last_run);
+    if (e != cudaSuccess) return cuda_error(e, "ldpc_batch_tune: synchronize");
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    int status = LDPC_OK;
+    for (size_t i = 0; i < b->items.size() && status == LDPC_OK; ++i) {
+        BatchItem &it = b->items[i];
+        if (!llr[i]) {
+            status = set_error(LDPC_EINVAL, "ldpc_batch_tune: NULL llr for item %zu", i);
+            break;
+        }
+        uint8_t *bits = nullptr, *ok = nullptr;
+        int32_t *iters = nullptr;
+        if ((e = cudaMalloc(&bits, (size_t)it.F * it.code->n + 1)) != cudaSuccess ||
+            (e = cudaMalloc(&ok, (size_t)it.F)) != cudaSuccess ||
+            (e = cudaMalloc(&iters, sizeof(int32_t) * it.F)) != cudaSuccess) {
+            status = cuda_error(e, "ldpc_batch_tune: scratch outputs");
+        }
+        float best = 1e30f;
+        ldpc_decode_opts_t best_opts = it.opts;
+        const int32_t lanes[4] = {1, 2, 4, 8};
+        for (int li = 0; li < 4 && status == LDPC_OK; ++li) {
+            int32_t v = lanes[li];
+            int32_t Fp = (it.F + 32 * v - 1) / (32 * v) * (32 * v);
+            if (v > 1 && Fp - it.F > it.F / 4) continue;  // padding wider than a quarter of the batch
+            for (int32_t sched = 1; sched <= 2 && status == LDPC_OK; ++sched) {
+                it.opts.frames_per_lane = v;
+                it.opts.check_schedule = sched;
+                float ms = 0.0f;
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                    if (rep == 1) e = cudaEventRecord(t0, it.stream);
+                    if (e == cudaSuccess) e = enqueue_item(it, b->max_iter, b->l_max, llr[i], bits, iters, ok, nullptr,
+                                                           it.stream);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(t1, it.stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e != cudaSuccess) {
+                    status = cuda_error(e, "ldpc_batch_tune: trial");
+                    break;
+                }
+                if (ms < best) {
+                    best = ms;
+                    best_opts = it.opts;
+                }
+            }
+        }
+        it.opts = best_opts;
+        cudaFree(bits);
+        cudaFree(ok);
+        cudaFree(iters);
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    b->warmed = true;   // every candidate kernel has run once
+    if (b->exec) {      // schedules changed: capture again on the next run
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    return status;
+}
+
+extern "C" int ldpc_batch_info(const ldpc_batch_t *b, int32_t item, int32_t *frames_per_lane, int32_t *check_schedule,
+                               int64_t *kernels_per_run) {
+    if (!b || item < 0 || item >= (int32_t)b->items.size()) return set_error(LDPC_EINVAL, "ldpc_batch_info: bad item");
+    if (frames_per_lane) *frames_per_lane = b->items[item].opts.frames_per_lane;
+    if (check_schedule) *check_schedule = b->items[item].opts.check_schedule;
+    if (kernels_per_run) *kernels_per_run = b->kernels_per_run;
     return LDPC_OK;
 }

@@ -109,6 +109,8 @@ struct ProfRecord {
     cudaEvent_t start, stop;
 };
 
+void free_workspace(Workspace &w);
+
 // Thread-local error text.
 int set_error(int status, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *what);

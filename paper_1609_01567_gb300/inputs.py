@@ -297,3 +297,42 @@ def tree_code(n_target: int, seed: int, max_check_degree: int = 4) -> Code:
 def coo_code(m: int, n: int, rows, cols, name: str = "") -> Code:
     """A code from explicit COO lists (kept in the given order)."""
     return Code(m=m, n=n, rows=np.asarray(rows, dtype=np.int32), cols=np.asarray(cols, dtype=np.int32), name=name)
+
+
+# --- mixed-code workload: 8 codes of different lengths, rates and degrees --------
+
+MIXED_SPECS = (  # (n, k, name); the 8192-bit code carries a degree-64 variable and a degree-96 check
+    (576, 480, "n576_r5/6"),
+    (1152, 864, "n1152_r3/4"),
+    (2304, 1536, "n2304_r2/3"),
+    (4096, 2048, "n4096_r1/2"),
+    (8192, 6144, "n8192_r3/4_deg64_96"),
+    (16200, 5400, "n16200_r1/3"),
+    (32400, 21600, "n32400_r2/3"),
+    (64800, 54000, "n64800_r5/6"),
+)
+
+
+def mixed_codes() -> list[Code]:
+    """The eight seeded IRA codes of the mixed-code workload, shortest first.
+
+    Info-bit degrees {3: 0.8, 4: 0.2}; check degrees follow from the rate
+    (about 3-4 at rate 1/3 up to about 18 at rate 5/6). Code 4 (n = 8192) has
+    one information bit of degree 64 and one check of degree 96 (94 H1
+    sockets plus its two staircase ones).
+    """
+    codes = []
+    for idx, (n, k, name) in enumerate(MIXED_SPECS):
+        over_v = {0: 64} if n == 8192 else None
+        over_c = {5: 94} if n == 8192 else None
+        codes.append(ira_code(n, k, {3: 0.8, 4: 0.2}, seed=100 + idx, var_degree_overrides=over_v,
+                              check_h1_overrides=over_c, name=name))
+    return codes
+
+
+def zipf_frames(total: int, count: int, s: float = 1.1) -> list[int]:
+    """Split `total` frames over `count` ranks with Zipf(s) weights (rank 1
+    gets the most), by largest remainder."""
+    weights = {r: r ** (-s) for r in range(1, count + 1)}
+    split = largest_remainder(total, weights)
+    return [split[r] for r in range(1, count + 1)]

@@ -48,7 +48,8 @@ class ldpc_prof_t(ctypes.Structure):
 
 
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
-           "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_count_errors", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
+           "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_count_errors", "ldpc_batch_create",
+           "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info", "ldpc_batch_destroy", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
            "ldpc_version")
 
 _LIB = None
@@ -77,12 +78,19 @@ def library():
             lib.ldpc_gen_awgn.argtypes = [u64, i64, i32, i32, ctypes.c_float, vp, vp, vp]
             lib.ldpc_philox4x64_10.argtypes = [u64, u64, u64, u64, i64, vp, vp]
             lib.ldpc_count_errors.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
+            lib.ldpc_batch_create.argtypes = [i32, vp, vp, i32, ctypes.POINTER(ldpc_decode_opts_t), ctypes.POINTER(vp)]
+            lib.ldpc_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+            lib.ldpc_batch_tune.argtypes = [vp, vp, vp]
+            lib.ldpc_batch_info.argtypes = [vp, i32, vp, vp, vp]
+            lib.ldpc_batch_destroy.argtypes = [vp]
+            lib.ldpc_batch_destroy.restype = None
             lib.ldpc_prof_read.argtypes = [vp, ctypes.POINTER(ldpc_prof_t), i32]
             lib.ldpc_last_error.restype = ctypes.c_char_p
             lib.ldpc_version.restype = ctypes.c_char_p
             for name in ("ldpc_code_create", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode", "ldpc_decode_host",
                          "ldpc_decode_static",
-                         "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_count_errors"):
+                         "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_count_errors",
+                         "ldpc_batch_create", "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info"):
                 getattr(lib, name).restype = ctypes.c_int
             _LIB = lib
         return _LIB
@@ -330,6 +338,89 @@ def ldpc_prof_read(code: Code, reset: bool = True) -> dict:
     out = {k: {"launches": int(p.launches[i]), "total_ms": float(p.total_ms[i])} for i, k in enumerate(KERNEL_CLASSES)}
     out["kernels"] = int(p.kernels)
     return out
+
+
+class Batch:
+    """Owner of an ``ldpc_batch_t``: several codes decoded as one CUDA graph.
+
+    Keeps references to its codes (the batch borrows their tables) and to the
+    buffers of the last run (the captured graph points at them)."""
+
+    def __init__(self, handle, codes, frames):
+        self._h = handle
+        self.codes = list(codes)
+        self.frames = list(frames)
+        self._keep = None
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("batch is closed")
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            library().ldpc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+def ldpc_batch_create(codes, n_frames, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
+                      msg_dtype: str = "f32", frames_per_lane: int = 0, check_schedule: int = 0) -> Batch:
+    """A mixed-code batch over ``codes`` (``Code`` handles on one device)."""
+    hs = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
+    fr = (ctypes.c_int32 * len(codes))(*[int(f) for f in n_frames])
+    opts = _opts(early_exit, l_max, msg_dtype, False, None, frames_per_lane, check_schedule)
+    h = ctypes.c_void_p()
+    _check(library().ldpc_batch_create(len(codes), hs, fr, max_iter, ctypes.byref(opts), ctypes.byref(h)))
+    return Batch(h, codes, n_frames)
+
+
+def ldpc_batch_run(batch: Batch, llrs, outs=None, want_post: bool = False, stream=None):
+    """Decode every item (llrs: CUDA float32 [F_i, n_i] tensors). Returns a
+    list of output dicts; pass the same ``outs`` again to replay the graph."""
+    import torch
+    if outs is None:
+        outs = []
+        for c, f in zip(batch.codes, batch.frames):
+            dev = torch.device("cuda", c.device)
+            o = {"bits": torch.empty((f, c.n), dtype=torch.uint8, device=dev),
+                 "iters": torch.empty((f,), dtype=torch.int32, device=dev),
+                 "ok": torch.empty((f,), dtype=torch.uint8, device=dev)}
+            if want_post:
+                o["post"] = torch.empty((f, c.n), dtype=torch.float32, device=dev)
+            outs.append(o)
+    for c, f, l in zip(batch.codes, batch.frames, llrs):
+        _dev_ptr(l, torch.float32, (f, c.n), "llr", c.device)
+    posts = [o.get("post") for o in outs]
+    _check(library().ldpc_batch_run(batch.handle, _ptr_array(llrs), _ptr_array([o["bits"] for o in outs]),
+                                    _ptr_array([o["iters"] for o in outs]), _ptr_array([o["ok"] for o in outs]),
+                                    _ptr_array(posts) if any(p is not None for p in posts) else None,
+                                    _stream_handle(stream)))
+    batch._keep = (llrs, outs)
+    return outs
+
+
+def ldpc_batch_tune(batch: Batch, llrs, stream=None) -> None:
+    _check(library().ldpc_batch_tune(batch.handle, _ptr_array(llrs), _stream_handle(stream)))
+
+
+def ldpc_batch_info(batch: Batch, item: int) -> dict:
+    v, s, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(library().ldpc_batch_info(batch.handle, item, ctypes.byref(v), ctypes.byref(s), ctypes.byref(k)))
+    return {"frames_per_lane": v.value, "check_schedule": s.value, "kernels_per_run": k.value}
 
 
 def code_from_inputs(code, device: int = 0) -> Code:
