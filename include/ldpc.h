@@ -218,6 +218,66 @@ int ldpc_batch_info(const ldpc_batch_t *batch, int32_t item, int32_t *frames_per
 void ldpc_batch_destroy(ldpc_batch_t *batch);
 
 /*
+ * Decode server: continuous request batching over device-resident codes.
+ * Requests (a code index, n_frames frames, caller-owned device buffers laid
+ * out as in ldpc_decode) queue per code; a dispatcher thread hands the
+ * oldest queued requests of one code, up to max_batch_frames frames, to a
+ * free slot (a decode workspace with its own stream), gathers their LLRs,
+ * decodes, scatters the results back and completes the requests from a host
+ * callback. Several slots run at once, so requests that arrive while others
+ * are on the GPU are admitted as slots free up and their work overlaps. The
+ * slot count follows memory_budget (device bytes; admission by free memory)
+ * and max_slots; submits beyond max_pending_frames queued frames return
+ * LDPC_EBUSY. A request's results do not depend on the requests it was
+ * batched with. Buffers must stay valid until ldpc_server_wait returns for
+ * the request. All entry points are thread-safe.
+ */
+typedef struct ldpc_server ldpc_server_t;
+
+typedef struct {
+    int32_t max_batch_frames;   /* frames per batch, 1..8192 (0 = 1024); also the
+                                   largest request                              */
+    int32_t max_slots;          /* batches in flight at once (0 = 4)              */
+    int64_t memory_budget;      /* device bytes for the slots (0 = a quarter of
+                                   the free device memory at creation)          */
+    int64_t max_pending_frames; /* queued frames beyond which submits are refused
+                                   with LDPC_EBUSY (0 = 2^20)                   */
+    int32_t max_iter;           /* 0 = 50                                        */
+    int32_t early_exit;         /* as in ldpc_decode_opts_t                      */
+    float l_max;                /* <= 0 = 20                                     */
+    int32_t msg_dtype;          /* ldpc_msg_dtype                                */
+} ldpc_server_opts_t;
+
+typedef struct {
+    int32_t slots;         /* slots allocated                                    */
+    int64_t completed;     /* requests completed                                 */
+    int64_t frames;        /* frames completed                                   */
+    int64_t batches;       /* batches dispatched                                 */
+    int64_t queued_frames; /* frames waiting for a slot                          */
+    int64_t info_bits;     /* information bits of the dispatched frames          */
+} ldpc_server_stats_t;
+
+/* Start a server over n_codes code handles (one device; the server borrows
+ * them: destroy the server first). Allocates the slots. */
+int ldpc_server_create(int32_t n_codes, ldpc_code_t *const *codes, const ldpc_server_opts_t *opts,
+                       ldpc_server_t **out);
+
+/* Queue a request; *request_id identifies it for ldpc_server_wait. post_llr
+ * may be NULL. Errors: LDPC_EINVAL, LDPC_EBUSY (queue full). */
+int ldpc_server_submit(ldpc_server_t *server, int32_t code_index, const float *llr, int32_t n_frames, uint8_t *bits,
+                       int32_t *iters, uint8_t *syndrome_ok, float *post_llr, uint64_t *request_id);
+
+/* Wait until the request completes (timeout_ms < 0: no limit; else
+ * LDPC_ETIMEOUT when it has not completed in time) and release its record;
+ * *latency_ms (optional) receives submit-to-completion time. */
+int ldpc_server_wait(ldpc_server_t *server, uint64_t request_id, int32_t timeout_ms, double *latency_ms);
+
+int ldpc_server_stats(ldpc_server_t *server, ldpc_server_stats_t *out);
+
+/* Finish the queued work, stop the dispatcher and free the slots. */
+void ldpc_server_destroy(ldpc_server_t *server);
+
+/*
  * ldpc_decode for callers that cannot allocate device memory when they
  * decode: a latency-bound receive chain that must not stall on cudaMalloc
  * (which may synchronise the device), or a plug-in confined to another

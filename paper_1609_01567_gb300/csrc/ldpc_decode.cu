@@ -146,8 +146,9 @@ static cudaError_t grow(T **p, size_t count) {
     return cudaMalloc(p, sizeof(T) * std::max<size_t>(count, 1));
 }
 
-// Device buffers for Fp frames and max_iter iterations (grown, never shrunk).
-static int ensure_workspace(ldpc_code *c, Workspace &w, int32_t Fp, int32_t max_iter, int msg_bytes) {
+// Device buffers for Fp frames and max_iter iterations of a code with n
+// variables and E edges (grown, never shrunk).
+static int ensure_workspace_dims(Workspace &w, int32_t n, int64_t E, int32_t Fp, int32_t max_iter, int msg_bytes) {
     bool need_frames = Fp > w.fp_cap || msg_bytes > w.msg_bytes;
     bool need_iters = need_frames || max_iter > w.iter_cap;
     if (!need_frames && !need_iters) return LDPC_OK;
@@ -156,9 +157,9 @@ static int ensure_workspace(ldpc_code *c, Workspace &w, int32_t Fp, int32_t max_
     if (need_frames) {
         int32_t cap = std::max(Fp, w.fp_cap);
         int mb = std::max(msg_bytes, w.msg_bytes);
-        if ((e = grow(&w.lamT, (size_t)c->n * cap)) != cudaSuccess ||
-            (e = grow(&w.app, (size_t)c->n * cap)) != cudaSuccess ||
-            (e = grow(reinterpret_cast<char **>(&w.r), (size_t)c->E * cap * mb)) != cudaSuccess ||
+        if ((e = grow(&w.lamT, (size_t)n * cap)) != cudaSuccess ||
+            (e = grow(&w.app, (size_t)n * cap)) != cudaSuccess ||
+            (e = grow(reinterpret_cast<char **>(&w.r), (size_t)E * cap * mb)) != cudaSuccess ||
             (e = grow(&w.done, (size_t)cap / 32)) != cudaSuccess ||
             (e = grow(&w.stop_iter, (size_t)cap)) != cudaSuccess) {
             w.fp_cap = 0;
@@ -166,7 +167,7 @@ static int ensure_workspace(ldpc_code *c, Workspace &w, int32_t Fp, int32_t max_
             return cuda_error(e, "ldpc_decode: workspace allocation");
         }
         // padding frames read finite posteriors
-        if ((e = cudaMemset(w.app, 0, sizeof(float) * std::max<size_t>((size_t)c->n * cap, 1))) != cudaSuccess)
+        if ((e = cudaMemset(w.app, 0, sizeof(float) * std::max<size_t>((size_t)n * cap, 1))) != cudaSuccess)
             return cuda_error(e, "ldpc_decode: workspace init");
         w.fp_cap = cap;
         w.msg_bytes = mb;
@@ -178,6 +179,10 @@ static int ensure_workspace(ldpc_code *c, Workspace &w, int32_t Fp, int32_t max_
     }
     w.iter_cap = icap;
     return LDPC_OK;
+}
+
+static int ensure_workspace(ldpc_code *c, Workspace &w, int32_t Fp, int32_t max_iter, int msg_bytes) {
+    return ensure_workspace_dims(w, c->n, c->E, Fp, max_iter, msg_bytes);
 }
 
 static cudaEvent_t take_event(ldpc_code *c) {
@@ -832,3 +837,31 @@ extern "C" int ldpc_batch_info(const ldpc_batch_t *b, int32_t item, int32_t *fra
     if (kernels_per_run) *kernels_per_run = b->kernels_per_run;
     return LDPC_OK;
 }
+
+namespace ldpc {
+
+// Entry points for the serving runtime (ldpc_server.cpp).
+int workspace_reserve(Workspace &w, int32_t n, int64_t E, int32_t Fp, int32_t max_iter, int msg_bytes) {
+    return ensure_workspace_dims(w, n, E, Fp, max_iter, msg_bytes);
+}
+
+cudaError_t enqueue_decode(ldpc_code *c, Workspace &w, const float *llr, int32_t F, int32_t max_iter,
+                           const ldpc_decode_opts_t &o, float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok,
+                           float *post, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(c->mu);
+    switch (o.msg_dtype) {
+    case LDPC_MSG_F16:
+        return run_chunk<__half>(c, w, llr, F, max_iter, o, l_max, bits, iters, ok, post, nullptr, s);
+    case LDPC_MSG_BF16:
+        return run_chunk<__nv_bfloat16>(c, w, llr, F, max_iter, o, l_max, bits, iters, ok, post, nullptr, s);
+    default:
+        return run_chunk<float>(c, w, llr, F, max_iter, o, l_max, bits, iters, ok, post, nullptr, s);
+    }
+}
+
+int check_opts(const ldpc_code *c, int32_t F, int32_t max_iter, const ldpc_decode_opts_t &o, float *l_max,
+               const char *fn) {
+    return check_decode_args(c, F, max_iter, o, l_max, fn);
+}
+
+}  // namespace ldpc

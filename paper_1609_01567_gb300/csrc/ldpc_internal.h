@@ -110,6 +110,12 @@ struct ProfRecord {
 };
 
 void free_workspace(Workspace &w);
+int workspace_reserve(Workspace &w, int32_t n, int64_t E, int32_t Fp, int32_t max_iter, int msg_bytes);
+cudaError_t enqueue_decode(ldpc_code *c, Workspace &w, const float *llr, int32_t F, int32_t max_iter,
+                           const ldpc_decode_opts_t &o, float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok,
+                           float *post, cudaStream_t s);
+int check_opts(const ldpc_code *c, int32_t F, int32_t max_iter, const ldpc_decode_opts_t &o, float *l_max,
+               const char *fn);
 
 // Thread-local error text.
 int set_error(int status, const char *fmt, ...);

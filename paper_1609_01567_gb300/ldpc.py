@@ -43,13 +43,25 @@ class ldpc_decode_opts_t(ctypes.Structure):
                 ("check_schedule", ctypes.c_int32), ("streams", ctypes.c_int32), ("tile_frames", ctypes.c_int32)]
 
 
+class ldpc_server_opts_t(ctypes.Structure):
+    _fields_ = [("max_batch_frames", ctypes.c_int32), ("max_slots", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
+                ("max_pending_frames", ctypes.c_int64), ("max_iter", ctypes.c_int32), ("early_exit", ctypes.c_int32),
+                ("l_max", ctypes.c_float), ("msg_dtype", ctypes.c_int32)]
+
+
+class ldpc_server_stats_t(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("completed", ctypes.c_int64), ("frames", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("queued_frames", ctypes.c_int64), ("info_bits", ctypes.c_int64)]
+
+
 class ldpc_prof_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 7), ("total_ms", ctypes.c_double * 7), ("kernels", ctypes.c_int64)]
 
 
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
            "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_count_errors", "ldpc_batch_create",
-           "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info", "ldpc_batch_destroy", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
+           "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info", "ldpc_batch_destroy", "ldpc_server_create",
+           "ldpc_server_submit", "ldpc_server_wait", "ldpc_server_stats", "ldpc_server_destroy", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
            "ldpc_version")
 
 _LIB = None
@@ -84,13 +96,20 @@ def library():
             lib.ldpc_batch_info.argtypes = [vp, i32, vp, vp, vp]
             lib.ldpc_batch_destroy.argtypes = [vp]
             lib.ldpc_batch_destroy.restype = None
+            lib.ldpc_server_create.argtypes = [i32, vp, ctypes.POINTER(ldpc_server_opts_t), ctypes.POINTER(vp)]
+            lib.ldpc_server_submit.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+            lib.ldpc_server_wait.argtypes = [vp, ctypes.c_uint64, i32, ctypes.POINTER(ctypes.c_double)]
+            lib.ldpc_server_stats.argtypes = [vp, ctypes.POINTER(ldpc_server_stats_t)]
+            lib.ldpc_server_destroy.argtypes = [vp]
+            lib.ldpc_server_destroy.restype = None
             lib.ldpc_prof_read.argtypes = [vp, ctypes.POINTER(ldpc_prof_t), i32]
             lib.ldpc_last_error.restype = ctypes.c_char_p
             lib.ldpc_version.restype = ctypes.c_char_p
             for name in ("ldpc_code_create", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode", "ldpc_decode_host",
                          "ldpc_decode_static",
                          "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_count_errors",
-                         "ldpc_batch_create", "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info"):
+                         "ldpc_batch_create", "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info",
+                         "ldpc_server_create", "ldpc_server_submit", "ldpc_server_wait", "ldpc_server_stats"):
                 getattr(lib, name).restype = ctypes.c_int
             _LIB = lib
         return _LIB
@@ -421,6 +440,84 @@ def ldpc_batch_info(batch: Batch, item: int) -> dict:
     v, s, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
     _check(library().ldpc_batch_info(batch.handle, item, ctypes.byref(v), ctypes.byref(s), ctypes.byref(k)))
     return {"frames_per_lane": v.value, "check_schedule": s.value, "kernels_per_run": k.value}
+
+
+class Server:
+    """Owner of an ``ldpc_server_t`` (continuous request batching)."""
+
+    def __init__(self, handle, codes):
+        self._h = handle
+        self.codes = list(codes)
+        self._live = {}  # request id -> tensors kept alive until waited
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("server is closed")
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            library().ldpc_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ldpc_server_create(codes, *, max_batch_frames: int = 1024, max_slots: int = 4, memory_budget: int = 0,
+                       max_pending_frames: int = 0, max_iter: int = 50, early_exit: bool = True, l_max: float = 20.0,
+                       msg_dtype: str = "f16") -> Server:
+    hs = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
+    o = ldpc_server_opts_t(max_batch_frames=max_batch_frames, max_slots=max_slots, memory_budget=memory_budget,
+                           max_pending_frames=max_pending_frames, max_iter=max_iter, early_exit=1 if early_exit else 0,
+                           l_max=float(l_max), msg_dtype=LDPC_MSG[msg_dtype])
+    h = ctypes.c_void_p()
+    _check(library().ldpc_server_create(len(codes), hs, ctypes.byref(o), ctypes.byref(h)))
+    return Server(h, codes)
+
+
+def ldpc_server_submit(server: Server, code_index: int, llr, out: dict | None = None, want_post: bool = False) -> tuple:
+    """Queue ``llr`` (CUDA float32 [F, n]) for code ``code_index``; returns
+    (request id, output dict filled when the request completes)."""
+    import torch
+    if not 0 <= code_index < len(server.codes):
+        raise ValueError(f"code_index {code_index} outside [0, {len(server.codes)})")
+    c = server.codes[code_index]
+    f = int(llr.shape[0])
+    dev = torch.device("cuda", c.device)
+    o = dict(out or {})
+    o.setdefault("bits", torch.empty((f, c.n), dtype=torch.uint8, device=dev))
+    o.setdefault("iters", torch.empty((f,), dtype=torch.int32, device=dev))
+    o.setdefault("ok", torch.empty((f,), dtype=torch.uint8, device=dev))
+    if want_post:
+        o.setdefault("post", torch.empty((f, c.n), dtype=torch.float32, device=dev))
+    rid = ctypes.c_uint64()
+    _check(library().ldpc_server_submit(
+        server.handle, code_index, _dev_ptr(llr, torch.float32, (f, c.n), "llr", c.device), f,
+        _dev_ptr(o["bits"], torch.uint8, (f, c.n), "bits", c.device),
+        _dev_ptr(o["iters"], torch.int32, (f,), "iters", c.device), _dev_ptr(o["ok"], torch.uint8, (f,), "ok", c.device),
+        _dev_ptr(o.get("post"), torch.float32, (f, c.n), "post", c.device) if want_post else None, ctypes.byref(rid)))
+    server._live[rid.value] = (llr, o)
+    return rid.value, o
+
+
+def ldpc_server_wait(server: Server, request_id: int, timeout_ms: int = -1) -> float:
+    """Wait for a request; returns its submit-to-completion latency in ms."""
+    lat = ctypes.c_double()
+    _check(library().ldpc_server_wait(server.handle, request_id, timeout_ms, ctypes.byref(lat)))
+    server._live.pop(request_id, None)
+    return lat.value
+
+
+def ldpc_server_stats(server: Server) -> dict:
+    st = ldpc_server_stats_t()
+    _check(library().ldpc_server_stats(server.handle, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in ldpc_server_stats_t._fields_}
 
 
 def code_from_inputs(code, device: int = 0) -> Code:
