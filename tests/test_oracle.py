@@ -254,3 +254,14 @@ def test_awgn_frames_are_independent_of_batching(oracle_mod):
     whole = oracle_mod.gen_awgn(3, 100, 10, 37, s2)
     part = oracle_mod.gen_awgn(3, 104, 3, 37, s2)
     np.testing.assert_array_equal(whole[4:7], part)
+
+
+def test_paper_sweep_stand_in_codes_have_four_edges_per_bit(oracle_mod):
+    """The Table 3 stand-ins: rate 1/2 and E = 4n - 1 (the paper lists 4n)."""
+    from paper_1609_01567_gb300 import sweep
+    for n in (256, 512, 4096):
+        code = sweep.stand_in_code(n)
+        assert code.n == n and code.m == n // 2 and code.n_edges == 4 * n - 1
+        cw = I.encode_ira(code, I.random_info(3, code.k, seed=n))
+        assert np.all(oracle_mod.syndrome_weight(code, cw) == 0)
+    assert sorted(sweep.PAPER_TABLE3_SECONDS) == [2 ** p for p in range(8, 19)]
