@@ -40,6 +40,12 @@
  *   of bit pass, check pass, estimation, syndrome test. With early exit off
  *   every frame runs all max_iter iterations and reports the final syndrome.
  *
+ *   Min-sum family (named by the paper as a derived algorithm the same
+ *   edge-level parallel scheme supports; not part of its exact SP rule):
+ *   |r_ij| = min(L_MAX, max(alpha * min_{j' in N_i \ j} |q_ij'| - beta, 0)),
+ *   same sign rule; alpha < 1 is the normalised, beta > 0 the offset variant.
+ *   An empty minimum (degree-1 check) is L_MAX.
+ *
  *   Channel (BER-simulator section, Eqs. 3-4): x = 2c - 1, y = x + sigma z,
  *   lambda = 2 y / sigma^2, with z from Philox-4x64-10 (Salmon et al., SC'11)
  *   and the Box-Muller transform.
@@ -120,6 +126,33 @@ static double phi_hat(double x, double l_max) {
     return phi(x);
 }
 
+/* Check rule selection: 0 = sum-product, 1 = min-sum family. */
+typedef struct {
+    int rule;
+    double alpha, beta;
+} orc_rule;
+
+/* Min-sum check rule for one check. */
+static void check_update_min_sum(const orc_graph *g, int32_t i, const double *q, double *r, double l_max,
+                                 const orc_rule *rule, int *one) {
+    int64_t b = g->cstart[i], d = g->cstart[i + 1] - b;
+    for (int64_t k = 0; k < d; ++k) one[k] = q[g->cedge[b + k]] > 0.0;
+    for (int64_t k = 0; k < d; ++k) {
+        double m = l_max;
+        int parity = 0;
+        for (int64_t k2 = 0; k2 < d; ++k2) {
+            if (k2 == k) continue;
+            double a = fabs(q[g->cedge[b + k2]]);
+            if (a < m) m = a;
+            parity ^= one[k2];
+        }
+        double a = rule->alpha * m - rule->beta;
+        if (a < 0.0) a = 0.0;
+        if (a > l_max) a = l_max;
+        r[g->cedge[b + k]] = parity ? a : -a;
+    }
+}
+
 /* Check-node rule for one check: r[e] for every e in N_i from q[e]. */
 static void check_update(const orc_graph *g, int32_t i, const double *q, double *r, double l_max,
                          double *mag, int *one) {
@@ -147,7 +180,8 @@ static void check_update(const orc_graph *g, int32_t i, const double *q, double 
  * Otherwise q_e = lambda_j + sum over the other edges of j of r_prev.
  * Writes r_next [E], app [n], chat [n] and returns the syndrome weight. */
 static int64_t sp_pass(const orc_graph *g, const double *lam, const double *r_prev, double *r_next,
-                       double *app, uint8_t *chat, double l_max, double *q, double *mag, int *one) {
+                       double *app, uint8_t *chat, double l_max, const orc_rule *rule, double *q, double *mag,
+                       int *one) {
     for (int32_t j = 0; j < g->n; ++j) {
         for (int64_t e = g->vstart[j]; e < g->vstart[j + 1]; ++e) {
             double v = lam[j];
@@ -157,7 +191,12 @@ static int64_t sp_pass(const orc_graph *g, const double *lam, const double *r_pr
             q[e] = v;
         }
     }
-    for (int32_t i = 0; i < g->m; ++i) check_update(g, i, q, r_next, l_max, mag, one);
+    for (int32_t i = 0; i < g->m; ++i) {
+        if (rule && rule->rule == 1)
+            check_update_min_sum(g, i, q, r_next, l_max, rule, one);
+        else
+            check_update(g, i, q, r_next, l_max, mag, one);
+    }
     for (int32_t j = 0; j < g->n; ++j) {
         double v = lam[j];
         for (int64_t e = g->vstart[j]; e < g->vstart[j + 1]; ++e) v += r_next[e];
@@ -190,8 +229,11 @@ static int64_t max_check_degree(const orc_graph *g) {
  * Returns 0, or -1 on bad input / allocation failure. */
 int orc_decode(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t *cols,
                const double *lam, int32_t n_frames, int32_t max_iter, int32_t early_exit, double l_max,
-               uint8_t *bits, int32_t *iters, uint8_t *ok, double *post, double *r_out, int32_t n_threads) {
+               uint8_t *bits, int32_t *iters, uint8_t *ok, double *post, double *r_out, int32_t n_threads,
+               int32_t check_rule, double alpha, double beta) {
     if (m < 0 || n < 0 || E < 0 || n_frames < 0 || max_iter < 0 || !(l_max > 0.0)) return -1;
+    if (check_rule < 0 || check_rule > 1 || !(alpha > 0.0) || beta < 0.0) return -1;
+    orc_rule rule = {check_rule, alpha, beta};
     orc_graph g;
     if (graph_build(m, n, E, rows, cols, &g)) return -1;
     int64_t dmax = max_check_degree(&g);
@@ -215,11 +257,11 @@ int orc_decode(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32
             const double *lf = lam + (size_t)f * n;
             double *r_cur = ra, *r_new = rb;
             /* first check pass, estimation and syndrome test (before the loop) */
-            int64_t w = sp_pass(&g, lf, NULL, r_cur, app, chat, l_max, q, mag, one);
+            int64_t w = sp_pass(&g, lf, NULL, r_cur, app, chat, l_max, &rule, q, mag, one);
             int32_t it_done = 0;
             int stopped = early_exit && w == 0;
             for (int32_t it = 1; it <= max_iter && !stopped; ++it) {
-                w = sp_pass(&g, lf, r_cur, r_new, app, chat, l_max, q, mag, one);
+                w = sp_pass(&g, lf, r_cur, r_new, app, chat, l_max, &rule, q, mag, one);
                 double *t = r_cur; r_cur = r_new; r_new = t;
                 it_done = it;
                 if (early_exit && w == 0) stopped = 1;
@@ -242,8 +284,11 @@ int orc_decode(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32
  * one iteration at a time from its own state. */
 int orc_pass(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t *cols,
              const double *lam, int32_t n_frames, const double *r_prev, double l_max,
-             double *r_next, double *app, uint8_t *bits, int64_t *weight, int32_t n_threads) {
+             double *r_next, double *app, uint8_t *bits, int64_t *weight, int32_t n_threads,
+             int32_t check_rule, double alpha, double beta) {
     if (m < 0 || n < 0 || E < 0 || n_frames < 0 || !(l_max > 0.0)) return -1;
+    if (check_rule < 0 || check_rule > 1 || !(alpha > 0.0) || beta < 0.0) return -1;
+    orc_rule rule = {check_rule, alpha, beta};
     orc_graph g;
     if (graph_build(m, n, E, rows, cols, &g)) return -1;
     int64_t dmax = max_check_degree(&g);
@@ -260,8 +305,8 @@ int orc_pass(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t
             failed = 1;
         } else {
             weight[f] = sp_pass(&g, lam + (size_t)f * n, r_prev ? r_prev + (size_t)f * E : NULL,
-                                r_next + (size_t)f * E, app + (size_t)f * n, bits + (size_t)f * n, l_max, q,
-                                mag, one);
+                                r_next + (size_t)f * E, app + (size_t)f * n, bits + (size_t)f * n, l_max, &rule,
+                                q, mag, one);
         }
         free(q); free(mag); free(one);
     }

@@ -265,3 +265,51 @@ def test_paper_sweep_stand_in_codes_have_four_edges_per_bit(oracle_mod):
         cw = I.encode_ira(code, I.random_info(3, code.k, seed=n))
         assert np.all(oracle_mod.syndrome_weight(code, cw) == 0)
     assert sorted(sweep.PAPER_TABLE3_SECONDS) == [2 ** p for p in range(8, 19)]
+
+
+# --- min-sum family (a derived algorithm the paper names) -------------------------
+
+def max_log_parity(lam):
+    """Brute-force max-log LLR of each bit of one parity check: over the
+    other bits' configurations x with the right parity, max sum x*lambda for
+    c_j = 1 minus the same for c_j = 0."""
+    import itertools
+    f, d = lam.shape
+    out = np.zeros_like(lam)
+    for j in range(d):
+        others = [t for t in range(d) if t != j]
+        best = {0: np.full(f, -np.inf), 1: np.full(f, -np.inf)}
+        for x in itertools.product((0, 1), repeat=d - 1):
+            par = sum(x) % 2  # c_j must equal the parity of the others
+            score = sum(lam[:, t] * xi for t, xi in zip(others, x))
+            best[par] = np.maximum(best[par], score)
+        out[:, j] = best[1] - best[0]
+    return out
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 6])
+def test_min_sum_is_max_log_on_one_check(oracle_mod, d):
+    code = I.coo_code(1, d, [0] * d, list(range(d)))
+    lam = np.random.default_rng(d).normal(0.0, 3.0, size=(25, d))
+    out = oracle_mod.decode(code, lam, 0, early_exit=False, l_max=60.0, rule="min_sum")
+    np.testing.assert_allclose(out["post"] - lam, max_log_parity(lam), rtol=1e-12, atol=1e-12)
+
+
+def test_min_sum_variants_and_bounds(oracle_mod):
+    """Degree-2 checks: min-sum equals sum-product. Normalised and offset
+    variants scale and shift the plain messages; min-sum magnitudes never
+    fall below the sum-product ones on the first pass."""
+    code2 = I.coo_code(1, 2, [0, 0], [0, 1])
+    lam2 = np.random.default_rng(1).normal(0.0, 4.0, size=(30, 2))
+    sp = oracle_mod.decode(code2, lam2, 0, early_exit=False)
+    ms = oracle_mod.decode(code2, lam2, 0, early_exit=False, rule="min_sum")
+    np.testing.assert_allclose(ms["post"], sp["post"], rtol=1e-12, atol=1e-9)
+    code = I.small_code_n1008()
+    lam = I.gaussian_llr(np.zeros((6, code.n), np.uint8), I.sigma2_from_ebn0(1.0, 0.5), seed=2).astype(np.float64)
+    plain = oracle_mod.sp_pass(code, lam, rule="min_sum")["r"]
+    norm = oracle_mod.sp_pass(code, lam, rule="min_sum", alpha=0.75)["r"]
+    off = oracle_mod.sp_pass(code, lam, rule="min_sum", beta=0.5)["r"]
+    np.testing.assert_allclose(norm, 0.75 * plain, rtol=1e-14)
+    np.testing.assert_allclose(off, np.sign(plain) * np.maximum(np.abs(plain) - 0.5, 0.0), rtol=1e-14, atol=1e-15)
+    exact = oracle_mod.sp_pass(code, lam)["r"]
+    assert np.all(np.abs(plain) >= np.abs(exact) - 1e-12)
