@@ -146,7 +146,17 @@ typedef struct {
                            alternate between the two streams), so that one
                            tile's working set can stay in L2; 0 = one tile per
                            stream. Results do not depend on any tuning field */
+    int32_t check_rule; /* LDPC_RULE_SUM_PRODUCT (0, the paper's exact rule)
+                           or LDPC_RULE_MIN_SUM (1): |r| = clamp(alpha m -
+                           beta, 0, L_MAX), m the smallest other |q|, same
+                           signs -- plain (alpha 1, beta 0), normalised
+                           (alpha < 1) or offset (beta > 0) min-sum, a
+                           derived algorithm the paper names              */
+    float rule_alpha;   /* min-sum scale; <= 0 selects 1                   */
+    float rule_beta;    /* min-sum offset, >= 0                            */
 } ldpc_decode_opts_t;
+
+enum { LDPC_RULE_SUM_PRODUCT = 0, LDPC_RULE_MIN_SUM = 1 };
 
 /*
  * Decode n_frames frames.

@@ -264,6 +264,9 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     a.check_schedule = o.check_schedule;
     a.f_begin = 0;
     a.f_count = Fp;
+    a.check_rule = o.check_rule;
+    a.ms_alpha = o.rule_alpha > 0.0f ? o.rule_alpha : 1.0f;
+    a.ms_beta = o.rule_beta;
 
     Launcher L{c, s, o.profile != 0};
     cudaError_t e;
@@ -396,6 +399,10 @@ static int check_decode_args(const ldpc_code *c, int32_t F, int32_t max_iter, co
         return set_error(LDPC_EINVAL, "%s: frames_per_lane=%d not in {0, 1, 2, 4, 8}", fn, o.frames_per_lane);
     if (o.streams < 0 || o.streams > 2) return set_error(LDPC_EINVAL, "%s: streams=%d not in {0, 1, 2}", fn, o.streams);
     if (o.tile_frames < 0) return set_error(LDPC_EINVAL, "%s: tile_frames=%d < 0", fn, o.tile_frames);
+    if (o.check_rule != LDPC_RULE_SUM_PRODUCT && o.check_rule != LDPC_RULE_MIN_SUM)
+        return set_error(LDPC_EINVAL, "%s: unknown check_rule %d", fn, o.check_rule);
+    if (!(o.rule_beta >= 0.0f) || !std::isfinite(o.rule_alpha))
+        return set_error(LDPC_EINVAL, "%s: rule_beta must be >= 0 and rule_alpha finite", fn);
     if (o.msg_dtype != LDPC_MSG_F32 && o.msg_dtype != LDPC_MSG_F16 && o.msg_dtype != LDPC_MSG_BF16)
         return set_error(LDPC_EINVAL, "%s: unknown msg_dtype %d", fn, o.msg_dtype);
     *l_max_out = l_max;

@@ -71,6 +71,9 @@ struct PassArgs {
     int32_t check_schedule;  // 0 auto, 1 direct loads, 2 shared-memory pipeline
     int32_t f_begin;     // first frame of the range this launch covers (a multiple of 32 V)
     int32_t f_count;     // frames in that range (a multiple of 32 V)
+    int32_t check_rule;  // 0 sum-product, 1 min-sum family
+    float ms_alpha;      // min-sum scale
+    float ms_beta;       // min-sum offset
 };
 
 template <typename M>

@@ -445,79 +445,142 @@ __device__ __forceinline__ void or_frame_bits(uint32_t *row, int g, int lane, co
 // (or lambda_j on the first pass), rv = the previous message r_ij (unused on
 // the first pass). Writes the d new messages to rows out + k * Fp and ors the
 // check's syndrome of the previous hard decision into unsat.
+// The min-sum family for one check of degree d <= D (a derived algorithm the
+// paper names, not its exact rule): |r_k| = clamp(alpha m_k - beta, 0, L_MAX)
+// with m_k the smallest |q| of the other inputs (L_MAX when there is none),
+// found from the two smallest magnitudes and the position of the smallest;
+// same sign rule as sum-product.
 template <int D, int V, typename M, typename Load>
-__device__ __forceinline__ void check_node(int d, bool first, bool syn, Load &&load, M *out, size_t Fp,
-                                           const PassArgs &a, bool (&unsat)[V]) {
-    float dc[D][V];    // D_k = 1 - tanh(|q_k| / 2)
-    uint32_t ones[V];  // bit k: input k says "bit 1" (q > 0)
-    uint32_t z[V];
+__device__ __forceinline__ void min_sum_node(int d, bool first, bool syn, Load &&load, M *out, size_t Fp,
+                                             const PassArgs &a, bool (&unsat)[V]) {
+    float m1[V], m2[V];
+    int idx[V];
+    uint32_t ones[V], z[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) ones[v] = z[v] = 0u;
+    for (int v = 0; v < V; ++v) {
+        m1[v] = m2[v] = a.l_max;
+        idx[v] = -1;
+        ones[v] = z[v] = 0u;
+    }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         if (k < d) {
             float av[V], rv[V];
             load(k, av, rv);
-            if (syn) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) z[v] ^= av[v] > 0.0f ? 1u : 0u;
-            }
-            if (!first) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) av[v] = av[v] - rv[v];
-            }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                ones[v] |= (av[v] > 0.0f ? 1u : 0u) << k;
-                dc[k][v] = fabsf(av[v]);
+                if (syn) z[v] ^= av[v] > 0.0f ? 1u : 0u;
+                const float q = first ? av[v] : av[v] - rv[v];
+                ones[v] |= (q > 0.0f ? 1u : 0u) << k;
+                const float x = fminf(fabsf(q), a.l_max);
+                if (x < m1[v]) {
+                    m2[v] = m1[v];
+                    m1[v] = x;
+                    idx[v] = k;
+                } else if (x < m2[v]) {
+                    m2[v] = x;
+                }
             }
-            vtanh_complement<V>(dc[k], a.l_max, a.phi_lmax);
-        } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v) dc[k][v] = 0.0f;  // T = 1: neutral
         }
     }
-#pragma unroll
-    for (int v = 0; v < V; ++v) unsat[v] |= z[v] != 0u;
-    // complements of the suffix products, then a running prefix
-    float csuf[D][V];
-    {
-        float cr[V], pr[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            cr[v] = 0.0f;
-            pr[v] = 1.0f;
-        }
-#pragma unroll
-        for (int k = D - 1; k >= 0; --k) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) csuf[k][v] = cr[v];
-            vfma<V>(cr, pr, dc[k], cr);
-            vscale_by_tanh<V>(pr, dc[k]);
-        }
-    }
-    // output k is negative (bit-0 message) iff the other inputs hold an even
-    // number of ones, i.e. iff input k's bit equals the total parity
-    float cp[V], pp[V];
     uint32_t neg[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        cp[v] = 0.0f;
-        pp[v] = 1.0f;
+        unsat[v] |= z[v] != 0u;
         neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
     }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         if (k < d) {
             float o[V];
-            vfma<V>(o, pp, csuf[k], cp);  // C of all inputs but k
-            vmag_of_complement<V>(o, a.c_min, a.c_max);
 #pragma unroll
-            for (int v = 0; v < V; ++v)
-                o[v] = __int_as_float(__float_as_int(o[v]) | (int)((neg[v] << (31 - k)) & 0x80000000u));
+            for (int v = 0; v < V; ++v) {
+                const float m = idx[v] == k ? m2[v] : m1[v];
+                const float mag = fminf(fmaxf(fmaf(a.ms_alpha, m, -a.ms_beta), 0.0f), a.l_max);
+                o[v] = __int_as_float(__float_as_int(mag) | (int)((neg[v] << (31 - k)) & 0x80000000u));
+            }
             store_v<V, M>(out + (size_t)k * Fp, o);
-            vfma<V>(cp, pp, dc[k], cp);
-            vscale_by_tanh<V>(pp, dc[k]);
+        }
+    }
+}
+
+template <int D, int V, typename M, int RULE, typename Load>
+__device__ __forceinline__ void check_node(int d, bool first, bool syn, Load &&load, M *out, size_t Fp,
+                                           const PassArgs &a, bool (&unsat)[V]) {
+    if constexpr (RULE == 1) {
+        min_sum_node<D, V, M>(d, first, syn, load, out, Fp, a, unsat);
+    } else {
+        float dc[D][V];    // D_k = 1 - tanh(|q_k| / 2)
+        uint32_t ones[V];  // bit k: input k says "bit 1" (q > 0)
+        uint32_t z[V];
+    #pragma unroll
+        for (int v = 0; v < V; ++v) ones[v] = z[v] = 0u;
+    #pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (k < d) {
+                float av[V], rv[V];
+                load(k, av, rv);
+                if (syn) {
+    #pragma unroll
+                    for (int v = 0; v < V; ++v) z[v] ^= av[v] > 0.0f ? 1u : 0u;
+                }
+                if (!first) {
+    #pragma unroll
+                    for (int v = 0; v < V; ++v) av[v] = av[v] - rv[v];
+                }
+    #pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    ones[v] |= (av[v] > 0.0f ? 1u : 0u) << k;
+                    dc[k][v] = fabsf(av[v]);
+                }
+                vtanh_complement<V>(dc[k], a.l_max, a.phi_lmax);
+            } else {
+    #pragma unroll
+                for (int v = 0; v < V; ++v) dc[k][v] = 0.0f;  // T = 1: neutral
+            }
+        }
+    #pragma unroll
+        for (int v = 0; v < V; ++v) unsat[v] |= z[v] != 0u;
+        // complements of the suffix products, then a running prefix
+        float csuf[D][V];
+        {
+            float cr[V], pr[V];
+    #pragma unroll
+            for (int v = 0; v < V; ++v) {
+                cr[v] = 0.0f;
+                pr[v] = 1.0f;
+            }
+    #pragma unroll
+            for (int k = D - 1; k >= 0; --k) {
+    #pragma unroll
+                for (int v = 0; v < V; ++v) csuf[k][v] = cr[v];
+                vfma<V>(cr, pr, dc[k], cr);
+                vscale_by_tanh<V>(pr, dc[k]);
+            }
+        }
+        // output k is negative (bit-0 message) iff the other inputs hold an even
+        // number of ones, i.e. iff input k's bit equals the total parity
+        float cp[V], pp[V];
+        uint32_t neg[V];
+    #pragma unroll
+        for (int v = 0; v < V; ++v) {
+            cp[v] = 0.0f;
+            pp[v] = 1.0f;
+            neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
+        }
+    #pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (k < d) {
+                float o[V];
+                vfma<V>(o, pp, csuf[k], cp);  // C of all inputs but k
+                vmag_of_complement<V>(o, a.c_min, a.c_max);
+    #pragma unroll
+                for (int v = 0; v < V; ++v)
+                    o[v] = __int_as_float(__float_as_int(o[v]) | (int)((neg[v] << (31 - k)) & 0x80000000u));
+                store_v<V, M>(out + (size_t)k * Fp, o);
+                vfma<V>(cp, pp, dc[k], cp);
+                vscale_by_tanh<V>(pp, dc[k]);
+            }
         }
     }
 }
@@ -537,77 +600,92 @@ __device__ __forceinline__ void store_pairs(M *p, const float2 (&o)[P]) {
     store_v<2 * P, M>(p, x);
 }
 
-template <int D, int P, typename M, typename Load>
+template <int D, int P, typename M, int RULE, typename Load>
 __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Load &&load, M *out, size_t Fp,
                                                  const PassArgs &a, bool (&unsat)[2 * P]) {
-    float2 dc[D][P];       // D_k = 1 - tanh(|q_k| / 2), two frames per entry
-    uint32_t ones[2 * P];  // bit k: input k says "bit 1" (q > 0)
-    uint32_t z[2 * P];
-#pragma unroll
-    for (int v = 0; v < 2 * P; ++v) ones[v] = z[v] = 0u;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        if (k < d) {
-            float2 av[P], rv[P];
-            load(k, av, rv);
+    if constexpr (RULE == 1) {
+        auto load_flat = [&](int k, float (&av)[2 * P], float (&rv)[2 * P]) {
+            float2 a2[P], r2[P];
+            load(k, a2, r2);
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                if (syn) {
-                    z[2 * q] ^= av[q].x > 0.0f ? 1u : 0u;
-                    z[2 * q + 1] ^= av[q].y > 0.0f ? 1u : 0u;
+                av[2 * q] = a2[q].x;
+                av[2 * q + 1] = a2[q].y;
+                rv[2 * q] = first ? 0.0f : r2[q].x;
+                rv[2 * q + 1] = first ? 0.0f : r2[q].y;
+            }
+        };
+        min_sum_node<D, 2 * P, M>(d, first, syn, load_flat, out, Fp, a, unsat);
+    } else {
+        float2 dc[D][P];       // D_k = 1 - tanh(|q_k| / 2), two frames per entry
+        uint32_t ones[2 * P];  // bit k: input k says "bit 1" (q > 0)
+        uint32_t z[2 * P];
+    #pragma unroll
+        for (int v = 0; v < 2 * P; ++v) ones[v] = z[v] = 0u;
+    #pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (k < d) {
+                float2 av[P], rv[P];
+                load(k, av, rv);
+    #pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    if (syn) {
+                        z[2 * q] ^= av[q].x > 0.0f ? 1u : 0u;
+                        z[2 * q + 1] ^= av[q].y > 0.0f ? 1u : 0u;
+                    }
+                    if (!first) av[q] = fma2(rv[q], f2(-1.0f), av[q]);
+                    ones[2 * q] |= (av[q].x > 0.0f ? 1u : 0u) << k;
+                    ones[2 * q + 1] |= (av[q].y > 0.0f ? 1u : 0u) << k;
+                    dc[k][q] = tanh_complement2(make_float2(fabsf(av[q].x), fabsf(av[q].y)), a.l_max, a.phi_lmax);
                 }
-                if (!first) av[q] = fma2(rv[q], f2(-1.0f), av[q]);
-                ones[2 * q] |= (av[q].x > 0.0f ? 1u : 0u) << k;
-                ones[2 * q + 1] |= (av[q].y > 0.0f ? 1u : 0u) << k;
-                dc[k][q] = tanh_complement2(make_float2(fabsf(av[q].x), fabsf(av[q].y)), a.l_max, a.phi_lmax);
+            } else {
+    #pragma unroll
+                for (int q = 0; q < P; ++q) dc[k][q] = f2(0.0f);  // T = 1: neutral
             }
-        } else {
-#pragma unroll
-            for (int q = 0; q < P; ++q) dc[k][q] = f2(0.0f);  // T = 1: neutral
         }
-    }
-#pragma unroll
-    for (int v = 0; v < 2 * P; ++v) unsat[v] |= z[v] != 0u;
-    float2 csuf[D][P];
-    {
-        float2 cr[P], pr[P];
-#pragma unroll
+    #pragma unroll
+        for (int v = 0; v < 2 * P; ++v) unsat[v] |= z[v] != 0u;
+        float2 csuf[D][P];
+        {
+            float2 cr[P], pr[P];
+    #pragma unroll
+            for (int q = 0; q < P; ++q) {
+                cr[q] = f2(0.0f);
+                pr[q] = f2(1.0f);
+            }
+    #pragma unroll
+            for (int k = D - 1; k >= 0; --k) {
+    #pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    csuf[k][q] = cr[q];
+                    cr[q] = fma2(pr[q], dc[k][q], cr[q]);
+                    pr[q] = mul2(pr[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
+                }
+            }
+        }
+        float2 cp[P], pp[P];
+        uint32_t neg[2 * P];
+    #pragma unroll
         for (int q = 0; q < P; ++q) {
-            cr[q] = f2(0.0f);
-            pr[q] = f2(1.0f);
+            cp[q] = f2(0.0f);
+            pp[q] = f2(1.0f);
         }
-#pragma unroll
-        for (int k = D - 1; k >= 0; --k) {
-#pragma unroll
-            for (int q = 0; q < P; ++q) {
-                csuf[k][q] = cr[q];
-                cr[q] = fma2(pr[q], dc[k][q], cr[q]);
-                pr[q] = mul2(pr[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
+    #pragma unroll
+        for (int v = 0; v < 2 * P; ++v) neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
+    #pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (k < d) {
+                float2 o[P];
+    #pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    o[q] = mag_of_complement2(fma2(pp[q], csuf[k][q], cp[q]), a.c_min, a.c_max);
+                    o[q].x = __int_as_float(__float_as_int(o[q].x) | (int)((neg[2 * q] << (31 - k)) & 0x80000000u));
+                    o[q].y = __int_as_float(__float_as_int(o[q].y) | (int)((neg[2 * q + 1] << (31 - k)) & 0x80000000u));
+                    cp[q] = fma2(pp[q], dc[k][q], cp[q]);
+                    pp[q] = mul2(pp[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
+                }
+                store_pairs<M, P>(out + (size_t)k * Fp, o);
             }
-        }
-    }
-    float2 cp[P], pp[P];
-    uint32_t neg[2 * P];
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-        cp[q] = f2(0.0f);
-        pp[q] = f2(1.0f);
-    }
-#pragma unroll
-    for (int v = 0; v < 2 * P; ++v) neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        if (k < d) {
-            float2 o[P];
-#pragma unroll
-            for (int q = 0; q < P; ++q) {
-                o[q] = mag_of_complement2(fma2(pp[q], csuf[k][q], cp[q]), a.c_min, a.c_max);
-                o[q].x = __int_as_float(__float_as_int(o[q].x) | (int)((neg[2 * q] << (31 - k)) & 0x80000000u));
-                o[q].y = __int_as_float(__float_as_int(o[q].y) | (int)((neg[2 * q + 1] << (31 - k)) & 0x80000000u));
-                cp[q] = fma2(pp[q], dc[k][q], cp[q]);
-                pp[q] = mul2(pp[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
-            }
-            store_pairs<M, P>(out + (size_t)k * Fp, o);
         }
     }
 }
@@ -621,7 +699,7 @@ __device__ __forceinline__ void load_pairs(const M *p, float2 (&x)[V / 2]) {
 }
 
 // Checks of degree <= D, inputs read straight from global memory.
-template <int D, int V, typename M>
+template <int D, int V, typename M, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_t *__restrict__ checks,
                                                         int32_t count) {
     const int lane = threadIdx.x & 31;
@@ -657,14 +735,14 @@ __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_
                 load_pairs<V, float>(qsrc + (size_t)a.col_idx[slot] * Fp + f0, av);
                 if (!first) load_pairs<V, M>(r + (size_t)slot * Fp + f0, rv);
             };
-            check_node_pairs<D, V / 2, M>(d, first, syn, load, r + (size_t)b * Fp + f0, Fp, a, unsat);
+            check_node_pairs<D, V / 2, M, RULE>(d, first, syn, load, r + (size_t)b * Fp + f0, Fp, a, unsat);
         } else {
             auto load = [&](int k, float (&av)[V], float (&rv)[V]) {
                 const int slot = b + k;
                 load_v<V, float>(qsrc + (size_t)a.col_idx[slot] * Fp + f0, av);
                 if (!first) load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
             };
-            check_node<D, V, M>(d, first, syn, load, r + (size_t)b * Fp + f0, Fp, a, unsat);
+            check_node<D, V, M, RULE>(d, first, syn, load, r + (size_t)b * Fp + f0, Fp, a, unsat);
         }
     }
     if (a.syndrome) {
@@ -702,7 +780,7 @@ struct PipeShape {
     static constexpr int kStage = D * (kRowA + kRowR);        // bytes of one check's rows
 };
 
-template <int D, int V, typename M, int S, int MODE>
+template <int D, int V, typename M, int S, int MODE, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 *__restrict__ desc, int32_t count) {
     using P = PipeShape<D, V, M>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -798,7 +876,7 @@ __global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 
             if (!first)
                 load_pairs<V, M>(reinterpret_cast<const M *>(base + D * P::kRowA + k * P::kRowR) + lane * V, rv);
         };
-        check_node_pairs<D, V / 2, M>(qd[0], first, syn, load, r + (size_t)qb[0] * Fp + f0, Fp, a, unsat);
+        check_node_pairs<D, V / 2, M, RULE>(qd[0], first, syn, load, r + (size_t)qb[0] * Fp + f0, Fp, a, unsat);
         __syncwarp();
 #pragma unroll
         for (int s = 0; s < S - 1; ++s) {
@@ -820,7 +898,7 @@ __global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 
 // error-free two-sums and the parity of the signs; the second recomputes each
 // term and takes the exclusive sum as (hi - own) + lo, again error-free, so
 // the result keeps ~48 bits of the total even when one term dominates.
-template <int V, typename M>
+template <int V, typename M, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_t *__restrict__ checks,
                                                         int32_t count) {
     const int lane = threadIdx.x & 31;
@@ -848,11 +926,13 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
         const int i = checks[w];
         const int b = a.row_ptr[i];
         const int d = a.row_ptr[i + 1] - b;
-        float hi[V], lo[V];
+        float hi[V], lo[V];  // sum-product: compensated total; min-sum: two smallest |q|
+        int idx[V];
         uint32_t par[V], z[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            hi[v] = lo[v] = 0.0f;
+            hi[v] = lo[v] = RULE == 1 ? a.l_max : 0.0f;
+            idx[v] = -1;
             par[v] = z[v] = 0u;
         }
         for (int k = 0; k < d; ++k) {
@@ -874,9 +954,20 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                float err;
-                hi[v] = two_sum(hi[v], phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax), err);
-                lo[v] += err;
+                if constexpr (RULE == 1) {
+                    const float x = fminf(fabsf(qv[v]), a.l_max);
+                    if (x < hi[v]) {
+                        lo[v] = hi[v];
+                        hi[v] = x;
+                        idx[v] = k;
+                    } else if (x < lo[v]) {
+                        lo[v] = x;
+                    }
+                } else {
+                    float err;
+                    hi[v] = two_sum(hi[v], phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax), err);
+                    lo[v] += err;
+                }
                 par[v] ^= qv[v] > 0.0f ? 1u : 0u;
             }
         }
@@ -899,11 +990,17 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
             float out[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                float own = phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax);
-                float err;
-                float s = two_sum(hi[v], -own, err);
-                float excl = s + (err + lo[v]);
-                float mm = phi_hat(excl, a.l_max, a.phi_lmax);
+                float mm;
+                if constexpr (RULE == 1) {
+                    const float m = idx[v] == k ? lo[v] : hi[v];
+                    mm = fminf(fmaxf(fmaf(a.ms_alpha, m, -a.ms_beta), 0.0f), a.l_max);
+                } else {
+                    float own = phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax);
+                    float err;
+                    float s = two_sum(hi[v], -own, err);
+                    float excl = s + (err + lo[v]);
+                    mm = phi_hat(excl, a.l_max, a.phi_lmax);
+                }
                 uint32_t others = par[v] ^ (qv[v] > 0.0f ? 1u : 0u);
                 out[v] = others ? mm : -mm;
             }
@@ -1017,23 +1114,35 @@ inline dim3 pass_grid(const PassArgs &a, int64_t nodes, int V) {
     return dim3((unsigned)x, (unsigned)groups, 1);
 }
 
-template <int V, typename M>
+// Only the (bin, frames-per-lane) pairs launch_check_rule selects are
+// instantiated: V = 4 for bins 0-1, V = 2 for bins 0-2 and the unbounded bin,
+// V = 1 for every bin.
+template <int V, typename M, int RULE>
 static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t *checks, int32_t count,
                                       cudaStream_t s) {
     dim3 grid = pass_grid(a, count, V);
-    switch (bin) {
-    case 0: k_check_reg<4, V, M><<<grid, kThreads, 0, s>>>(a, checks, count); break;
-    case 1: k_check_reg<8, V, M><<<grid, kThreads, 0, s>>>(a, checks, count); break;
-    case 2: k_check_reg<16, V, M><<<grid, kThreads, 0, s>>>(a, checks, count); break;
-    case 3: k_check_reg<32, V, M><<<grid, kThreads, 0, s>>>(a, checks, count); break;
-    default: k_check_any<V, M><<<grid, kThreads, 0, s>>>(a, checks, count); break;
+    if (bin == 0) {
+        k_check_reg<4, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+    } else if (bin == 1) {
+        k_check_reg<8, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+    } else if constexpr (V <= 2) {
+        if (bin == 2) {
+            k_check_reg<16, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+        } else if (bin == 3) {
+            if constexpr (V == 1) k_check_reg<32, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+            else return cudaErrorInvalidValue;
+        } else {
+            k_check_any<V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+        }
+    } else {
+        return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 // Pipelined kernel: dynamic shared memory above 48 KB needs an opt-in, and
 // the grid is sized to the CTAs that fit on the GPU at once.
-template <int D, int V, typename M, int S, int MODE>
+template <int D, int V, typename M, int S, int MODE, int RULE>
 static cudaError_t launch_pipe_mode(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
     static int resident_by_device[64] = {0};  // CTAs per SM, once per device
     int dev = 0;
@@ -1041,47 +1150,54 @@ static cudaError_t launch_pipe_mode(const PassArgs &a, const int2 *desc, int32_t
     int &resident = resident_by_device[dev & 63];
     const size_t smem = (size_t)(kThreads / 32) * S * PipeShape<D, V, M>::kStage;
     if (resident == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_check_pipe<D, V, M, S, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(k_check_pipe<D, V, M, S, MODE, RULE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_pipe<D, V, M, S, MODE>, kThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_pipe<D, V, M, S, MODE, RULE>, kThreads, smem);
         if (e != cudaSuccess) return e;
         resident = nb > 0 ? nb : 1;
     }
     PassArgs b = a;
     b.grid_ctas = a.sm_count * resident;
     dim3 grid = pass_grid(b, count, V);
-    k_check_pipe<D, V, M, S, MODE><<<grid, kThreads, smem, s>>>(a, desc, count);
+    k_check_pipe<D, V, M, S, MODE, RULE><<<grid, kThreads, smem, s>>>(a, desc, count);
     return cudaGetLastError();
 }
 
 // Pipelined kernel: dynamic shared memory above 48 KB needs an opt-in, and
 // the grid is sized to the CTAs that fit on the GPU at once.
-template <int D, int V, typename M, int S>
+template <int D, int V, typename M, int S, int RULE>
 static cudaError_t launch_pipe(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
-    if (a.pass == 0) return launch_pipe_mode<D, V, M, S, 0>(a, desc, count, s);
-    if (a.syndrome) return launch_pipe_mode<D, V, M, S, 2>(a, desc, count, s);
-    return launch_pipe_mode<D, V, M, S, 1>(a, desc, count, s);
+    if (a.pass == 0) return launch_pipe_mode<D, V, M, S, 0, RULE>(a, desc, count, s);
+    if (a.syndrome) return launch_pipe_mode<D, V, M, S, 2, RULE>(a, desc, count, s);
+    return launch_pipe_mode<D, V, M, S, 1, RULE>(a, desc, count, s);
+}
+
+template <typename M, int RULE>
+static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *checks, const int2 *desc,
+                                     int32_t count, cudaStream_t s) {
+    if (a.check_schedule != 1 && bin <= 2 && a.f_count % 64 == 0 && a.f_begin % 64 == 0) {
+        switch (bin) {
+        case 0: return launch_pipe<4, 2, M, 4, RULE>(a, desc, count, s);
+        case 1: return launch_pipe<8, 2, M, 3, RULE>(a, desc, count, s);
+        default: return launch_pipe<16, 2, M, 2, RULE>(a, desc, count, s);
+        }
+    }
+    // Wider bins keep more messages per frame in registers: fewer frames per
+    // lane there, to stay clear of spills (bins 2-4 run two frames per lane
+    // at most, bin 3 and the unbounded bin one when V is odd).
+    if (a.V == 4 && bin < 2) return launch_check_bin_v<4, M, RULE>(a, bin, checks, count, s);
+    if (a.V >= 2 && bin != 3) return launch_check_bin_v<2, M, RULE>(a, bin, checks, count, s);
+    return launch_check_bin_v<1, M, RULE>(a, bin, checks, count, s);
 }
 
 template <typename M>
 cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, const int2 *desc, int32_t count,
                              cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    if (a.check_schedule != 1 && bin <= 2 && a.f_count % 64 == 0 && a.f_begin % 64 == 0) {
-        switch (bin) {
-        case 0: return launch_pipe<4, 2, M, 4>(a, desc, count, s);
-        case 1: return launch_pipe<8, 2, M, 3>(a, desc, count, s);
-        default: return launch_pipe<16, 2, M, 2>(a, desc, count, s);
-        }
-    }
-    // Wider bins keep more messages per frame in registers: fewer frames per
-    // lane there, to stay clear of spills (bins 2-4 run two frames per lane
-    // at most, bin 3 and the unbounded bin one when V is odd).
-    if (a.V == 4 && bin < 2) return launch_check_bin_v<4, M>(a, bin, checks, count, s);
-    if (a.V >= 2 && bin != 3) return launch_check_bin_v<2, M>(a, bin, checks, count, s);
-    return launch_check_bin_v<1, M>(a, bin, checks, count, s);
+    if (a.check_rule == 1) return launch_check_rule<M, 1>(a, bin, checks, desc, count, s);
+    return launch_check_rule<M, 0>(a, bin, checks, desc, count, s);
 }
 
 template <typename M>

@@ -175,6 +175,9 @@ cudaError_t run_static(ldpc_code *c, unsigned char *scratch, const float *llr, i
     a.check_schedule = o.check_schedule;
     a.f_begin = 0;
     a.f_count = Fp;
+    a.check_rule = o.check_rule;
+    a.ms_alpha = o.rule_alpha > 0.0f ? o.rule_alpha : 1.0f;
+    a.ms_beta = o.rule_beta;
 
     // what must start at zero: the syndrome flag rows, and posteriors (the
     // padding frames' columns are read but never written)
@@ -254,6 +257,10 @@ extern "C" int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int
     if (o.msg_dtype != LDPC_MSG_F32 && o.msg_dtype != LDPC_MSG_F16 && o.msg_dtype != LDPC_MSG_BF16)
         return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown msg_dtype %d", o.msg_dtype);
     if (o.profile) return set_error(LDPC_EINVAL, "ldpc_decode_static: profiling is not available on this entry point");
+    if (o.check_rule != LDPC_RULE_SUM_PRODUCT && o.check_rule != LDPC_RULE_MIN_SUM)
+        return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown check_rule %d", o.check_rule);
+    if (!(o.rule_beta >= 0.0f) || !std::isfinite(o.rule_alpha))
+        return set_error(LDPC_EINVAL, "ldpc_decode_static: rule_beta must be >= 0 and rule_alpha finite");
     if (o.check_schedule < 0 || o.check_schedule > 2)
         return set_error(LDPC_EINVAL, "ldpc_decode_static: check_schedule=%d not in {0, 1, 2}", o.check_schedule);
     if (o.frames_per_lane != 0 && o.frames_per_lane != 1 && o.frames_per_lane != 2 && o.frames_per_lane != 4)

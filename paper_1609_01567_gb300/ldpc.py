@@ -16,6 +16,7 @@ import numpy as np
 from . import build as _build
 
 LDPC_MSG = {"f32": 0, "f16": 1, "bf16": 2}
+LDPC_RULE = {"sum_product": 0, "min_sum": 1}
 KERNEL_CLASSES = ("interleave", "check", "bit", "syndrome", "finalize", "other", "passes")
 
 
@@ -40,7 +41,8 @@ class ldpc_code_info_t(ctypes.Structure):
 class ldpc_decode_opts_t(ctypes.Structure):
     _fields_ = [("early_exit", ctypes.c_int32), ("l_max", ctypes.c_float), ("msg_dtype", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("r_out", ctypes.c_void_p), ("frames_per_lane", ctypes.c_int32),
-                ("check_schedule", ctypes.c_int32), ("streams", ctypes.c_int32), ("tile_frames", ctypes.c_int32)]
+                ("check_schedule", ctypes.c_int32), ("streams", ctypes.c_int32), ("tile_frames", ctypes.c_int32),
+                ("check_rule", ctypes.c_int32), ("rule_alpha", ctypes.c_float), ("rule_beta", ctypes.c_float)]
 
 
 class ldpc_server_opts_t(ctypes.Structure):
@@ -201,19 +203,24 @@ def ldpc_code_tables(code: Code) -> dict:
     return arrs
 
 
+
 def _opts(early_exit, l_max, msg_dtype, profile, r_out_ptr, frames_per_lane=0, check_schedule=0, streams=0,
-          tile_frames=0):
+          tile_frames=0, rule="sum_product", rule_alpha=1.0, rule_beta=0.0):
     if msg_dtype not in LDPC_MSG:
         raise ValueError(f"msg_dtype must be one of {sorted(LDPC_MSG)}")
+    if rule not in LDPC_RULE:
+        raise ValueError(f"rule must be one of {sorted(LDPC_RULE)}")
     return ldpc_decode_opts_t(early_exit=1 if early_exit else 0, l_max=float(l_max), msg_dtype=LDPC_MSG[msg_dtype],
                               profile=1 if profile else 0, r_out=r_out_ptr, frames_per_lane=int(frames_per_lane),
-                              check_schedule=int(check_schedule), streams=int(streams), tile_frames=int(tile_frames))
+                              check_schedule=int(check_schedule), streams=int(streams), tile_frames=int(tile_frames),
+                              check_rule=LDPC_RULE[rule], rule_alpha=float(rule_alpha), rule_beta=float(rule_beta))
 
 
 def ldpc_decode(code: Code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
                 msg_dtype: str = "f32", profile: bool = False, want_post: bool = True, want_r: bool = False,
                 out: dict | None = None, stream=None, frames_per_lane: int = 0, check_schedule: int = 0,
-                streams: int = 0, tile_frames: int = 0) -> dict:
+                streams: int = 0, tile_frames: int = 0, rule: str = "sum_product", rule_alpha: float = 1.0,
+                rule_beta: float = 0.0) -> dict:
     """Decode ``llr`` (CUDA float32 [F, n]); returns CUDA tensors
     ``bits`` uint8 [F, n], ``iters`` int32 [F], ``ok`` uint8 [F] and, when
     asked, ``post`` float32 [F, n] and ``r`` float32 [F, E] (edge order)."""
@@ -234,7 +241,7 @@ def ldpc_decode(code: Code, llr, max_iter: int, *, early_exit: bool = True, l_ma
         o["r"] = torch.empty((f, code.n_edges), dtype=torch.float32, device=dev)
     r_ptr = _dev_ptr(o.get("r"), torch.float32, (f, code.n_edges), "r", code.device) if want_r else None
     opts = _opts(early_exit, l_max, msg_dtype, profile, r_ptr.value if r_ptr else None, frames_per_lane,
-                 check_schedule, streams, tile_frames)
+                 check_schedule, streams, tile_frames, rule, rule_alpha, rule_beta)
     _check(library().ldpc_decode(
         code.handle, _dev_ptr(llr, torch.float32, (f, code.n), "llr", code.device), f, max_iter, ctypes.byref(opts),
         _dev_ptr(o["bits"], torch.uint8, (f, code.n), "bits", code.device),
@@ -284,7 +291,8 @@ def ldpc_decode_host(code: Code, llr: np.ndarray, max_iter: int, *, early_exit: 
 
 def ldpc_decode_static(code: Code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
                        msg_dtype: str = "f32", want_post: bool = True, out: dict | None = None, stream=None,
-                       frames_per_lane: int = 0, check_schedule: int = 0) -> dict:
+                       frames_per_lane: int = 0, check_schedule: int = 0, rule: str = "sum_product",
+                       rule_alpha: float = 1.0, rule_beta: float = 0.0) -> dict:
     """ldpc_decode for callers that may not allocate device memory while they
     decode: the library's scratch is a fixed 64 MiB device array (see
     include/ldpc.h). Output tensors are allocated here unless passed in
@@ -301,7 +309,8 @@ def ldpc_decode_static(code: Code, llr, max_iter: int, *, early_exit: bool = Tru
         o["ok"] = torch.empty((f,), dtype=torch.uint8, device=dev)
     if want_post and "post" not in o:
         o["post"] = torch.empty((f, code.n), dtype=torch.float32, device=dev)
-    opts = _opts(early_exit, l_max, msg_dtype, False, None, frames_per_lane, check_schedule)
+    opts = _opts(early_exit, l_max, msg_dtype, False, None, frames_per_lane, check_schedule, 0, 0, rule, rule_alpha,
+                 rule_beta)
     _check(library().ldpc_decode_static(
         code.handle, _dev_ptr(llr, torch.float32, (f, code.n), "llr", code.device), f, max_iter, ctypes.byref(opts),
         _dev_ptr(o["bits"], torch.uint8, (f, code.n), "bits", code.device),

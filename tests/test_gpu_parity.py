@@ -272,3 +272,62 @@ def test_profile_counts_launches(ldpc, n1008):
     assert prof["bit"]["launches"] == 5
     assert prof["check"]["launches"] >= 5
     assert prof["check"]["total_ms"] > 0.0
+
+
+# --- min-sum family --------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [1, 2, 3, 8, 16, 32, 33, 96])
+def test_min_sum_single_check_any_degree(ldpc, oracle_mod, d):
+    code = I.coo_code(1, d, [0] * d, list(range(d)))
+    h = ldpc.code_from_inputs(code)
+    llr = np.random.default_rng(d).normal(0.0, 3.0, size=(70, d)).astype(np.float32)
+    llr[1, :] = llr[1, 0]  # ties between the two smallest magnitudes
+    for alpha, beta in ((1.0, 0.0), (0.75, 0.0), (1.0, 0.5)):
+        got = gpu_decode(ldpc, h, llr, 0, early_exit=False, rule="min_sum", rule_alpha=alpha, rule_beta=beta)
+        ref = oracle_mod.decode(code, llr.astype(np.float64), 0, early_exit=False, rule="min_sum", alpha=alpha,
+                                beta=beta)
+        assert close(got["post"], ref["post"]).all(), (alpha, beta, np.abs(got["post"] - ref["post"]).max())
+
+
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (0.8, 0.0), (1.0, 0.3)])
+def test_min_sum_n1008_matches_oracle(ldpc, oracle_mod, n1008, alpha, beta):
+    """End to end on frames that stop within 20 iterations; longer
+    trajectories are checked pass by pass in the lock-step test below."""
+    code, cw, llr = n1008
+    h = ldpc.code_from_inputs(code)
+    got = gpu_decode(ldpc, h, llr, 50, rule="min_sum", rule_alpha=alpha, rule_beta=beta)
+    ref = oracle_mod.decode(code, llr.astype(np.float64), 50, n_threads=8, rule="min_sum", alpha=alpha, beta=beta)
+    same = (got["bits"] == ref["bits"]).all(axis=1) & (got["iters"] == ref["iters"]) & (got["ok"] == ref["ok"])
+    exempt = near_zero_frames(ref["post"])
+    short = ref["iters"] <= 20
+    assert np.all(same | exempt | ~short), np.flatnonzero(~same & ~exempt & short)[:10]
+    assert close(got["post"], ref["post"]).all(axis=1)[short & ~exempt].all()
+    assert short.mean() > 0.5 and same.mean() > 0.98
+
+
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (0.8, 0.2)])
+def test_min_sum_lock_step_every_pass_n1008(ldpc, oracle_mod, n1008, alpha, beta):
+    code, cw, llr = n1008
+    h = ldpc.code_from_inputs(code)
+    kw = dict(rule="min_sum", rule_alpha=alpha, rule_beta=beta)
+    prev_r = None
+    lam = llr.astype(np.float64)
+    for t in range(0, 51, 5):
+        if t > 0:
+            prev = gpu_decode(ldpc, h, llr, t - 1, early_exit=False, want_r=True, **kw)
+            prev_r = prev["r"].astype(np.float64)
+        got = gpu_decode(ldpc, h, llr, t, early_exit=False, want_r=True, **kw)
+        ref = oracle_mod.sp_pass(code, lam, prev_r, n_threads=8, rule="min_sum", alpha=alpha, beta=beta)
+        assert close(got["post"], ref["post"]).all(), (t, float(np.abs(got["post"] - ref["post"]).max()))
+        assert close(got["r"], ref["r"], atol=1e-4).all(), (t, float(np.abs(got["r"] - ref["r"]).max()))
+
+
+def test_min_sum_schedules_do_not_change_results(ldpc, n1008):
+    code, cw, llr = n1008
+    h = ldpc.code_from_inputs(code)
+    kw = dict(rule="min_sum", rule_alpha=0.8)
+    base = gpu_decode(ldpc, h, llr, 15, frames_per_lane=1, check_schedule=1, streams=1, **kw)
+    for v, sched, nst in ((4, 2, 2), (2, 2, 1), (8, 1, 1)):
+        other = gpu_decode(ldpc, h, llr, 15, frames_per_lane=v, check_schedule=sched, streams=nst, **kw)
+        for k in ("bits", "iters", "ok", "post"):
+            np.testing.assert_array_equal(other[k], base[k], err_msg=f"V={v} schedule={sched} streams={nst} {k}")
