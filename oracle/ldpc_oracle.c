@@ -46,6 +46,14 @@
  *   same sign rule; alpha < 1 is the normalised, beta > 0 the offset variant.
  *   An empty minimum (degree-1 check) is L_MAX.
  *
+ *   Quantised message storage (the paper's "lower precision" direction for
+ *   further speed-up; its own decoder keeps FP64): when qstep > 0 every
+ *   check-to-bit message is stored as r = k * qstep, k = r / qstep rounded to
+ *   the nearest integer (ties to even) and clamped to [-qlevels, qlevels].
+ *   Everything computed from the stored messages (q, APP, the decision) uses
+ *   the stored values; node arithmetic stays FP64. int8 storage is
+ *   qstep = 20/127, qlevels = 127.
+ *
  *   Channel (BER-simulator section, Eqs. 3-4): x = 2c - 1, y = x + sigma z,
  *   lambda = 2 y / sigma^2, with z from Philox-4x64-10 (Salmon et al., SC'11)
  *   and the Box-Muller transform.
@@ -130,7 +138,17 @@ static double phi_hat(double x, double l_max) {
 typedef struct {
     int rule;
     double alpha, beta;
+    double qstep;     /* > 0: stored messages are quantised to this step */
+    int32_t qlevels;  /* largest stored |k| */
 } orc_rule;
+
+/* The stored value of a message under quantised storage. */
+static double quantise(double r, const orc_rule *rule) {
+    double k = nearbyint(r / rule->qstep);
+    if (k > rule->qlevels) k = rule->qlevels;
+    if (k < -rule->qlevels) k = -rule->qlevels;
+    return k * rule->qstep;
+}
 
 /* Min-sum check rule for one check. */
 static void check_update_min_sum(const orc_graph *g, int32_t i, const double *q, double *r, double l_max,
@@ -197,6 +215,8 @@ static int64_t sp_pass(const orc_graph *g, const double *lam, const double *r_pr
         else
             check_update(g, i, q, r_next, l_max, mag, one);
     }
+    if (rule && rule->qstep > 0.0)
+        for (int64_t e = 0; e < g->E; ++e) r_next[e] = quantise(r_next[e], rule);
     for (int32_t j = 0; j < g->n; ++j) {
         double v = lam[j];
         for (int64_t e = g->vstart[j]; e < g->vstart[j + 1]; ++e) v += r_next[e];
@@ -230,10 +250,11 @@ static int64_t max_check_degree(const orc_graph *g) {
 int orc_decode(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t *cols,
                const double *lam, int32_t n_frames, int32_t max_iter, int32_t early_exit, double l_max,
                uint8_t *bits, int32_t *iters, uint8_t *ok, double *post, double *r_out, int32_t n_threads,
-               int32_t check_rule, double alpha, double beta) {
+               int32_t check_rule, double alpha, double beta, double qstep, int32_t qlevels) {
     if (m < 0 || n < 0 || E < 0 || n_frames < 0 || max_iter < 0 || !(l_max > 0.0)) return -1;
     if (check_rule < 0 || check_rule > 1 || !(alpha > 0.0) || beta < 0.0) return -1;
-    orc_rule rule = {check_rule, alpha, beta};
+    if (qstep < 0.0 || (qstep > 0.0 && qlevels < 1)) return -1;
+    orc_rule rule = {check_rule, alpha, beta, qstep, qlevels};
     orc_graph g;
     if (graph_build(m, n, E, rows, cols, &g)) return -1;
     int64_t dmax = max_check_degree(&g);
@@ -285,10 +306,11 @@ int orc_decode(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32
 int orc_pass(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t *cols,
              const double *lam, int32_t n_frames, const double *r_prev, double l_max,
              double *r_next, double *app, uint8_t *bits, int64_t *weight, int32_t n_threads,
-             int32_t check_rule, double alpha, double beta) {
+             int32_t check_rule, double alpha, double beta, double qstep, int32_t qlevels) {
     if (m < 0 || n < 0 || E < 0 || n_frames < 0 || !(l_max > 0.0)) return -1;
     if (check_rule < 0 || check_rule > 1 || !(alpha > 0.0) || beta < 0.0) return -1;
-    orc_rule rule = {check_rule, alpha, beta};
+    if (qstep < 0.0 || (qstep > 0.0 && qlevels < 1)) return -1;
+    orc_rule rule = {check_rule, alpha, beta, qstep, qlevels};
     orc_graph g;
     if (graph_build(m, n, E, rows, cols, &g)) return -1;
     int64_t dmax = max_check_degree(&g);

@@ -40,9 +40,10 @@ def _lib():
         lib = ctypes.CDLL(str(path))
         i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
         vp = ctypes.c_void_p
-        lib.orc_decode.argtypes = [i32, i32, i64, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp, vp, vp, i32, i32, dbl, dbl]
+        lib.orc_decode.argtypes = [i32, i32, i64, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp, vp, vp, i32, i32, dbl, dbl,
+                                   dbl, i32]
         lib.orc_decode.restype = ctypes.c_int
-        lib.orc_pass.argtypes = [i32, i32, i64, vp, vp, vp, i32, vp, dbl, vp, vp, vp, vp, i32, i32, dbl, dbl]
+        lib.orc_pass.argtypes = [i32, i32, i64, vp, vp, vp, i32, vp, dbl, vp, vp, vp, vp, i32, i32, dbl, dbl, dbl, i32]
         lib.orc_pass.restype = ctypes.c_int
         lib.orc_syndrome.argtypes = [i32, i32, i64, vp, vp, vp, i32, vp]
         lib.orc_syndrome.restype = ctypes.c_int
@@ -72,12 +73,24 @@ def default_threads() -> int:
 
 RULES = {"sp": 0, "min_sum": 1}
 
+# Stored-message formats: (quantisation step, largest |level|); "f64" keeps
+# the messages unrounded, "i8" stores k * 20/127 with |k| <= 127.
+MSG = {"f64": (0.0, 0), "i8": (20.0 / 127.0, 127)}
+
+
+def _msg(msg):
+    if isinstance(msg, tuple):
+        return float(msg[0]), int(msg[1])
+    return MSG[msg]
+
 
 def decode(code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
            want_post: bool = True, want_r: bool = False, n_threads: int | None = None,
-           rule: str = "sp", alpha: float = 1.0, beta: float = 0.0):
+           rule: str = "sp", alpha: float = 1.0, beta: float = 0.0, msg="f64"):
     """Sum-product decode (Algorithm 2) of LLRs ``llr`` [F, n] in FP64
-    (``rule="min_sum"``: the min-sum family, |r| = clamp(alpha min - beta)).
+    (``rule="min_sum"``: the min-sum family, |r| = clamp(alpha min - beta);
+    ``msg``: a key of :data:`MSG` or a (step, levels) pair for quantised
+    message storage).
 
     Returns a dict with ``bits`` uint8 [F, n], ``iters`` int32 [F], ``ok``
     uint8 [F], and optionally ``post`` float64 [F, n] (APP LLRs) and ``r``
@@ -96,7 +109,7 @@ def decode(code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 
     rc = _lib().orc_decode(code.m, code.n, e, _ptr(rows), _ptr(cols), _ptr(lam), f, max_iter,
                            1 if early_exit else 0, l_max, _ptr(bits), _ptr(iters), _ptr(ok), _ptr(post),
                            _ptr(r), n_threads if n_threads is not None else default_threads(), RULES[rule],
-                           alpha, beta)
+                           alpha, beta, *_msg(msg))
     if rc != 0:
         raise ValueError("oracle decode rejected its input")
     out = {"bits": bits, "iters": iters, "ok": ok}
@@ -108,7 +121,7 @@ def decode(code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 
 
 
 def sp_pass(code, llr, r_prev=None, *, l_max: float = 20.0, n_threads: int | None = None, rule: str = "sp",
-            alpha: float = 1.0, beta: float = 0.0):
+            alpha: float = 1.0, beta: float = 0.0, msg="f64"):
     """One flooding pass from messages ``r_prev`` [F, E] (None: first pass).
 
     Returns ``r`` [F, E], ``post`` [F, n], ``bits`` [F, n], ``weight`` [F].
@@ -124,7 +137,7 @@ def sp_pass(code, llr, r_prev=None, *, l_max: float = 20.0, n_threads: int | Non
     w = np.zeros(f, dtype=np.int64)
     rc = _lib().orc_pass(code.m, code.n, e, _ptr(rows), _ptr(cols), _ptr(lam), f, _ptr(rp), l_max, _ptr(r),
                          _ptr(app), _ptr(bits), _ptr(w), n_threads if n_threads is not None else default_threads(),
-                         RULES[rule], alpha, beta)
+                         RULES[rule], alpha, beta, *_msg(msg))
     if rc != 0:
         raise ValueError("oracle pass rejected its input")
     return {"r": r, "post": app, "bits": bits, "weight": w}

@@ -313,3 +313,57 @@ def test_min_sum_variants_and_bounds(oracle_mod):
     np.testing.assert_allclose(off, np.sign(plain) * np.maximum(np.abs(plain) - 0.5, 0.0), rtol=1e-14, atol=1e-15)
     exact = oracle_mod.sp_pass(code, lam)["r"]
     assert np.all(np.abs(plain) >= np.abs(exact) - 1e-12)
+
+
+# --- quantised message storage (int8: step 20/127, |k| <= 127) ----------------
+
+def test_quantised_messages_lie_on_the_int8_lattice_and_round_to_nearest(oracle_mod, n1008):
+    """Stored messages are k * 20/127 with |k| <= 127, within half a step of
+    the unrounded messages computed from the same inputs, and the APP sums the
+    stored (not the unrounded) messages."""
+    code, cw = n1008
+    step = 20.0 / 127.0
+    lam = I.gaussian_llr(cw[:8], I.sigma2_from_ebn0(1.5, 0.5), seed=5).astype(np.float64)
+    q0 = oracle_mod.sp_pass(code, lam, msg="i8")
+    prev = q0["r"]
+    for r_prev in (None, prev):
+        exact = oracle_mod.sp_pass(code, lam, r_prev)
+        quant = oracle_mod.sp_pass(code, lam, r_prev, msg="i8")
+        k = quant["r"] / step
+        np.testing.assert_allclose(k, np.round(k), atol=1e-9)
+        assert np.abs(k).max() <= 127 + 1e-9
+        assert np.abs(quant["r"] - exact["r"]).max() <= step / 2 + 1e-12
+        v = oracle_mod.address_iterators(code)["v"]
+        app = lam.copy()
+        for f in range(lam.shape[0]):
+            np.add.at(app[f], v, quant["r"][f])
+        np.testing.assert_allclose(quant["post"], app, rtol=1e-12, atol=1e-12)
+        np.testing.assert_array_equal(quant["bits"], (app > 0).astype(np.uint8))
+    # a saturated message is stored at the top level: a degree-2 check passes
+    # its other input clamped to L_MAX = 20 = 127 steps
+    code2 = I.coo_code(1, 2, [0, 0], [0, 1])
+    out = oracle_mod.sp_pass(code2, np.array([[35.0, -3.0]]), msg="i8")
+    np.testing.assert_allclose(out["r"][0], [np.round(-3.0 / step) * step, 127 * step], atol=1e-12)
+
+
+def test_fine_quantisation_reduces_to_unrounded_decoder(oracle_mod, n1008):
+    code, cw = n1008
+    lam = I.gaussian_llr(cw[:10], I.sigma2_from_ebn0(1.25, 0.5), seed=6).astype(np.float64)
+    exact = oracle_mod.decode(code, lam, 25)
+    fine = oracle_mod.decode(code, lam, 25, msg=(1e-8, 2 ** 31 - 1))  # top level 21.5 > L_MAX
+    np.testing.assert_array_equal(fine["iters"], exact["iters"])
+    np.testing.assert_array_equal(fine["bits"], exact["bits"])
+    np.testing.assert_allclose(fine["post"], exact["post"], rtol=0, atol=1e-6)
+
+
+def test_quantised_decoder_keeps_codeword_symmetry(oracle_mod, n1008):
+    """Rounding to the nearest level (ties to even) is odd-symmetric, so the
+    int8 decoder keeps the exact codeword sign symmetry."""
+    code, cw = n1008
+    lam = I.gaussian_llr(np.zeros_like(cw), I.sigma2_from_ebn0(1.5, 0.5), seed=3).astype(np.float64)
+    base = oracle_mod.decode(code, lam, 30, msg="i8")
+    flip = oracle_mod.decode(code, lam * (1.0 - 2.0 * cw), 30, msg="i8")
+    np.testing.assert_array_equal(flip["iters"], base["iters"])
+    np.testing.assert_array_equal(flip["bits"], base["bits"] ^ cw)
+    np.testing.assert_array_equal(flip["post"], base["post"] * (1.0 - 2.0 * cw))
+    assert base["ok"].mean() > 0.5
