@@ -33,7 +33,7 @@ METRIC = "decoded Gbit/s and edge-updates/s at n=64800, 10 iters; HBM roofline %
 UNIT = "Gbit/s"
 N_BITS, K_BITS = 64800, 32400
 PROFILE_DIR = ROOT / "profiles"
-HOT_SOURCES = ("ldpc_pass_kernels.cuh", "ldpc_decode.cu", "ldpc_internal.h")
+HOT_SOURCES = ("ldpc_pass_kernels.cuh", "ldpc_pass.h", "ldpc_decode.cu")
 
 
 def parse_args():
@@ -45,7 +45,7 @@ def parse_args():
     p.add_argument("--frames", type=int, default=256, help="frames per GPU per step")
     p.add_argument("--max-iter", type=int, default=10)
     p.add_argument("--ebn0", type=float, default=1.0)
-    p.add_argument("--msg", choices=("f32", "f16", "bf16"), default="f32")
+    p.add_argument("--msg", choices=("f32", "f16", "bf16", "i8"), default="f32")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=50)
@@ -292,7 +292,7 @@ def run_ours(args):
     # Roofline of the dominant work, the flooding passes (check-node and
     # bit-node kernels; with two streams they overlap, so the unit timed is the
     # pass region on the launching stream): algorithmic bytes / time.
-    s = 4 if args.msg == "f32" else 2
+    s = {"f32": 4, "f16": 2, "bf16": 2, "i8": 1}[args.msg]
     n = code.n
     check_bytes_step = ((passes - 1) * (2 * s * E + 4 * n) + (s * E + 4 * n)) * F
     bit_bytes_step = passes * (s * E + 8 * n) * F

@@ -52,7 +52,10 @@ typedef enum {
 typedef enum {
     LDPC_MSG_F32 = 0,   /* check-to-bit messages stored as float              */
     LDPC_MSG_F16 = 1,   /* stored as IEEE half; all node sums stay in float   */
-    LDPC_MSG_BF16 = 2   /* stored as bfloat16; all node sums stay in float    */
+    LDPC_MSG_BF16 = 2,  /* stored as bfloat16; all node sums stay in float    */
+    LDPC_MSG_I8 = 3     /* stored as int8 in steps of 20/127, saturating at
+                           +-20 (L_MAX above 20 acts as 20 for the stored
+                           messages); all node arithmetic stays in float    */
 } ldpc_msg_dtype;
 
 /* Opaque code handle: host tables plus their device copies. */
@@ -78,6 +81,11 @@ typedef struct {
                                         reports INT32_MAX                     */
     int32_t check_bin_count[8];  /* checks in each bin                       */
     int32_t device;              /* device of the tables, -1 for host only   */
+    int32_t ira_k;               /* k = n - m when the last m columns of H are
+                                    the dual-diagonal staircase of an IRA code
+                                    (column k + i joins checks i and i + 1, the
+                                    last column only check m - 1), so that
+                                    ldpc_encode_ira applies; else -1          */
 } ldpc_code_info_t;
 
 /*
@@ -94,6 +102,24 @@ typedef struct {
  */
 int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t *rows, const int32_t *cols,
                      const ldpc_code_opts_t *opts, ldpc_code_t **out);
+
+/*
+ * Build a quasi-cyclic code by lifting a base matrix (protograph) with
+ * circulant permutations: the family of the paper's benchmark codes (the
+ * CCSDS code and its protograph expansions, Section IV); the paper builds
+ * such codes off-line and feeds the decoder their H. The lifted H has
+ * mb * Z rows and nb * Z columns; base entry b puts the Z x Z circulant
+ * P^shift[b] at block (brow[b], bcol[b]): row t of the block joins column
+ * (t + shift[b]) mod Z. Several entries at one block with distinct shifts are
+ * parallel protograph edges. Edge ids follow the COO order entry-major,
+ * t-minor, stably sorted by column, as in ldpc_code_create.
+ * Errors: LDPC_EINVAL for sizes out of range (Z >= 1; the lifted rows,
+ * columns and edges each at most 2^31 - 1) or an entry outside the base
+ * matrix or with shift outside [0, Z); LDPC_EDUP when an entry repeats with
+ * the same shift; otherwise as ldpc_code_create. The caller owns the arrays.
+ */
+int ldpc_code_create_qc(int32_t mb, int32_t nb, int32_t Z, int64_t n_entries, const int32_t *brow,
+                        const int32_t *bcol, const int32_t *shift, const ldpc_code_opts_t *opts, ldpc_code_t **out);
 
 /* Release a code, its device tables and its decode workspace. Waits for
  * the code's pending work. NULL is ignored. */
@@ -331,6 +357,31 @@ int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int32_t n_fram
  */
 int ldpc_gen_awgn(uint64_t seed, int64_t frame_offset, int32_t n_frames, int32_t n, float sigma2,
                   const uint8_t *codewords, float *llr, void *stream);
+
+/*
+ * Random information words for the BER simulator (Section IV transmits
+ * random or all-zero codewords): device bits [n_frames][k] uint8, one bit per
+ * byte. Bit j of frame f is bit (j mod 64) of word (j mod 256) / 64 of the
+ * Philox-4x64-10 block with key (seed, 1) and counter (j / 256,
+ * frame_offset + f, 0, 0); key word 1 keeps these bits independent of the
+ * channel noise of ldpc_gen_awgn (key word 1 = 0).
+ * Errors: LDPC_EINVAL for negative sizes or offset. Asynchronous.
+ */
+int ldpc_gen_bits(uint64_t seed, int64_t frame_offset, int32_t n_frames, int32_t k, uint8_t *bits, void *stream);
+
+/*
+ * Systematic encoding of an IRA code (ldpc_code_info_t.ira_k >= 0): for
+ * information words info [n_frames][k] (device uint8, bit 0 of each byte
+ * used) writes codewords [n_frames][n] (device uint8) c = [u | p] with
+ * p_i = (H1 u)_i xor p_(i-1), the unique codeword of H with that systematic
+ * part (the staircase makes H2 invertible). The paper's simulator takes its
+ * codewords as given; this keeps random-codeword simulation on the device.
+ * Scratch ((k + m) * ceil(n_frames / 32) words) is stream-ordered
+ * (cudaMallocAsync / cudaFreeAsync on `stream`). Asynchronous.
+ * Errors: LDPC_EINVAL when the code is not in IRA form, for n_frames < 0 or
+ * NULL buffers; LDPC_ENODEV for a host-only code.
+ */
+int ldpc_encode_ira(ldpc_code_t *code, const uint8_t *info, int32_t n_frames, uint8_t *codeword, void *stream);
 
 /*
  * Error counts of the BER simulator (Section IV): for decoded words bits

@@ -1,13 +1,14 @@
 """BER/FER simulation on the GPU (the BER simulator of Section IV).
 
-Every batch runs three library calls on one stream: the Philox BPSK/AWGN
-generator (all-zero codeword, enough by linearity, or random codewords),
-the decoder, and the on-device error count. Counters stay on the device
+Every batch runs its library calls on one stream: the Philox BPSK/AWGN
+generator (all-zero codeword, enough by linearity, or random codewords --
+given, or drawn on the device from Philox information bits and the IRA
+encoder), the decoder, and the on-device error count. Counters stay on the device
 until the end. Frame noise depends only on (seed, global frame index), so
 runs split across batches or ranks see the same channel.
 
     python -m paper_1609_01567_gb300.ber --code n64800 --ebn0 1.0 1.2 1.4 \
-        --frames 1000000 --batch 1024 --msg f32 f16 bf16
+        --frames 1000000 --batch 1024 --msg f32 f16 bf16 i8
 """
 from __future__ import annotations
 
@@ -36,8 +37,10 @@ def simulate(handle, code, ebn0_db: float, n_frames: int, *, batch: int = 1024, 
              codewords=None, stream=None, **decode_kw) -> Counts:
     """Decode n_frames noisy frames; returns summed Counts.
 
-    codewords: None for the all-zero word, else a CUDA uint8 tensor
-    [n_frames, n] of transmitted codewords.
+    codewords: None for the all-zero word, "random" for random codewords
+    made on the device (information bits from Philox key (seed, 1), encoded
+    by the library's IRA encoder), else a CUDA uint8 tensor [n_frames, n] of
+    transmitted codewords.
     """
     import torch
 
@@ -49,9 +52,20 @@ def simulate(handle, code, ebn0_db: float, n_frames: int, *, batch: int = 1024, 
     llr = torch.empty((batch, code.n), dtype=torch.float32, device=dev)
     out = None
     done = 0
+    rand = isinstance(codewords, str)
+    if rand:
+        if codewords != "random":
+            raise ValueError("codewords must be None, 'random' or a tensor")
+        k = code.n - code.m
+        info = torch.empty((batch, k), dtype=torch.uint8, device=dev)
+        cw_buf = torch.empty((batch, code.n), dtype=torch.uint8, device=dev)
     while done < n_frames:
         b = min(batch, n_frames - done)
-        cw = None if codewords is None else codewords[done:done + b]
+        if rand:
+            ldpc.ldpc_gen_bits(seed, frame_offset + done, b, k, out=info[:b], device=handle.device, stream=stream)
+            cw = ldpc.ldpc_encode_ira(handle, info[:b], out=cw_buf[:b], stream=stream)
+        else:
+            cw = None if codewords is None else codewords[done:done + b]
         lb = llr[:b]
         ldpc.ldpc_gen_awgn(seed, frame_offset + done, b, code.n, sigma2, cw, out=lb, device=handle.device,
                            stream=stream)

@@ -83,9 +83,54 @@ __global__ void k_gen_awgn(uint64_t seed, int64_t frame_offset, int32_t F, int32
     }
 }
 
+// One thread per (frame, 256-bit Philox block): information bits, one byte
+// each. Bit j of frame f is bit (j mod 64) of word (j mod 256) / 64 of the
+// block at counter (j / 256, frame_offset + f), key (seed, 1); the key's
+// second word keeps these bits apart from the channel noise (key (seed, 0)).
+__global__ void k_gen_bits(uint64_t seed, int64_t frame_offset, int32_t F, int32_t k, uint8_t *__restrict__ out) {
+    const int32_t B = (k + 255) / 256;
+    const int64_t total = (int64_t)F * B;
+    for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < total;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t f = (int32_t)(id / B);
+        const int32_t t = (int32_t)(id - (int64_t)f * B);
+        U64x4 w = philox4x64_10((uint64_t)t, (uint64_t)(frame_offset + f), 0, 0, seed, 1);
+        uint8_t *o = out + (size_t)f * k + (size_t)t * 256;
+        const int32_t len = min(256, k - t * 256);
+        if ((reinterpret_cast<uintptr_t>(o) & 7) == 0) {
+            // eight bytes per store: byte b of the word is bit q + b
+            int32_t q = 0;
+            for (; q + 8 <= len; q += 8) {
+                const uint32_t x = (uint32_t)(w.x[q >> 6] >> (q & 63)) & 0xFFu;
+                uint64_t v = 0;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) v |= (uint64_t)((x >> b) & 1u) << (8 * b);
+                *reinterpret_cast<uint64_t *>(o + q) = v;
+            }
+            for (; q < len; ++q) o[q] = (uint8_t)((w.x[q >> 6] >> (q & 63)) & 1u);
+        } else {
+            for (int32_t q = 0; q < len; ++q) o[q] = (uint8_t)((w.x[q >> 6] >> (q & 63)) & 1u);
+        }
+    }
+}
+
 }  // namespace ldpc
 
 using namespace ldpc;
+
+extern "C" int ldpc_gen_bits(uint64_t seed, int64_t frame_offset, int32_t F, int32_t k, uint8_t *bits, void *stream) {
+    if (F < 0 || k < 0) return set_error(LDPC_EINVAL, "ldpc_gen_bits: negative size F=%d k=%d", F, k);
+    if (frame_offset < 0) return set_error(LDPC_EINVAL, "ldpc_gen_bits: frame_offset < 0");
+    if ((int64_t)F * k == 0) return LDPC_OK;
+    if (!bits) return set_error(LDPC_EINVAL, "ldpc_gen_bits: bits is NULL");
+    const int64_t total = (int64_t)F * ((k + 255) / 256);
+    int64_t blocks = (total + 127) / 128;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_gen_bits<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(seed, frame_offset, F, k, bits);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "ldpc_gen_bits: launch");
+    return LDPC_OK;
+}
 
 extern "C" int ldpc_gen_awgn(uint64_t seed, int64_t frame_offset, int32_t F, int32_t n, float sigma2,
                              const uint8_t *codewords, float *llr, void *stream) {

@@ -137,6 +137,22 @@ extern "C" int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t
         }
         for (int32_t i = 0; i < m; ++i) c->max_cdeg = std::max(c->max_cdeg, c->row_ptr[i + 1] - c->row_ptr[i]);
         for (int32_t j = 0; j < n; ++j) c->max_vdeg = std::max(c->max_vdeg, c->col_ptr[j + 1] - c->col_ptr[j]);
+        // IRA form: column k + i joins checks i and i + 1 (the last one only
+        // check m - 1), k = n - m
+        if (n >= m) {
+            const int32_t k = n - m;
+            bool stair = true;
+            for (int32_t i = 0; i < m && stair; ++i) {
+                const int32_t j = k + i, d = c->col_ptr[j + 1] - c->col_ptr[j];
+                const int32_t e = c->col_ptr[j];
+                if (i + 1 < m)
+                    stair = d == 2 && std::min(c->chk_of_edge[e], c->chk_of_edge[e + 1]) == i &&
+                            std::max(c->chk_of_edge[e], c->chk_of_edge[e + 1]) == i + 1;
+                else
+                    stair = d == 1 && c->chk_of_edge[e] == i;
+            }
+            if (stair) c->ira_k = k;
+        }
         // check degree bins (degree-0 checks carry no message and are skipped)
         for (int b = 0; b < kNumCheckBins; ++b) {
             c->bin_off[b] = (int32_t)c->bin_checks.size();
@@ -187,6 +203,40 @@ extern "C" int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t
     return LDPC_OK;
 }
 
+extern "C" int ldpc_code_create_qc(int32_t mb, int32_t nb, int32_t Z, int64_t n_entries, const int32_t *brow,
+                                   const int32_t *bcol, const int32_t *shift, const ldpc_code_opts_t *opts,
+                                   ldpc_code_t **out) {
+    if (!out) return set_error(LDPC_EINVAL, "ldpc_code_create_qc: out is NULL");
+    *out = nullptr;
+    if (mb < 0 || nb < 0 || Z < 1 || n_entries < 0)
+        return set_error(LDPC_EINVAL, "ldpc_code_create_qc: bad size mb=%d nb=%d Z=%d entries=%lld", mb, nb, Z,
+                         (long long)n_entries);
+    if ((int64_t)mb * Z > INT32_MAX || (int64_t)nb * Z > INT32_MAX || n_entries * Z > INT32_MAX)
+        return set_error(LDPC_EINVAL, "ldpc_code_create_qc: lifted code exceeds 2^31-1 rows, columns or edges");
+    if (n_entries > 0 && (!brow || !bcol || !shift)) return set_error(LDPC_EINVAL, "ldpc_code_create_qc: NULL entry array");
+    std::vector<int32_t> rows, cols;
+    try {
+        rows.resize((size_t)(n_entries * Z));
+        cols.resize((size_t)(n_entries * Z));
+    } catch (const std::bad_alloc &) {
+        return set_error(LDPC_ENOMEM, "ldpc_code_create_qc: out of host memory");
+    }
+    for (int64_t b = 0; b < n_entries; ++b) {
+        if (brow[b] < 0 || brow[b] >= mb || bcol[b] < 0 || bcol[b] >= nb || shift[b] < 0 || shift[b] >= Z)
+            return set_error(LDPC_EINVAL, "ldpc_code_create_qc: entry %lld = (%d, %d, shift %d) outside %d x %d, Z %d",
+                             (long long)b, brow[b], bcol[b], shift[b], mb, nb, Z);
+        // circulant P^s: row t of the block joins column (t + s) mod Z
+        for (int32_t t = 0; t < Z; ++t) {
+            const size_t o = (size_t)b * Z + t;
+            rows[o] = brow[b] * Z + t;
+            cols[o] = bcol[b] * Z + (int32_t)(((int64_t)t + shift[b]) % Z);
+        }
+    }
+    int st = ldpc_code_create(mb * Z, nb * Z, n_entries * Z, rows.data(), cols.data(), opts, out);
+    if (st == LDPC_EDUP) set_error(LDPC_EDUP, "ldpc_code_create_qc: a base entry repeats (same block, same shift)");
+    return st;
+}
+
 extern "C" void ldpc_code_destroy(ldpc_code_t *code) {
     if (!code) return;
     free_device_tables(code);
@@ -209,6 +259,7 @@ extern "C" int ldpc_code_info(const ldpc_code_t *c, ldpc_code_info_t *info) {
         info->check_bin_count[b] = c->bin_off[b + 1] - c->bin_off[b];
     }
     info->device = c->device;
+    info->ira_k = c->ira_k;
     return LDPC_OK;
 }
 

@@ -127,7 +127,7 @@ struct DeviceGuard {
     }
 };
 
-static int msg_size(int dtype) { return dtype == LDPC_MSG_F32 ? 4 : 2; }
+static int msg_size(int dtype) { return msg_bytes(dtype); }
 
 // Frames per lane V and padded frame count Fp (a multiple of 32 V).
 // `want` = 0 picks by batch size: four frames per lane (the widest rows,
@@ -403,8 +403,7 @@ static int check_decode_args(const ldpc_code *c, int32_t F, int32_t max_iter, co
         return set_error(LDPC_EINVAL, "%s: unknown check_rule %d", fn, o.check_rule);
     if (!(o.rule_beta >= 0.0f) || !std::isfinite(o.rule_alpha))
         return set_error(LDPC_EINVAL, "%s: rule_beta must be >= 0 and rule_alpha finite", fn);
-    if (o.msg_dtype != LDPC_MSG_F32 && o.msg_dtype != LDPC_MSG_F16 && o.msg_dtype != LDPC_MSG_BF16)
-        return set_error(LDPC_EINVAL, "%s: unknown msg_dtype %d", fn, o.msg_dtype);
+    if (!msg_dtype_valid(o.msg_dtype)) return set_error(LDPC_EINVAL, "%s: unknown msg_dtype %d", fn, o.msg_dtype);
     *l_max_out = l_max;
     return LDPC_OK;
 }
@@ -434,17 +433,10 @@ static int decode_locked(ldpc_code *c, const float *llr, int32_t F, int32_t max_
         uint8_t *bb = bits + (size_t)f0 * c->n;
         float *pp = post ? post + (size_t)f0 * c->n : nullptr;
         float *rr = o.r_out ? o.r_out + (size_t)f0 * c->E : nullptr;
-        switch (o.msg_dtype) {
-        case LDPC_MSG_F16:
-            e = run_chunk<__half>(c, c->ws, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
-            break;
-        case LDPC_MSG_BF16:
-            e = run_chunk<__nv_bfloat16>(c, c->ws, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
-            break;
-        default:
-            e = run_chunk<float>(c, c->ws, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
-            break;
-        }
+        e = with_msg_type(o.msg_dtype, [&](auto tag) {
+            using M = typename decltype(tag)::type;
+            return run_chunk<M>(c, c->ws, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
+        });
         if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: kernel launch");
     }
     e = cudaEventRecord(c->ws.last_use, s);
@@ -584,15 +576,10 @@ struct BatchItem {
 static cudaError_t enqueue_item(BatchItem &it, int32_t max_iter, float l_max, const float *llr, uint8_t *bits,
                                 int32_t *iters, uint8_t *ok, float *post, cudaStream_t s) {
     std::lock_guard<std::mutex> lock(it.code->mu);
-    switch (it.opts.msg_dtype) {
-    case LDPC_MSG_F16:
-        return run_chunk<__half>(it.code, it.ws, llr, it.F, max_iter, it.opts, l_max, bits, iters, ok, post, nullptr, s);
-    case LDPC_MSG_BF16:
-        return run_chunk<__nv_bfloat16>(it.code, it.ws, llr, it.F, max_iter, it.opts, l_max, bits, iters, ok, post,
-                                        nullptr, s);
-    default:
-        return run_chunk<float>(it.code, it.ws, llr, it.F, max_iter, it.opts, l_max, bits, iters, ok, post, nullptr, s);
-    }
+    return with_msg_type(it.opts.msg_dtype, [&](auto tag) {
+        using M = typename decltype(tag)::type;
+        return run_chunk<M>(it.code, it.ws, llr, it.F, max_iter, it.opts, l_max, bits, iters, ok, post, nullptr, s);
+    });
 }
 
 }  // namespace ldpc
@@ -856,14 +843,10 @@ cudaError_t enqueue_decode(ldpc_code *c, Workspace &w, const float *llr, int32_t
                            const ldpc_decode_opts_t &o, float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok,
                            float *post, cudaStream_t s) {
     std::lock_guard<std::mutex> lock(c->mu);
-    switch (o.msg_dtype) {
-    case LDPC_MSG_F16:
-        return run_chunk<__half>(c, w, llr, F, max_iter, o, l_max, bits, iters, ok, post, nullptr, s);
-    case LDPC_MSG_BF16:
-        return run_chunk<__nv_bfloat16>(c, w, llr, F, max_iter, o, l_max, bits, iters, ok, post, nullptr, s);
-    default:
-        return run_chunk<float>(c, w, llr, F, max_iter, o, l_max, bits, iters, ok, post, nullptr, s);
-    }
+    return with_msg_type(o.msg_dtype, [&](auto tag) {
+        using M = typename decltype(tag)::type;
+        return run_chunk<M>(c, w, llr, F, max_iter, o, l_max, bits, iters, ok, post, nullptr, s);
+    });
 }
 
 int check_opts(const ldpc_code *c, int32_t F, int32_t max_iter, const ldpc_decode_opts_t &o, float *l_max,

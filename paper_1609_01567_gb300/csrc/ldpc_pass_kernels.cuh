@@ -30,7 +30,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
-#include "ldpc_internal.h"
+#include "ldpc_pass.h"
 
 namespace ldpc {
 
@@ -115,6 +115,30 @@ struct MsgIO<__nv_bfloat16> {
     }
     static __device__ __forceinline__ float load1(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void store1(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
+};
+
+template <>
+struct MsgIO<int8_t> {
+    static __device__ __forceinline__ int8_t quantize(float x) {
+        int q = __float2int_rn(x * kI8Inv);
+        return (int8_t)max(-127, min(127, q));
+    }
+    static __device__ __forceinline__ void load4(const int8_t *p, float (&x)[4]) {
+        char4 v = *reinterpret_cast<const char4 *>(p);
+        x[0] = v.x * kI8Step; x[1] = v.y * kI8Step; x[2] = v.z * kI8Step; x[3] = v.w * kI8Step;
+    }
+    static __device__ __forceinline__ void store4(int8_t *p, const float (&x)[4]) {
+        *reinterpret_cast<char4 *>(p) = make_char4(quantize(x[0]), quantize(x[1]), quantize(x[2]), quantize(x[3]));
+    }
+    static __device__ __forceinline__ void load2(const int8_t *p, float (&x)[2]) {
+        char2 v = *reinterpret_cast<const char2 *>(p);
+        x[0] = v.x * kI8Step; x[1] = v.y * kI8Step;
+    }
+    static __device__ __forceinline__ void store2(int8_t *p, const float (&x)[2]) {
+        *reinterpret_cast<char2 *>(p) = make_char2(quantize(x[0]), quantize(x[1]));
+    }
+    static __device__ __forceinline__ float load1(const int8_t *p) { return *p * kI8Step; }
+    static __device__ __forceinline__ void store1(int8_t *p, float x) { *p = quantize(x); }
 };
 
 template <int V, typename M>

@@ -279,7 +279,7 @@ extern "C" int ldpc_server_create(int32_t n_codes, ldpc_code_t *const *codes, co
     cudaSetDevice(s->device);
     // slots: as many as the memory budget allows (at least one)
     const int32_t Fp = (max_batch + 255) / 256 * 256;
-    const int mb = d.msg_dtype == LDPC_MSG_F32 ? 4 : 2;
+    const int mb = msg_bytes(d.msg_dtype);
     const int64_t per_slot = (int64_t)Fp * (8 * (int64_t)n_max + mb * e_max) +
                              (int64_t)max_batch * (5 * (int64_t)n_max + 5) + (int64_t)(max_iter + 1) * Fp / 8;
     int64_t budget = o.memory_budget;

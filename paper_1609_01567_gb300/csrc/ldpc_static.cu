@@ -254,8 +254,7 @@ extern "C" int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int
         return set_error(LDPC_EINVAL, "ldpc_decode_static: max_iter=%d outside [0, 100000]", max_iter);
     float l_max = o.l_max > 0.0f ? o.l_max : 20.0f;
     if (!(l_max <= 80.0f)) return set_error(LDPC_EINVAL, "ldpc_decode_static: l_max=%g outside (0, 80]", (double)o.l_max);
-    if (o.msg_dtype != LDPC_MSG_F32 && o.msg_dtype != LDPC_MSG_F16 && o.msg_dtype != LDPC_MSG_BF16)
-        return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown msg_dtype %d", o.msg_dtype);
+    if (!msg_dtype_valid(o.msg_dtype)) return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown msg_dtype %d", o.msg_dtype);
     if (o.profile) return set_error(LDPC_EINVAL, "ldpc_decode_static: profiling is not available on this entry point");
     if (o.check_rule != LDPC_RULE_SUM_PRODUCT && o.check_rule != LDPC_RULE_MIN_SUM)
         return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown check_rule %d", o.check_rule);
@@ -273,7 +272,7 @@ extern "C" int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int
     int32_t V = o.frames_per_lane;
     if (V != 1 && V != 2 && V != 4) V = n_frames > 64 ? 4 : (n_frames > 32 ? 2 : 1);
     const int32_t Fp = (n_frames + 32 * V - 1) / (32 * V) * (32 * V);
-    const size_t msg = o.msg_dtype == LDPC_MSG_F32 ? 4 : 2;
+    const size_t msg = (size_t)msg_bytes(o.msg_dtype);
     const size_t words = (size_t)Fp / 32;
     const size_t need = align256(4 * (size_t)c->n * Fp) * 2 + align256(msg * (size_t)c->E * Fp) +
                         align256(4 * words) + align256(4 * words * ((size_t)max_iter + 1)) + align256(4 * (size_t)Fp);
@@ -290,18 +289,10 @@ extern "C" int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *base = static_cast<unsigned char *>(scratch);
     cudaError_t e;
-    switch (o.msg_dtype) {
-    case LDPC_MSG_F16:
-        e = run_static<__half>(c, base, llr, n_frames, max_iter, o, l_max, V, Fp, bits, iters, syndrome_ok, post_llr, s);
-        break;
-    case LDPC_MSG_BF16:
-        e = run_static<__nv_bfloat16>(c, base, llr, n_frames, max_iter, o, l_max, V, Fp, bits, iters, syndrome_ok,
-                                      post_llr, s);
-        break;
-    default:
-        e = run_static<float>(c, base, llr, n_frames, max_iter, o, l_max, V, Fp, bits, iters, syndrome_ok, post_llr, s);
-        break;
-    }
+    e = with_msg_type(o.msg_dtype, [&](auto tag) {
+        using M = typename decltype(tag)::type;
+        return run_static<M>(c, base, llr, n_frames, max_iter, o, l_max, V, Fp, bits, iters, syndrome_ok, post_llr, s);
+    });
     if (e != cudaSuccess) return cuda_error(e, "ldpc_decode_static: kernel launch");
     return LDPC_OK;
 }

@@ -299,6 +299,37 @@ def coo_code(m: int, n: int, rows, cols, name: str = "") -> Code:
     return Code(m=m, n=n, rows=np.asarray(rows, dtype=np.int32), cols=np.asarray(cols, dtype=np.int32), name=name)
 
 
+# --- quasi-cyclic (protograph-lifted) codes -----------------------------------------
+
+def qc_code(mb: int, nb: int, Z: int, entries, name: str = "") -> Code:
+    """Lift a base matrix with circulants: each (row, col, shift) entry puts
+    P^shift at that block, row t joining column (t + shift) mod Z. COO order:
+    entry-major, t-minor (the order the library's lifting entry uses)."""
+    e = np.asarray(entries, dtype=np.int64).reshape(-1, 3)
+    t = np.arange(Z, dtype=np.int64)
+    rows = (e[:, 0:1] * Z + t[None, :]).reshape(-1)
+    cols = (e[:, 1:2] * Z + (t[None, :] + e[:, 2:3]) % Z).reshape(-1)
+    return Code(m=mb * Z, n=nb * Z, rows=rows.astype(np.int32), cols=cols.astype(np.int32),
+                name=name or f"qc_{mb}x{nb}_Z{Z}")
+
+
+def qc_regular_entries(dv: int, dc: int, Z: int, seed: int) -> list[tuple[int, int, int]]:
+    """All-ones dv x dc base matrix with seeded circulant shifts: a (dv, dc)-
+    regular QC code of design rate 1 - dv/dc and dv * Z * dc edges."""
+    rng = np.random.default_rng(seed)
+    return [(i, j, int(rng.integers(0, Z))) for i in range(dv) for j in range(dc)]
+
+
+def qc_stand_in_code(n: int, seed: int | None = None) -> tuple[Code, list]:
+    """Rate-1/2 (4, 8)-regular QC stand-in of length n (4 edges per bit), the
+    protograph-lifted counterpart of the paper's benchmark family."""
+    if n % 8:
+        raise ValueError("n must be a multiple of 8")
+    Z = n // 8
+    ent = qc_regular_entries(4, 8, Z, seed if seed is not None else n + 1)
+    return qc_code(4, 8, Z, ent, name=f"qc48_n{n}_Z{Z}"), ent
+
+
 # --- mixed-code workload: 8 codes of different lengths, rates and degrees --------
 
 MIXED_SPECS = (  # (n, k, name); the 8192-bit code carries a degree-64 variable and a degree-96 check

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-LDPC_MSG = {"f32": 0, "f16": 1, "bf16": 2}
+LDPC_MSG = {"f32": 0, "f16": 1, "bf16": 2, "i8": 3}
 LDPC_RULE = {"sum_product": 0, "min_sum": 1}
 KERNEL_CLASSES = ("interleave", "check", "bit", "syndrome", "finalize", "other", "passes")
 
@@ -35,7 +35,7 @@ class ldpc_code_info_t(ctypes.Structure):
                 ("max_check_degree", ctypes.c_int32), ("max_var_degree", ctypes.c_int32),
                 ("mean_check_degree", ctypes.c_double), ("mean_var_degree", ctypes.c_double),
                 ("n_check_bins", ctypes.c_int32), ("check_bin_max_degree", ctypes.c_int32 * 8),
-                ("check_bin_count", ctypes.c_int32 * 8), ("device", ctypes.c_int32)]
+                ("check_bin_count", ctypes.c_int32 * 8), ("device", ctypes.c_int32), ("ira_k", ctypes.c_int32)]
 
 
 class ldpc_decode_opts_t(ctypes.Structure):
@@ -60,7 +60,7 @@ class ldpc_prof_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 7), ("total_ms", ctypes.c_double * 7), ("kernels", ctypes.c_int64)]
 
 
-EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
+EXPORTS = ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira", "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
            "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_count_errors", "ldpc_batch_create",
            "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info", "ldpc_batch_destroy", "ldpc_server_create",
            "ldpc_server_submit", "ldpc_server_wait", "ldpc_server_stats", "ldpc_server_destroy", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
@@ -81,6 +81,10 @@ def library():
             lib = ctypes.CDLL(str(path))
             vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
             lib.ldpc_code_create.argtypes = [i32, i32, i64, vp, vp, ctypes.POINTER(ldpc_code_opts_t), ctypes.POINTER(vp)]
+            lib.ldpc_code_create_qc.argtypes = [i32, i32, i32, i64, vp, vp, vp, ctypes.POINTER(ldpc_code_opts_t),
+                                                ctypes.POINTER(vp)]
+            lib.ldpc_gen_bits.argtypes = [u64, i64, i32, i32, vp, vp]
+            lib.ldpc_encode_ira.argtypes = [vp, vp, i32, vp, vp]
             lib.ldpc_code_destroy.argtypes = [vp]
             lib.ldpc_code_destroy.restype = None
             lib.ldpc_code_info.argtypes = [vp, ctypes.POINTER(ldpc_code_info_t)]
@@ -107,7 +111,7 @@ def library():
             lib.ldpc_prof_read.argtypes = [vp, ctypes.POINTER(ldpc_prof_t), i32]
             lib.ldpc_last_error.restype = ctypes.c_char_p
             lib.ldpc_version.restype = ctypes.c_char_p
-            for name in ("ldpc_code_create", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode", "ldpc_decode_host",
+            for name in ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode", "ldpc_decode_host",
                          "ldpc_decode_static",
                          "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_count_errors",
                          "ldpc_batch_create", "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info",
@@ -183,6 +187,23 @@ def ldpc_code_create(m: int, n: int, rows, cols, device: int = 0) -> Code:
     return Code(h, m, n, int(r.shape[0]), device)
 
 
+def ldpc_code_create_qc(mb: int, nb: int, Z: int, entries, device: int = 0) -> Code:
+    """Lift a base matrix: ``entries`` is a sequence of (row, col, shift)
+    triples, each a Z x Z circulant P^shift (row t -> column (t + shift) mod
+    Z) at that block; repeated blocks with distinct shifts are parallel
+    protograph edges."""
+    e = np.asarray(entries, dtype=np.int64).reshape(-1, 3)
+    br = np.ascontiguousarray(e[:, 0], dtype=np.int32)
+    bc = np.ascontiguousarray(e[:, 1], dtype=np.int32)
+    sh = np.ascontiguousarray(e[:, 2], dtype=np.int32)
+    h = ctypes.c_void_p()
+    opts = ldpc_code_opts_t(device=device)
+    vp = ctypes.c_void_p
+    _check(library().ldpc_code_create_qc(mb, nb, Z, e.shape[0], br.ctypes.data_as(vp), bc.ctypes.data_as(vp),
+                                         sh.ctypes.data_as(vp), ctypes.byref(opts), ctypes.byref(h)))
+    return Code(h, mb * Z, nb * Z, int(e.shape[0]) * Z, device)
+
+
 def ldpc_code_info(code: Code) -> dict:
     info = ldpc_code_info_t()
     _check(library().ldpc_code_info(code.handle, ctypes.byref(info)))
@@ -190,7 +211,8 @@ def ldpc_code_info(code: Code) -> dict:
     return {"m": info.m, "n": info.n, "n_edges": info.n_edges, "max_check_degree": info.max_check_degree,
             "max_var_degree": info.max_var_degree, "mean_check_degree": info.mean_check_degree,
             "mean_var_degree": info.mean_var_degree, "check_bin_max_degree": list(info.check_bin_max_degree[:nb]),
-            "check_bin_count": list(info.check_bin_count[:nb]), "device": info.device}
+            "check_bin_count": list(info.check_bin_count[:nb]), "device": info.device,
+            "ira_k": info.ira_k}
 
 
 TABLE_NAMES = ("v", "c", "t", "s", "u", "ebar", "vbar", "cbar", "tbar", "sbar", "ubar")
@@ -332,6 +354,31 @@ def ldpc_gen_awgn(seed: int, frame_offset: int, n_frames: int, n: int, sigma2: f
     _check(library().ldpc_gen_awgn(seed, frame_offset, n_frames, n, float(sigma2),
                                    _dev_ptr(codewords, torch.uint8, (n_frames, n), "codewords", None),
                                    _dev_ptr(out, torch.float32, (n_frames, n), "out", None), _stream_handle(stream)))
+    return out
+
+
+def ldpc_gen_bits(seed: int, frame_offset: int, n_frames: int, k: int, out=None, device: int = 0, stream=None):
+    """Random information words (CUDA uint8 [n_frames, k], one bit per byte)
+    from the on-device Philox-4x64-10 generator (key (seed, 1))."""
+    import torch
+    if out is None:
+        out = torch.empty((n_frames, k), dtype=torch.uint8, device=torch.device("cuda", device))
+    _check(library().ldpc_gen_bits(seed, frame_offset, n_frames, k,
+                                   _dev_ptr(out, torch.uint8, (n_frames, k), "out", None), _stream_handle(stream)))
+    return out
+
+
+def ldpc_encode_ira(code: Code, info, out=None, stream=None):
+    """Systematic IRA encoding on the device: CUDA uint8 info [F, k] ->
+    codewords [F, n] (``k`` = ``ldpc_code_info(code)["ira_k"]``)."""
+    import torch
+    k = code.n - code.m
+    f = int(info.shape[0])
+    if out is None:
+        out = torch.empty((f, code.n), dtype=torch.uint8, device=info.device)
+    _check(library().ldpc_encode_ira(code.handle, _dev_ptr(info, torch.uint8, (f, k), "info", code.device), f,
+                                     _dev_ptr(out, torch.uint8, (f, code.n), "out", code.device),
+                                     _stream_handle(stream)))
     return out
 
 

@@ -4,9 +4,11 @@ The paper times a BER simulation of 10,000 codewords at Eb/N0 = 2 dB for
 rate-1/2 codes of n = 2^8 .. 2^18 bits with 4 edges per bit (noise
 generation included), on a Tesla K40/K80 and a Xeon E5-2695v2. Its codes
 (CCSDS (256,128) and protograph expansions) are not available here, so each
-length gets a seeded IRA stand-in with the same size and edge count
-(information bits of degree 6, the staircase parity bits of degree 2:
-E = 4n - 1). Per length: the on-device Philox generator, the decoder
+length gets a seeded stand-in with the same size and edge count: an IRA
+code (information bits of degree 6, the staircase parity bits of degree 2:
+E = 4n - 1), or, with --family qc, a (4, 8)-regular quasi-cyclic code lifted
+from an all-ones 4 x 8 protograph with seeded circulant shifts (E = 4n), the
+structure of the paper's protograph expansions. Per length: the on-device Philox generator, the decoder
 (max_iter 50, early exit) and the error counter, all on one stream; the
 paper's seconds are printed beside as context (other hardware, other codes,
 unstated iteration limit).
@@ -49,6 +51,7 @@ def main(argv=None):
     p.add_argument("--max-iter", type=int, default=50)
     p.add_argument("--lengths", type=int, nargs="+", default=sorted(PAPER_TABLE3_SECONDS))
     p.add_argument("--msg", default="f32")
+    p.add_argument("--family", choices=("ira", "qc"), default="ira")
     args = p.parse_args(argv)
 
     import torch
@@ -56,8 +59,12 @@ def main(argv=None):
     from . import ber, ldpc
 
     for n in args.lengths:
-        code = stand_in_code(n)
-        h = ldpc.code_from_inputs(code)
+        if args.family == "qc":
+            code, entries = inputs.qc_stand_in_code(n)
+            h = ldpc.ldpc_code_create_qc(4, 8, n // 8, entries)
+        else:
+            code = stand_in_code(n)
+            h = ldpc.code_from_inputs(code)
         batch = max(256, min(args.frames, (1 << 31) // (16 * code.n_edges)))
         ber.simulate(h, code, args.ebn0, min(batch, args.frames), batch=batch, max_iter=args.max_iter,
                      msg_dtype=args.msg, seed=99)  # warm-up (workspace, kernel set-up)
@@ -67,7 +74,7 @@ def main(argv=None):
                          seed=1)
         sec = time.perf_counter() - t0
         paper_cuda, paper_cpu = PAPER_TABLE3_SECONDS.get(n, (None, None))
-        print(json.dumps({"n": n, "edges": code.n_edges, "frames": args.frames, "ebn0_db": args.ebn0,
+        print(json.dumps({"n": n, "family": args.family, "code": code.name, "edges": code.n_edges, "frames": args.frames, "ebn0_db": args.ebn0,
                           "max_iter": args.max_iter, "msg_dtype": args.msg, "batch": batch, "seconds": sec,
                           "frames_per_s": args.frames / sec, "info_gbps": args.frames * (n // 2) / sec / 1e9,
                           **ber.summary(c, n), "paper_cuda_seconds": paper_cuda, "paper_cpu_o3_seconds": paper_cpu,

@@ -111,3 +111,51 @@ def test_argument_errors(ldpc):
     assert lib.ldpc_gen_awgn(1, 0, 1, 4, ctypes.c_float(0.0), None, None, None) == -1
     assert lib.ldpc_gen_awgn(1, 0, -1, 4, ctypes.c_float(1.0), None, None, None) == -1
     assert lib.ldpc_philox4x64_10(0, 0, 0, 0, -1, None, None) == -1
+
+
+def test_qc_lifting_matches_the_expanded_matrix(ldpc, oracle_mod):
+    """Lifting in the library gives the Table 1-2 arrays of the explicitly
+    expanded H (the oracle's address iterators), including parallel
+    protograph edges (two shifts at one block)."""
+    Z = 7
+    entries = [(0, 0, 0), (0, 1, 3), (0, 1, 5), (1, 0, 6), (1, 2, 1), (2, 2, 0), (2, 3, 4), (1, 3, 2)]
+    code = I.qc_code(3, 4, Z, entries)
+    h = ldpc.ldpc_code_create_qc(3, 4, Z, entries, device=-1)
+    got = ldpc.ldpc_code_tables(h)
+    want = oracle_mod.address_iterators(code)
+    for name in ("v", "c", "t", "s", "u", "ebar", "vbar", "cbar", "tbar", "sbar", "ubar"):
+        np.testing.assert_array_equal(got[name], want[name], err_msg=name)
+    dense = np.zeros((3 * Z, 4 * Z), dtype=np.int64)
+    np.add.at(dense, (code.rows, code.cols), 1)
+    assert dense.max() == 1 and dense.sum() == len(entries) * Z
+    # block (0, 1) holds P^3 + P^5: row t has ones at columns 7 + (t + 3) % 7 and 7 + (t + 5) % 7
+    for t in range(Z):
+        assert set(np.flatnonzero(dense[t, Z:2 * Z])) == {(t + 3) % Z, (t + 5) % Z}
+    info = ldpc.ldpc_code_info(h)
+    assert info["ira_k"] == -1 and info["m"] == 3 * Z and info["n"] == 4 * Z
+
+
+def test_qc_lifting_errors(ldpc):
+    with pytest.raises(ldpc.LdpcError) as e:
+        ldpc.ldpc_code_create_qc(2, 2, 4, [(0, 0, 4)], device=-1)
+    assert e.value.status == -1
+    with pytest.raises(ldpc.LdpcError) as e:
+        ldpc.ldpc_code_create_qc(2, 2, 4, [(2, 0, 1)], device=-1)
+    assert e.value.status == -1
+    with pytest.raises(ldpc.LdpcError) as e:
+        ldpc.ldpc_code_create_qc(2, 2, 4, [(0, 0, 1), (1, 1, 0), (0, 0, 1)], device=-1)
+    assert "repeats" in str(e.value)
+    with pytest.raises(ldpc.LdpcError):
+        ldpc.ldpc_code_create_qc(2, 2, 0, [], device=-1)
+
+
+def test_ira_form_is_detected(ldpc):
+    for code in (I.small_code_n1008(), I.mixed_codes()[4]):
+        h = ldpc.ldpc_code_create(code.m, code.n, code.rows, code.cols, device=-1)
+        assert ldpc.ldpc_code_info(h)["ira_k"] == code.k == code.n - code.m, code.name
+    # swapping the last staircase column with information column 0 leaves IRA form
+    code = I.small_code_n1008()
+    last = code.n - 1
+    cols = np.where(code.cols == last, 0, np.where(code.cols == 0, last, code.cols))
+    h = ldpc.ldpc_code_create(code.m, code.n, code.rows, cols, device=-1)
+    assert ldpc.ldpc_code_info(h)["ira_k"] == -1
