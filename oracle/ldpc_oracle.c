@@ -46,6 +46,15 @@
  *   same sign rule; alpha < 1 is the normalised, beta > 0 the offset variant.
  *   An empty minimum (degree-1 check) is L_MAX.
  *
+ *   Tabulated phi (rule 2; the paper's "look-up tables" direction for further
+ *   speed-up): phi is replaced by its chords on a log-spaced grid. The bucket
+ *   of x >= 0 is the top 15 bits of the IEEE single-precision pattern of x
+ *   (sign, 8 exponent bits, 6 mantissa bits): 64 buckets per octave, bucket
+ *   key k spanning [e_k, e_(k+1)) with e_k the float whose bits are k << 17.
+ *   On a bucket, phi_T(x) = phi(e_k) + (x - e_k) (phi(e_(k+1)) - phi(e_k)) /
+ *   (e_(k+1) - e_k), a continuous piecewise-linear function; the check rule
+ *   is the sum-product rule with phi_T in place of phi (same saturation).
+ *
  *   Quantised message storage (the paper's "lower precision" direction for
  *   further speed-up; its own decoder keeps FP64): when qstep > 0 every
  *   check-to-bit message is stored as r = k * qstep, k = r / qstep rounded to
@@ -134,7 +143,33 @@ static double phi_hat(double x, double l_max) {
     return phi(x);
 }
 
-/* Check rule selection: 0 = sum-product, 1 = min-sum family. */
+/* phi_T: phi on the chords of the log-spaced bucket grid (rule 2). */
+static double bucket_edge(uint32_t key) {
+    uint32_t bits = key << 17;
+    float f;
+    memcpy(&f, &bits, sizeof f);
+    return (double)f;
+}
+
+static double phi_chord(double x) {
+    float xf = (float)x;  /* the bucket is chosen on the single-precision value */
+    uint32_t bits;
+    memcpy(&bits, &xf, sizeof bits);
+    uint32_t key = bits >> 17;
+    double lo = bucket_edge(key), hi = bucket_edge(key + 1);
+    double plo = phi(lo), phi_hi = phi(hi);
+    return plo + (x - lo) * (phi_hi - plo) / (hi - lo);
+}
+
+static double phi_chord_hat(double x, double l_max) {
+    double lo = phi(l_max);
+    if (x < lo) x = lo;
+    if (x > l_max) x = l_max;
+    return phi_chord(x);
+}
+
+/* Check rule selection: 0 = sum-product, 1 = min-sum family, 2 = sum-product
+ * with tabulated phi. */
 typedef struct {
     int rule;
     double alpha, beta;
@@ -171,13 +206,14 @@ static void check_update_min_sum(const orc_graph *g, int32_t i, const double *q,
     }
 }
 
-/* Check-node rule for one check: r[e] for every e in N_i from q[e]. */
+/* Check-node rule for one check: r[e] for every e in N_i from q[e];
+ * `table` selects phi_T for phi. */
 static void check_update(const orc_graph *g, int32_t i, const double *q, double *r, double l_max,
-                         double *mag, int *one) {
+                         double *mag, int *one, int table) {
     int64_t b = g->cstart[i], d = g->cstart[i + 1] - b;
     for (int64_t k = 0; k < d; ++k) {
         double qk = q[g->cedge[b + k]];
-        mag[k] = phi_hat(fabs(qk), l_max);
+        mag[k] = table ? phi_chord_hat(fabs(qk), l_max) : phi_hat(fabs(qk), l_max);
         one[k] = qk > 0.0;
     }
     for (int64_t k = 0; k < d; ++k) {
@@ -188,7 +224,7 @@ static void check_update(const orc_graph *g, int32_t i, const double *q, double 
             s += mag[k2];
             parity ^= one[k2];
         }
-        double a = phi_hat(s, l_max);
+        double a = table ? phi_chord_hat(s, l_max) : phi_hat(s, l_max);
         r[g->cedge[b + k]] = parity ? a : -a;
     }
 }
@@ -213,7 +249,7 @@ static int64_t sp_pass(const orc_graph *g, const double *lam, const double *r_pr
         if (rule && rule->rule == 1)
             check_update_min_sum(g, i, q, r_next, l_max, rule, one);
         else
-            check_update(g, i, q, r_next, l_max, mag, one);
+            check_update(g, i, q, r_next, l_max, mag, one, rule && rule->rule == 2);
     }
     if (rule && rule->qstep > 0.0)
         for (int64_t e = 0; e < g->E; ++e) r_next[e] = quantise(r_next[e], rule);
@@ -252,7 +288,8 @@ int orc_decode(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32
                uint8_t *bits, int32_t *iters, uint8_t *ok, double *post, double *r_out, int32_t n_threads,
                int32_t check_rule, double alpha, double beta, double qstep, int32_t qlevels) {
     if (m < 0 || n < 0 || E < 0 || n_frames < 0 || max_iter < 0 || !(l_max > 0.0)) return -1;
-    if (check_rule < 0 || check_rule > 1 || !(alpha > 0.0) || beta < 0.0) return -1;
+    if (check_rule < 0 || check_rule > 2 || !(alpha > 0.0) || beta < 0.0) return -1;
+    if (check_rule == 2 && !(l_max <= 22.0)) return -1; /* the bucket grid spans [2^-32, 2^5) */
     if (qstep < 0.0 || (qstep > 0.0 && qlevels < 1)) return -1;
     orc_rule rule = {check_rule, alpha, beta, qstep, qlevels};
     orc_graph g;
@@ -308,7 +345,8 @@ int orc_pass(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t
              double *r_next, double *app, uint8_t *bits, int64_t *weight, int32_t n_threads,
              int32_t check_rule, double alpha, double beta, double qstep, int32_t qlevels) {
     if (m < 0 || n < 0 || E < 0 || n_frames < 0 || !(l_max > 0.0)) return -1;
-    if (check_rule < 0 || check_rule > 1 || !(alpha > 0.0) || beta < 0.0) return -1;
+    if (check_rule < 0 || check_rule > 2 || !(alpha > 0.0) || beta < 0.0) return -1;
+    if (check_rule == 2 && !(l_max <= 22.0)) return -1; /* the bucket grid spans [2^-32, 2^5) */
     if (qstep < 0.0 || (qstep > 0.0 && qlevels < 1)) return -1;
     orc_rule rule = {check_rule, alpha, beta, qstep, qlevels};
     orc_graph g;
@@ -335,6 +373,10 @@ int orc_pass(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t
     graph_free(&g);
     return failed ? -1 : 0;
 }
+
+/* phi and its tabulated form, exported for the pins of rule 2. */
+double orc_phi(double x) { return phi(x); }
+double orc_phi_chord(double x) { return phi_chord(x); }
 
 /* Syndrome weights of hard words bits [F][n]: number of unsatisfied checks. */
 int orc_syndrome(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t *cols,

@@ -45,6 +45,10 @@ def _lib():
         lib.orc_decode.restype = ctypes.c_int
         lib.orc_pass.argtypes = [i32, i32, i64, vp, vp, vp, i32, vp, dbl, vp, vp, vp, vp, i32, i32, dbl, dbl, dbl, i32]
         lib.orc_pass.restype = ctypes.c_int
+        lib.orc_phi.argtypes = [dbl]
+        lib.orc_phi.restype = dbl
+        lib.orc_phi_chord.argtypes = [dbl]
+        lib.orc_phi_chord.restype = dbl
         lib.orc_syndrome.argtypes = [i32, i32, i64, vp, vp, vp, i32, vp]
         lib.orc_syndrome.restype = ctypes.c_int
         lib.orc_address_iterators.argtypes = [i32, i32, i64, vp, vp] + [vp] * 11
@@ -71,7 +75,7 @@ def default_threads() -> int:
     return int(os.environ.get("LDPC_ORACLE_THREADS", "1"))
 
 
-RULES = {"sp": 0, "min_sum": 1}
+RULES = {"sp": 0, "min_sum": 1, "sp_table": 2}
 
 # Stored-message formats: (quantisation step, largest |level|); "f64" keeps
 # the messages unrounded, "i8" stores k * 20/127 with |k| <= 127.
@@ -89,6 +93,8 @@ def decode(code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 
            rule: str = "sp", alpha: float = 1.0, beta: float = 0.0, msg="f64"):
     """Sum-product decode (Algorithm 2) of LLRs ``llr`` [F, n] in FP64
     (``rule="min_sum"``: the min-sum family, |r| = clamp(alpha min - beta);
+    ``rule="sp_table"``: sum-product with phi on the chords of a log-spaced
+    grid, 64 buckets per octave;
     ``msg``: a key of :data:`MSG` or a (step, levels) pair for quantised
     message storage).
 
@@ -141,6 +147,16 @@ def sp_pass(code, llr, r_prev=None, *, l_max: float = 20.0, n_threads: int | Non
     if rc != 0:
         raise ValueError("oracle pass rejected its input")
     return {"r": r, "post": app, "bits": bits, "weight": w}
+
+
+def phi(x: float) -> float:
+    """phi(x) = ln((e^x + 1)/(e^x - 1)) as the oracle evaluates it."""
+    return _lib().orc_phi(float(x))
+
+
+def phi_chord(x: float) -> float:
+    """The tabulated phi of rule "sp_table" (chords on 64 buckets per octave)."""
+    return _lib().orc_phi_chord(float(x))
 
 
 def syndrome_weight(code, bits) -> np.ndarray:

@@ -367,3 +367,54 @@ def test_quantised_decoder_keeps_codeword_symmetry(oracle_mod, n1008):
     np.testing.assert_array_equal(flip["bits"], base["bits"] ^ cw)
     np.testing.assert_array_equal(flip["post"], base["post"] * (1.0 - 2.0 * cw))
     assert base["ok"].mean() > 0.5
+
+
+# --- tabulated phi (rule "sp_table") ------------------------------------------------
+
+def test_tabulated_phi_is_the_chord_of_a_convex_function(oracle_mod):
+    """phi is convex on (0, inf), so each chord lies on or above it and meets
+    it at the bucket edges; with 64 buckets per octave the chord stays within
+    a small relative distance. Edges are floats whose bits are key << 17."""
+    import struct
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([np.exp(rng.uniform(np.log(4e-9), np.log(22.0), 4000)), [1e-8, 0.5, 1.0, 2.0, 20.0]])
+    worst_abs = worst_rel_small = worst_rel = 0.0
+    for x in xs:
+        t, p = oracle_mod.phi_chord(x), oracle_mod.phi(x)
+        assert t >= p * (1 - 1e-12)
+        worst_abs = max(worst_abs, t - p)
+        worst_rel = max(worst_rel, (t - p) / p)
+        if x <= 1.0:
+            worst_rel_small = max(worst_rel_small, (t - p) / p)
+    # chord error ~ (bucket width)^2 / 8 * phi'': tiny in absolute terms, and
+    # relative to phi at most ~(x / 64)^2 / 8 where phi ~ 2 e^-x
+    assert worst_abs < 5e-5 and worst_rel_small < 2e-4 and worst_rel < 1e-2, (worst_abs, worst_rel_small, worst_rel)
+    for key in (95 << 6, (120 << 6) + 17, (127 << 6) + 5, (131 << 6) + 63):
+        e = struct.unpack("<f", struct.pack("<I", key << 17))[0]
+        assert abs(oracle_mod.phi_chord(e) - oracle_mod.phi(e)) <= 1e-12 * oracle_mod.phi(e)
+        # continuous across the edge
+        assert abs(oracle_mod.phi_chord(e * (1 - 1e-9)) - oracle_mod.phi_chord(e)) <= 1e-6 * oracle_mod.phi(e)
+
+
+def test_tabulated_rule_tracks_exact_sum_product(oracle_mod, n1008):
+    """One check: the tabulated rule is phi_T(sum phi_T); on the n = 1008 code
+    it decodes like exact sum-product (same decisions on converged frames,
+    posteriors within a few parts per thousand on the first pass)."""
+    code1 = I.coo_code(1, 4, [0] * 4, [0, 1, 2, 3])
+    lam = np.array([[0.7, -1.9, 3.3, 0.2]])
+    out = oracle_mod.sp_pass(code1, lam, rule="sp_table")["r"][0]
+    mags = [oracle_mod.phi_chord(abs(v)) for v in lam[0]]
+    for k in range(4):
+        want = oracle_mod.phi_chord(sum(mags) - mags[k])
+        others = sum(1 for j in range(4) if j != k and lam[0, j] > 0)
+        assert abs(abs(out[k]) - want) < 1e-12 and (out[k] > 0) == (others % 2 == 1)
+    code, cw = n1008
+    llr = I.gaussian_llr(cw[:30], I.sigma2_from_ebn0(2.0, 0.5), seed=12).astype(np.float64)
+    ex = oracle_mod.sp_pass(code, llr)
+    tb = oracle_mod.sp_pass(code, llr, rule="sp_table")
+    assert np.abs(tb["r"] - ex["r"]).max() < 5e-3 * (1 + np.abs(ex["r"]).max())
+    a = oracle_mod.decode(code, llr, 50)
+    b = oracle_mod.decode(code, llr, 50, rule="sp_table")
+    both = (a["ok"] == 1) & (b["ok"] == 1)
+    assert (a["iters"] == b["iters"]).mean() >= 0.9 and abs(int(a["ok"].sum()) - int(b["ok"].sum())) <= 1
+    np.testing.assert_array_equal(a["bits"][both], b["bits"][both])
