@@ -172,17 +172,23 @@ typedef struct {
                            alternate between the two streams), so that one
                            tile's working set can stay in L2; 0 = one tile per
                            stream. Results do not depend on any tuning field */
-    int32_t check_rule; /* LDPC_RULE_SUM_PRODUCT (0, the paper's exact rule)
-                           or LDPC_RULE_MIN_SUM (1): |r| = clamp(alpha m -
+    int32_t check_rule; /* LDPC_RULE_SUM_PRODUCT (0, the paper's exact rule);
+                           LDPC_RULE_MIN_SUM (1): |r| = clamp(alpha m -
                            beta, 0, L_MAX), m the smallest other |q|, same
                            signs -- plain (alpha 1, beta 0), normalised
                            (alpha < 1) or offset (beta > 0) min-sum, a
-                           derived algorithm the paper names              */
+                           derived algorithm the paper names;
+                           LDPC_RULE_SP_TABLE (2): sum-product with phi read
+                           from a table (the paper's look-up-table
+                           direction): phi replaced by its chords on 64
+                           buckets per octave, the bucket of x being the top
+                           15 bits of its float pattern (edges: the floats
+                           with bits key << 17); needs l_max <= 22        */
     float rule_alpha;   /* min-sum scale; <= 0 selects 1                   */
     float rule_beta;    /* min-sum offset, >= 0                            */
 } ldpc_decode_opts_t;
 
-enum { LDPC_RULE_SUM_PRODUCT = 0, LDPC_RULE_MIN_SUM = 1 };
+enum { LDPC_RULE_SUM_PRODUCT = 0, LDPC_RULE_MIN_SUM = 1, LDPC_RULE_SP_TABLE = 2 };
 
 /*
  * Decode n_frames frames.
@@ -376,7 +382,7 @@ int ldpc_gen_bits(uint64_t seed, int64_t frame_offset, int32_t n_frames, int32_t
  * p_i = (H1 u)_i xor p_(i-1), the unique codeword of H with that systematic
  * part (the staircase makes H2 invertible). The paper's simulator takes its
  * codewords as given; this keeps random-codeword simulation on the device.
- * Scratch ((k + m) * ceil(n_frames / 32) words) is stream-ordered
+ * Scratch ((k + m + ceil(m / 64)) * ceil(n_frames / 32) words) is stream-ordered
  * (cudaMallocAsync / cudaFreeAsync on `stream`). Asynchronous.
  * Errors: LDPC_EINVAL when the code is not in IRA form, for n_frames < 0 or
  * NULL buffers; LDPC_ENODEV for a host-only code.

@@ -6,6 +6,7 @@
 // stably sorted by variable (Table 1: e, v, c with segment start s, degree t
 // and rank u); the check order is e stably sorted by check (Table 2: ebar,
 // vbar, cbar, sbar, tbar, ubar).
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +48,7 @@ static void free_device_tables(ldpc_code *c) {
     cudaFree(c->d.edge_slot);
     cudaFree(c->d.bin_checks);
     cudaFree(c->d.bin_desc);
+    cudaFree(c->d.phi_table);
     free_workspace(c->ws);
     for (auto &p : c->prof) {
         cudaEventDestroy(p.start);
@@ -56,6 +58,27 @@ static void free_device_tables(ldpc_code *c) {
     c->d = DeviceTables{};
     c->ws = Workspace{};
     if (prev >= 0) cudaSetDevice(prev);
+}
+
+// Chords of the tabulated phi: bucket key k spans [e_k, e_(k+1)), e_k the
+// float with bits k << 17; on it phi(x) ~ a + b x through (e_k, phi(e_k)) and
+// (e_(k+1), phi(e_(k+1))), computed in double and stored as float.
+static std::vector<float2> phi_chords() {
+    auto edge = [](uint32_t key) {
+        uint32_t bits = key << 17;
+        float f;
+        memcpy(&f, &bits, sizeof f);
+        return (double)f;
+    };
+    auto phi = [](double x) { return std::log1p(2.0 / std::expm1(x)); };
+    std::vector<float2> t((size_t)kPhiTableSize);
+    for (int i = 0; i < kPhiTableSize; ++i) {
+        const double lo = edge(kPhiKey0 + (uint32_t)i), hi = edge(kPhiKey0 + (uint32_t)i + 1);
+        const double plo = phi(lo), phi_hi = phi(hi);
+        const double b = (phi_hi - plo) / (hi - lo);
+        t[(size_t)i] = make_float2((float)(plo - b * lo), (float)b);
+    }
+    return t;
 }
 
 template <typename T>
@@ -190,6 +213,7 @@ extern "C" int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t
             (e = upload(&c->d.edge_slot, c->edge_slot)) != cudaSuccess ||
             (e = upload(&c->d.bin_checks, c->bin_checks)) != cudaSuccess ||
             (e = upload(&c->d.bin_desc, c->bin_desc)) != cudaSuccess ||
+            (e = upload(&c->d.phi_table, phi_chords())) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&c->ws.last_use, cudaEventDisableTiming)) != cudaSuccess) {
             int st = cuda_error(e, "ldpc_code_create: device upload");
             free_device_tables(c);

@@ -37,8 +37,9 @@ __global__ void k_interleave(const float *__restrict__ llr, float *__restrict__ 
 }
 
 // done bits: padding frames (f >= F) start as stopped.
-__global__ void k_init_done(uint32_t *done, int32_t F, int32_t Fp) {
+__global__ void k_init_done(uint32_t *done, uint32_t *status, int32_t F, int32_t Fp) {
     int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w == 0) *status = 0u;
     if (w >= Fp / 32) return;
     uint32_t bits = 0;
     for (int b = 0; b < 32; ++b)
@@ -101,10 +102,15 @@ __global__ void k_finalize(const float *__restrict__ app, uint8_t *__restrict__ 
 }
 
 // Per-frame iteration count and syndrome status.
-__global__ void k_frame_results(const uint32_t *done, const int32_t *stop_iter, const uint32_t *final_unsat,
-                                int32_t F, int32_t max_iter, int32_t *iters, uint8_t *ok) {
+__global__ void k_frame_results(const uint32_t *done, const uint32_t *status, const int32_t *stop_iter,
+                                const uint32_t *final_unsat, int32_t F, int32_t max_iter, int32_t *iters, uint8_t *ok) {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= F) return;
+    if (*status != 0u) {  // a device wait of the call gave up: no result
+        iters[f] = -1;
+        ok[f] = 0;
+        return;
+    }
     bool stopped = frame_bit(done, f);
     iters[f] = stopped ? stop_iter[f] : max_iter;
     ok[f] = stopped ? 1 : (frame_bit(final_unsat, f) ? 0 : 1);
@@ -160,7 +166,7 @@ static int ensure_workspace_dims(Workspace &w, int32_t n, int64_t E, int32_t Fp,
         if ((e = grow(&w.lamT, (size_t)n * cap)) != cudaSuccess ||
             (e = grow(&w.app, (size_t)n * cap)) != cudaSuccess ||
             (e = grow(reinterpret_cast<char **>(&w.r), (size_t)E * cap * mb)) != cudaSuccess ||
-            (e = grow(&w.done, (size_t)cap / 32)) != cudaSuccess ||
+            (e = grow(&w.done, (size_t)cap / 32 + 1)) != cudaSuccess ||
             (e = grow(&w.stop_iter, (size_t)cap)) != cudaSuccess) {
             w.fp_cap = 0;
             w.iter_cap = -1;
@@ -242,6 +248,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     a.col_idx = c->d.col_idx;
     a.col_ptr = c->d.col_ptr;
     a.edge_slot = c->d.edge_slot;
+    a.phi_table = c->d.phi_table;
     a.lamT = w.lamT;
     a.app = w.app;
     a.r = w.r;
@@ -256,7 +263,9 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     a.phi_lmax = (float)std::log1p(2.0 / std::expm1((double)l_max));
     a.c_min = (float)(2.0 / (std::exp((double)l_max) + 1.0));
     a.c_max = (float)(-std::expm1(-(double)l_max));
+    a.t_min = (float)std::exp(-(double)l_max);
     a.done = w.done;
+    a.status = w.done + w.fp_cap / 32;  // the word after the frame bits
     a.unsat = w.unsat;
     a.stop_iter = w.stop_iter;
     a.grid_ctas = std::max(1, c->sm_count) * 4;
@@ -274,7 +283,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     e = L(LDPC_K_OTHER, 1, [&] {
         cudaError_t ee = cudaMemsetAsync(w.unsat, 0, sizeof(uint32_t) * (size_t)(max_iter + 1) * words, s);
         if (ee != cudaSuccess) return ee;
-        k_init_done<<<(words + 127) / 128, 128, 0, s>>>(w.done, F, Fp);
+        k_init_done<<<(words + 127) / 128, 128, 0, s>>>(w.done, a.status, F, Fp);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -373,7 +382,8 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
             dim3 grid((unsigned)((c->n + 31) / 32), (unsigned)((F + 31) / 32), 1);
             k_finalize<<<grid, dim3(32, 8, 1), 0, s>>>(w.app, bits, post, c->n, F, Fp);
         }
-        k_frame_results<<<(F + 255) / 256, 256, 0, s>>>(w.done, w.stop_iter, final_row, F, max_iter, iters, ok);
+        k_frame_results<<<(F + 255) / 256, 256, 0, s>>>(w.done, a.status, w.stop_iter, final_row, F, max_iter, iters,
+                                                        ok);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -399,8 +409,11 @@ static int check_decode_args(const ldpc_code *c, int32_t F, int32_t max_iter, co
         return set_error(LDPC_EINVAL, "%s: frames_per_lane=%d not in {0, 1, 2, 4, 8}", fn, o.frames_per_lane);
     if (o.streams < 0 || o.streams > 2) return set_error(LDPC_EINVAL, "%s: streams=%d not in {0, 1, 2}", fn, o.streams);
     if (o.tile_frames < 0) return set_error(LDPC_EINVAL, "%s: tile_frames=%d < 0", fn, o.tile_frames);
-    if (o.check_rule != LDPC_RULE_SUM_PRODUCT && o.check_rule != LDPC_RULE_MIN_SUM)
+    if (o.check_rule != LDPC_RULE_SUM_PRODUCT && o.check_rule != LDPC_RULE_MIN_SUM &&
+        o.check_rule != LDPC_RULE_SP_TABLE)
         return set_error(LDPC_EINVAL, "%s: unknown check_rule %d", fn, o.check_rule);
+    if (o.check_rule == LDPC_RULE_SP_TABLE && !(l_max <= kPhiTableMaxLmax))
+        return set_error(LDPC_EINVAL, "%s: the tabulated rule needs l_max <= 22 (got %g)", fn, (double)l_max);
     if (!(o.rule_beta >= 0.0f) || !std::isfinite(o.rule_alpha))
         return set_error(LDPC_EINVAL, "%s: rule_beta must be >= 0 and rule_alpha finite", fn);
     if (!msg_dtype_valid(o.msg_dtype)) return set_error(LDPC_EINVAL, "%s: unknown msg_dtype %d", fn, o.msg_dtype);

@@ -7,17 +7,17 @@
 // Frames travel bit-sliced: word g of a row holds one bit of frames
 // 32g .. 32g + 31, so one XOR combines 32 frames.
 //   1. pack      u [F][k] bytes      -> U [k][G] words
-//   2. checks    s_i = xor over the H1 neighbours of check i of U[j]
-//   3. prefix    p_i = s_0 xor ... xor s_i, per word column (block scan)
-//   4. write     c [F][n] bytes: the information bytes, then bit f of P
+//   2. checks    s_i = xor over the H1 neighbours of check i of U[j], and
+//                its running xor within a chunk of checks
+//   3. carries   exclusive xor-scan of the chunk totals
+//   4. write     c [F][n] bytes: the information bytes, then bit f of
+//                p_i = (running xor) xor (carry of the chunk)
 #include <algorithm>
 
 #include "ldpc_internal.h"
 
 namespace ldpc {
 namespace {
-
-constexpr int kScanThreads = 1024;
 
 __global__ void k_pack_info(const uint8_t *__restrict__ info, int32_t F, int32_t k, int32_t G,
                             uint32_t *__restrict__ U) {
@@ -31,61 +31,63 @@ __global__ void k_pack_info(const uint8_t *__restrict__ info, int32_t F, int32_t
     }
 }
 
-__global__ void k_check_words(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, int32_t m,
-                              int32_t k, int32_t G, const uint32_t *__restrict__ U, uint32_t *__restrict__ S) {
-    const int64_t total = (int64_t)m * G;
+// Checks are scanned in chunks of kChunk: one thread per (chunk, word
+// column) forms s_i and its running xor inside the chunk, then one warp per
+// word column turns the chunk totals into carries, and the write kernel
+// applies the carry of each chunk.
+constexpr int kChunk = 64;
+
+__global__ void k_chunk_prefix(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, int32_t m,
+                               int32_t k, int32_t G, const uint32_t *__restrict__ U, uint32_t *__restrict__ Pl,
+                               uint32_t *__restrict__ T) {
+    const int32_t nC = (m + kChunk - 1) / kChunk;
+    const int64_t total = (int64_t)nC * G;
     for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < total;
          id += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = (int32_t)(id / G);
-        const int32_t g = (int32_t)(id - (int64_t)i * G);
-        uint32_t s = 0;
-        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            const int32_t j = col_idx[e];
-            if (j < k) s ^= U[(size_t)j * G + g];
+        const int32_t c = (int32_t)(id / G);
+        const int32_t g = (int32_t)(id - (int64_t)c * G);
+        const int32_t i1 = min(m, (c + 1) * kChunk);
+        uint32_t run = 0;
+        for (int32_t i = c * kChunk; i < i1; ++i) {
+            uint32_t s = 0;
+            for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                const int32_t j = col_idx[e];
+                if (j < k) s ^= U[(size_t)j * G + g];
+            }
+            run ^= s;
+            Pl[(size_t)i * G + g] = run;
         }
-        S[(size_t)i * G + g] = s;
+        T[(size_t)c * G + g] = run;
     }
 }
 
-// Inclusive xor-scan over the checks of one word column g, in place.
-__global__ void __launch_bounds__(kScanThreads) k_prefix_xor(uint32_t *__restrict__ S, int32_t m, int32_t G) {
-    __shared__ uint32_t warp_tot[kScanThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t chunk = (m + kScanThreads - 1) / kScanThreads;
-    const int32_t i0 = min(m, (int32_t)threadIdx.x * chunk), i1 = min(m, i0 + chunk);
-    for (int32_t g = blockIdx.x; g < G; g += gridDim.x) {
+// Exclusive xor-scan of the chunk totals T[c][g] over c, in place: one warp
+// per word column g.
+__global__ void k_chunk_carry(uint32_t *__restrict__ T, int32_t nC, int32_t G) {
+    const int lane = threadIdx.x & 31;
+    const int32_t per = (nC + 31) / 32;
+    const int32_t c0 = min(nC, lane * per), c1 = min(nC, c0 + per);
+    for (int32_t g = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); g < G; g += gridDim.x * (blockDim.x / 32)) {
         uint32_t x = 0;
-        for (int32_t i = i0; i < i1; ++i) x ^= S[(size_t)i * G + g];
-        // block-wide exclusive xor-scan of the chunk totals
+        for (int32_t c = c0; c < c1; ++c) x ^= T[(size_t)c * G + g];
         uint32_t inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc ^= y;
         }
-        if (lane == 31) warp_tot[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t t = warp_tot[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t ^= y;
-            }
-            warp_tot[lane] = t;  // inclusive over warps
+        uint32_t run = inc ^ x;  // xor of the chunks before this lane's range
+        for (int32_t c = c0; c < c1; ++c) {
+            const uint32_t t = T[(size_t)c * G + g];
+            T[(size_t)c * G + g] = run;
+            run ^= t;
         }
-        __syncthreads();
-        uint32_t run = (inc ^ x) ^ (warp > 0 ? warp_tot[warp - 1] : 0u);
-        for (int32_t i = i0; i < i1; ++i) {
-            run ^= S[(size_t)i * G + g];
-            S[(size_t)i * G + g] = run;
-        }
-        __syncthreads();  // warp_tot is reused by the next column
     }
 }
 
-__global__ void k_write_codeword(const uint8_t *__restrict__ info, const uint32_t *__restrict__ P, int32_t F,
-                                 int32_t n, int32_t k, int32_t G, uint8_t *__restrict__ cw) {
+__global__ void k_write_codeword(const uint8_t *__restrict__ info, const uint32_t *__restrict__ Pl,
+                                 const uint32_t *__restrict__ carry, int32_t F, int32_t n, int32_t k, int32_t G,
+                                 uint8_t *__restrict__ cw) {
     const int64_t total = (int64_t)F * n;
     for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < total;
          id += (int64_t)gridDim.x * blockDim.x) {
@@ -94,8 +96,10 @@ __global__ void k_write_codeword(const uint8_t *__restrict__ info, const uint32_
         uint8_t v;
         if (j < k)
             v = info[(size_t)f * k + j] & 1u;
-        else
-            v = (uint8_t)((P[(size_t)(j - k) * G + (f >> 5)] >> (f & 31)) & 1u);
+        else {
+            const int32_t i = j - k, g = f >> 5;
+            v = (uint8_t)(((Pl[(size_t)i * G + g] ^ carry[(size_t)(i / kChunk) * G + g]) >> (f & 31)) & 1u);
+        }
         cw[id] = v;
     }
 }
@@ -126,23 +130,25 @@ extern "C" int ldpc_encode_ira(ldpc_code_t *c, const uint8_t *info, int32_t n_fr
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
     const int32_t G = (n_frames + 31) / 32;
-    // stream-ordered scratch: U [k][G] and S [m][G] words
-    uint32_t *U = nullptr, *S = nullptr;
-    const size_t words = ((size_t)k + (size_t)m) * G;
+    // stream-ordered scratch: U [k][G], Pl [m][G] and T [chunks][G] words
+    const int32_t nC = (m + kChunk - 1) / kChunk;
+    uint32_t *U = nullptr;
+    const size_t words = ((size_t)k + (size_t)m + (size_t)nC) * G;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&U), sizeof(uint32_t) * std::max<size_t>(words, 1), s);
     if (e == cudaSuccess) {
-        S = U + (size_t)k * G;
+        uint32_t *Pl = U + (size_t)k * G;
+        uint32_t *T = Pl + (size_t)m * G;
         if (k > 0) {
             dim3 grid((unsigned)((k + 255) / 256), (unsigned)std::min(G, 65535));
             k_pack_info<<<grid, 256, 0, s>>>(info, n_frames, k, G, U);
         }
         if (m > 0) {
-            k_check_words<<<grid_of((int64_t)m * G, 256, c->sm_count), 256, 0, s>>>(c->d.row_ptr, c->d.col_idx, m, k,
-                                                                                    G, U, S);
-            k_prefix_xor<<<(unsigned)std::min(G, 65535), kScanThreads, 0, s>>>(S, m, G);
+            k_chunk_prefix<<<grid_of((int64_t)nC * G, 128, c->sm_count), 128, 0, s>>>(c->d.row_ptr, c->d.col_idx, m,
+                                                                                      k, G, U, Pl, T);
+            k_chunk_carry<<<(unsigned)std::min((G + 7) / 8, 65535), 256, 0, s>>>(T, nC, G);
         }
-        k_write_codeword<<<grid_of((int64_t)n_frames * n, 256, c->sm_count), 256, 0, s>>>(info, S, n_frames, n, k, G,
-                                                                                          codeword);
+        k_write_codeword<<<grid_of((int64_t)n_frames * n, 256, c->sm_count), 256, 0, s>>>(info, Pl, T, n_frames, n, k,
+                                                                                          G, codeword);
         e = cudaGetLastError();
         cudaError_t e2 = cudaFreeAsync(U, s);
         if (e == cudaSuccess) e = e2;

@@ -24,11 +24,11 @@
 
 namespace ldpc {
 
-constexpr int kNumCheckBins = 5;
-// Upper degree bound of each check bin: the first four keep a check's
+constexpr int kNumCheckBins = 6;
+// Upper degree bound of each check bin: the first five keep a check's
 // messages in registers (exclusive sums by prefix/suffix), the last one
 // handles any degree with a compensated two-pass reduction.
-constexpr int kBinMaxDegree[kNumCheckBins] = {4, 8, 16, 32, INT32_MAX};
+constexpr int kBinMaxDegree[kNumCheckBins] = {4, 6, 8, 16, 32, INT32_MAX};
 constexpr int kMaxRegisterDegree = 32;
 
 constexpr int kThreads = 256;  // threads per CTA of the pass kernels (8 warps)
@@ -63,7 +63,14 @@ struct DeviceTables {
     int32_t *edge_slot = nullptr;  // [E]   check-order slot of each edge id (inverse of ebar)
     int32_t *bin_checks = nullptr; // [m']  checks grouped by degree bin
     int2 *bin_desc = nullptr;      // [m']  (first slot, degree) of each binned check
+    float2 *phi_table = nullptr;   // [kPhiTableSize] chords (a, b) of the tabulated phi
 };
+
+// Tabulated phi: bucket key = float bits >> 17 (64 buckets per octave) over
+// [2^-32, 2^5); entry key - kPhiKey0 holds the chord a + b x of the bucket.
+constexpr uint32_t kPhiKey0 = 95u << 6;
+constexpr int kPhiTableSize = 37 * 64;
+constexpr float kPhiTableMaxLmax = 22.0f;
 
 // Arguments of one flooding pass, shared by the kernels of all bins.
 struct PassArgs {
@@ -86,7 +93,9 @@ struct PassArgs {
     float phi_lmax;      // phi(l_max)
     float c_min;         // 1 - tanh(l_max / 2): complement of the largest |r|
     float c_max;         // 1 - e^-l_max: complement of the smallest |r|
+    float t_min;         // e^-l_max: the smallest t = e^-|q| of the product form
     uint32_t *done;      // [Fp/32]
+    uint32_t *status;    // one word, nonzero once a device wait of the call gave up
     uint32_t *unsat;     // [max_iter + 1][Fp/32]
     int32_t *stop_iter;  // [Fp] iteration at which a frame stopped
     int32_t grid_ctas;   // CTAs per launch target (a multiple of the SM count)
@@ -94,7 +103,8 @@ struct PassArgs {
     int32_t check_schedule;  // 0 auto, 1 direct loads, 2 shared-memory pipeline
     int32_t f_begin;     // first frame of the range this launch covers (a multiple of 32 V)
     int32_t f_count;     // frames in that range (a multiple of 32 V)
-    int32_t check_rule;  // 0 sum-product, 1 min-sum family
+    int32_t check_rule;  // 0 sum-product, 1 min-sum family, 2 sum-product with tabulated phi
+    const float2 *phi_table;  // device chords of the tabulated phi (rule 2)
     float ms_alpha;      // min-sum scale
     float ms_beta;       // min-sum offset
 };

@@ -294,6 +294,15 @@ __device__ __forceinline__ void phi_hat_v(float (&x)[V], float l_max, float phi_
     }
 }
 
+// Tabulated phi^: x clamped to [phi(L), L] (L <= 22, so x lies in
+// [2^-32, 2^5)), then the chord a + b x of its bucket, the bucket being the
+// top 15 bits of the float pattern of x.
+__device__ __forceinline__ float phi_tab(float x, float l_max, float phi_lmax, const float2 *tab) {
+    x = fminf(fmaxf(x, phi_lmax), l_max);
+    const float2 ab = tab[(__float_as_uint(x) >> 17) - kPhiKey0];
+    return fmaf(ab.y, x, ab.x);
+}
+
 // Error-free sum: s + err == a + b exactly.
 __device__ __forceinline__ float two_sum(float a, float b, float &err) {
     float s = a + b;
@@ -312,76 +321,77 @@ __device__ __forceinline__ float two_sum(float a, float b, float &err) {
 // products are kept as C = 1 - prod T, merged by C(A u {k}) = C(A) + P(A) D_k
 // and P(A u {k}) = P(A) (1 - D_k) (sums of non-negative terms), and the
 // output magnitude is |r| = ln((1 + P) / (1 - P)) = ln((2 - C) / C).
-// Saturation: |q| is clamped to [phi(L), L] as in phi^, and C to the range
-// that keeps |r| in [phi(L), L]. Scalar and packed forms run the same
-// operations in the same order.
+// Saturation: |q| > L acts as L (t is kept >= e^-L; the lower clamp of phi^,
+// |q| >= phi(L), leaves t = 1 in float and needs no instruction), and C is
+// kept >= 1 - tanh(L / 2) so that |r| <= L; C <= 1 holds up to rounding, so
+// the smallest magnitudes come out as 0 (or a rounding-sized value) instead
+// of phi(L). Scalar and packed forms run the same operations in the same
+// order.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ float tanh_complement(float x, float l_max, float phi_lmax) {
-    x = fminf(fmaxf(x, phi_lmax), l_max);
+__device__ __forceinline__ float tanh_complement(float x, float t_min) {
     float pn = x * -kL2E;
     float e = fmaf(x, kL2E, pn);
     e = fmaf(x, kL2ELo, e);
     float t = ex2_approx(pn);
-    t = fmaf(t, e * -kLn2, t);
+    t = fmaxf(fmaf(t, e * -kLn2, t), t_min);
     float rr = rcp_approx(t + 1.0f);
     return (t + t) * rr;
 }
 
-__device__ __forceinline__ float2 tanh_complement2(float2 x, float l_max, float phi_lmax) {
-    x.x = fminf(fmaxf(x.x, phi_lmax), l_max);
-    x.y = fminf(fmaxf(x.y, phi_lmax), l_max);
+__device__ __forceinline__ float2 tanh_complement2(float2 x, float t_min) {
     float2 pn = mul2(x, f2(-kL2E));
     float2 e = fma2(x, f2(kL2E), pn);
     e = fma2(x, f2(kL2ELo), e);
     float2 t = make_float2(ex2_approx(pn.x), ex2_approx(pn.y));
     t = fma2(t, mul2(e, f2(-kLn2)), t);
+    t = make_float2(fmaxf(t.x, t_min), fmaxf(t.y, t_min));
     float2 tp = add2(t, f2(1.0f));
     float2 rr = make_float2(rcp_approx(tp.x), rcp_approx(tp.y));
     return mul2(add2(t, t), rr);
 }
 
-__device__ __forceinline__ float mag_of_complement(float c, float c_min, float c_max) {
-    c = fminf(fmaxf(c, c_min), c_max);
+__device__ __forceinline__ float mag_of_complement(float c, float c_min) {
+    c = fmaxf(c, c_min);
     float ratio = fmaf(c, -1.0f, 2.0f) * rcp_approx(c);
     return lg2_approx(ratio) * kLn2;
 }
 
-__device__ __forceinline__ float2 mag_of_complement2(float2 c, float c_min, float c_max) {
-    c.x = fminf(fmaxf(c.x, c_min), c_max);
-    c.y = fminf(fmaxf(c.y, c_min), c_max);
+__device__ __forceinline__ float2 mag_of_complement2(float2 c, float c_min) {
+    c.x = fmaxf(c.x, c_min);
+    c.y = fmaxf(c.y, c_min);
     float2 ratio = mul2(fma2(c, f2(-1.0f), f2(2.0f)), make_float2(rcp_approx(c.x), rcp_approx(c.y)));
     return mul2(make_float2(lg2_approx(ratio.x), lg2_approx(ratio.y)), f2(kLn2));
 }
 
 // Element-wise helpers over V frames (packed when V is even).
 template <int V>
-__device__ __forceinline__ void vtanh_complement(float (&x)[V], float l_max, float phi_lmax) {
+__device__ __forceinline__ void vtanh_complement(float (&x)[V], float t_min) {
     if constexpr (V % 2 == 0) {
 #pragma unroll
         for (int v = 0; v < V; v += 2) {
-            float2 y = tanh_complement2(make_float2(x[v], x[v + 1]), l_max, phi_lmax);
+            float2 y = tanh_complement2(make_float2(x[v], x[v + 1]), t_min);
             x[v] = y.x;
             x[v + 1] = y.y;
         }
     } else {
 #pragma unroll
-        for (int v = 0; v < V; ++v) x[v] = tanh_complement(x[v], l_max, phi_lmax);
+        for (int v = 0; v < V; ++v) x[v] = tanh_complement(x[v], t_min);
     }
 }
 
 template <int V>
-__device__ __forceinline__ void vmag_of_complement(float (&c)[V], float c_min, float c_max) {
+__device__ __forceinline__ void vmag_of_complement(float (&c)[V], float c_min) {
     if constexpr (V % 2 == 0) {
 #pragma unroll
         for (int v = 0; v < V; v += 2) {
-            float2 y = mag_of_complement2(make_float2(c[v], c[v + 1]), c_min, c_max);
+            float2 y = mag_of_complement2(make_float2(c[v], c[v + 1]), c_min);
             c[v] = y.x;
             c[v + 1] = y.y;
         }
     } else {
 #pragma unroll
-        for (int v = 0; v < V; ++v) c[v] = mag_of_complement(c[v], c_min, c_max);
+        for (int v = 0; v < V; ++v) c[v] = mag_of_complement(c[v], c_min);
     }
 }
 
@@ -557,7 +567,7 @@ __device__ __forceinline__ void check_node(int d, bool first, bool syn, Load &&l
                     ones[v] |= (av[v] > 0.0f ? 1u : 0u) << k;
                     dc[k][v] = fabsf(av[v]);
                 }
-                vtanh_complement<V>(dc[k], a.l_max, a.phi_lmax);
+                vtanh_complement<V>(dc[k], a.t_min);
             } else {
     #pragma unroll
                 for (int v = 0; v < V; ++v) dc[k][v] = 0.0f;  // T = 1: neutral
@@ -597,7 +607,7 @@ __device__ __forceinline__ void check_node(int d, bool first, bool syn, Load &&l
             if (k < d) {
                 float o[V];
                 vfma<V>(o, pp, csuf[k], cp);  // C of all inputs but k
-                vmag_of_complement<V>(o, a.c_min, a.c_max);
+                vmag_of_complement<V>(o, a.c_min);
     #pragma unroll
                 for (int v = 0; v < V; ++v)
                     o[v] = __int_as_float(__float_as_int(o[v]) | (int)((neg[v] << (31 - k)) & 0x80000000u));
@@ -660,7 +670,7 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
                     if (!first) av[q] = fma2(rv[q], f2(-1.0f), av[q]);
                     ones[2 * q] |= (av[q].x > 0.0f ? 1u : 0u) << k;
                     ones[2 * q + 1] |= (av[q].y > 0.0f ? 1u : 0u) << k;
-                    dc[k][q] = tanh_complement2(make_float2(fabsf(av[q].x), fabsf(av[q].y)), a.l_max, a.phi_lmax);
+                    dc[k][q] = tanh_complement2(make_float2(fabsf(av[q].x), fabsf(av[q].y)), a.t_min);
                 }
             } else {
     #pragma unroll
@@ -702,7 +712,7 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
                 float2 o[P];
     #pragma unroll
                 for (int q = 0; q < P; ++q) {
-                    o[q] = mag_of_complement2(fma2(pp[q], csuf[k][q], cp[q]), a.c_min, a.c_max);
+                    o[q] = mag_of_complement2(fma2(pp[q], csuf[k][q], cp[q]), a.c_min);
                     o[q].x = __int_as_float(__float_as_int(o[q].x) | (int)((neg[2 * q] << (31 - k)) & 0x80000000u));
                     o[q].y = __int_as_float(__float_as_int(o[q].y) | (int)((neg[2 * q + 1] << (31 - k)) & 0x80000000u));
                     cp[q] = fma2(pp[q], dc[k][q], cp[q]);
@@ -711,6 +721,86 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
                 store_pairs<M, P>(out + (size_t)k * Fp, o);
             }
         }
+    }
+}
+
+// The sum-product rule for checks whose D input rows are all readable
+// (the shared-memory ring of the pipelined kernel): every one of the D slots
+// is computed without a branch and the d <= D real inputs are selected by
+// predicates, so a bin whose checks mostly have degree D pays no control
+// flow per edge. Slots k >= d become neutral inputs (D_k = 0, no sign, no
+// syndrome term) and their outputs are not stored. Same operations, same
+// order, same results as check_node_pairs for the real inputs.
+template <int D, int P, typename M, bool kFirst, bool kSyn, typename Load>
+__device__ __forceinline__ void check_node_pairs_masked(int d, Load &&load, M *out, size_t Fp, const PassArgs &a,
+                                                        bool (&unsat)[2 * P]) {
+    const float t_min = a.t_min, c_min = a.c_min;
+    float2 dc[D][P];
+    uint32_t ones[2 * P];
+    uint32_t z[2 * P];
+#pragma unroll
+    for (int v = 0; v < 2 * P; ++v) ones[v] = z[v] = 0u;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const bool real = k < d;
+        float2 av[P], rv[P];
+        load(k, av, rv);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            if constexpr (kSyn) {
+                z[2 * q] ^= (real && av[q].x > 0.0f) ? 1u : 0u;
+                z[2 * q + 1] ^= (real && av[q].y > 0.0f) ? 1u : 0u;
+            }
+            if constexpr (!kFirst) av[q] = fma2(rv[q], f2(-1.0f), av[q]);
+            ones[2 * q] |= ((real && av[q].x > 0.0f) ? 1u : 0u) << k;
+            ones[2 * q + 1] |= ((real && av[q].y > 0.0f) ? 1u : 0u) << k;
+            const float2 t = tanh_complement2(make_float2(fabsf(av[q].x), fabsf(av[q].y)), t_min);
+            dc[k][q] = make_float2(real ? t.x : 0.0f, real ? t.y : 0.0f);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 2 * P; ++v) unsat[v] |= z[v] != 0u;
+    float2 csuf[D][P];
+    {
+        float2 cr[P], pr[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            cr[q] = f2(0.0f);
+            pr[q] = f2(1.0f);
+        }
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                csuf[k][q] = cr[q];
+                cr[q] = fma2(pr[q], dc[k][q], cr[q]);
+                pr[q] = mul2(pr[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
+            }
+        }
+    }
+    float2 cp[P], pp[P];
+    uint32_t neg[2 * P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        cp[q] = f2(0.0f);
+        pp[q] = f2(1.0f);
+    }
+#pragma unroll
+    for (int v = 0; v < 2 * P; ++v) neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float2 o[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            o[q] = mag_of_complement2(fma2(pp[q], csuf[k][q], cp[q]), c_min);
+            o[q].x = __int_as_float(__float_as_int(o[q].x) | (int)((neg[2 * q] << (31 - k)) & 0x80000000u));
+            o[q].y = __int_as_float(__float_as_int(o[q].y) | (int)((neg[2 * q + 1] << (31 - k)) & 0x80000000u));
+            if (k + 1 < D) {
+                cp[q] = fma2(pp[q], dc[k][q], cp[q]);
+                pp[q] = mul2(pp[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
+            }
+        }
+        if (k < d) store_pairs<M, P>(out + (size_t)k * Fp, o);
     }
 }
 
@@ -778,46 +868,75 @@ __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_
 }
 
 // ---------------------------------------------------------------------------
-// Software-pipelined check kernel: every warp streams the rows of its next
-// S - 1 checks into its own shared-memory ring with 16-byte cp.async copies
-// while it computes the current one, so row loads overlap the check rule.
-// Check descriptors (first slot, degree) and column indices are fetched one
-// and two checks ahead of their copies.
+// Pipelined check kernel: every warp keeps the APP and message rows of its
+// next S - 1 checks in flight into its own shared-memory ring while it
+// computes the current one. The rows arrive by bulk copies (cp.async.bulk,
+// the copy engine): lane k issues one copy for the APP row of input k and one
+// for its message row, completing on the stage's mbarrier, so a check costs
+// the warp two copy instructions per input instead of one 16-byte copy per
+// lane and chunk. Check descriptors (first slot, degree) and column indices
+// are fetched one and two checks ahead of their copies. Waits on an mbarrier
+// give up after kSpinLimit polls: the warp then flags the call (status word)
+// and stops.
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 template <int D, int V, typename M>
 struct PipeShape {
     static constexpr int kRowA = 32 * V * 4;                  // bytes of one APP row segment
     static constexpr int kRowR = 32 * V * (int)sizeof(M);     // bytes of one message row segment
-    static constexpr int kChunksA = kRowA / 16;
-    static constexpr int kChunksR = kRowR / 16;
     static constexpr int kStage = D * (kRowA + kRowR);        // bytes of one check's rows
 };
 
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for phase `parity` of a barrier; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+template <int D, int V, typename M, int S>
+struct BulkShape {
+    static constexpr int kBarBytes = ((kThreads / 32) * S * 8 + 127) / 128 * 128;  // mbarriers, then the rings
+    static constexpr int kSmem = kBarBytes + (kThreads / 32) * S * PipeShape<D, V, M>::kStage;
+};
+
 template <int D, int V, typename M, int S, int MODE, int RULE>
-__global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 *__restrict__ desc, int32_t count) {
+__global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 *__restrict__ desc, int32_t count) {
     using P = PipeShape<D, V, M>;
+    using B = BulkShape<D, V, M, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    unsigned char *ring = smem + (size_t)warp * S * P::kStage;
+    unsigned char *ring = smem + B::kBarBytes + (size_t)warp * S * P::kStage;
+    const uint32_t bar0 = smem_u32(smem) + (uint32_t)(warp * S * 8);
     const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
     const int fbase = g * 32 * V;
     const int f0 = fbase + lane * V;
     const size_t Fp = (size_t)a.Fp;
     M *r = reinterpret_cast<M *>(a.r);
-    // MODE: 0 = first pass (q = lambda), 1 = later pass, 2 = later pass that
-    // also tests the previous hard decision (compile-time, no per-edge tests)
     constexpr bool first = MODE == 0;
     constexpr bool syn = MODE == 2;
     const float *qsrc = first ? a.lamT : a.app;
@@ -834,45 +953,38 @@ __global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 
 #pragma unroll
     for (int v = 0; v < V; ++v) unsat[v] = false;
 
+    if (lane < S) mbar_init(bar0 + 8 * lane, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    __syncwarp();
+
     const int stride = gridDim.x * (kThreads / 32);
     const int w0 = blockIdx.x * (kThreads / 32) + warp;
+    constexpr uint32_t kTx = (uint32_t)P::kRowA + (first ? 0u : (uint32_t)P::kRowR);  // bytes per input
 
-    // Copy the d APP rows (and message rows) of one check into ring stage st.
+    // Copy the rows of one check (first slot b, degree d, lane k holding the
+    // column of input k) into stage st.
     auto issue = [&](int st, int b, int d, int jl) {
-        unsigned char *base = ring + st * P::kStage;
-        const int nA = d * P::kChunksA;
-        for (int c0 = 0; c0 < nA; c0 += 32) {
-            const int c = c0 + lane;
-            const int k = min(c / P::kChunksA, 31);
-            const int j = __shfl_sync(kFull, jl, k);
-            if (c < nA) {
-                const int o = c - k * P::kChunksA;
-                cp_async16(base + k * P::kRowA + o * 16,
-                           reinterpret_cast<const unsigned char *>(qsrc + (size_t)j * Fp + fbase) + o * 16);
-            }
-        }
-        if (!first) {
-            const int nR = d * P::kChunksR;
-            for (int c = lane; c < nR; c += 32) {
-                const int k = c / P::kChunksR;
-                const int o = c - k * P::kChunksR;
-                cp_async16(base + D * P::kRowA + k * P::kRowR + o * 16,
-                           reinterpret_cast<const unsigned char *>(r + (size_t)(b + k) * Fp + fbase) + o * 16);
-            }
+        if (d <= 0) return;
+        const uint32_t bar = bar0 + 8 * st;
+        if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)d * kTx);
+        __syncwarp();
+        if (lane < d) {
+            const uint32_t base = smem_u32(ring + st * P::kStage);
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            bulk_g2s(base + lane * P::kRowA, qsrc + (size_t)jl * Fp + fbase, P::kRowA, bar);
+            if (!first)
+                bulk_g2s(base + D * P::kRowA + lane * P::kRowR, r + (size_t)(b + lane) * Fp + fbase, P::kRowR, bar);
         }
     };
     auto get_desc = [&](int w) { return w < count ? desc[w] : make_int2(0, 0); };
     auto get_col = [&](int2 dd) { return lane < dd.y ? a.col_idx[dd.x + lane] : 0; };
 
-    // queue of the checks whose rows are in flight: (first slot, degree)
     int qb[S], qd[S];
-    // prologue: stages 0 .. S-2
     int2 nd = get_desc(w0);
     int njl = get_col(nd);
 #pragma unroll
     for (int s = 0; s < S - 1; ++s) {
         issue(s, nd.x, nd.y, njl);
-        cp_async_commit();
         qb[s] = nd.x;
         qd[s] = nd.y;
         nd = get_desc(w0 + (s + 1) * stride);
@@ -880,18 +992,22 @@ __global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 
     }
     int2 nd2 = get_desc(w0 + S * stride);
     int n = 0;
+    bool timed_out = false;
     for (int w = w0; w < count; w += stride, ++n) {
-        // rows of the check S - 1 ahead
         issue((n + S - 1) % S, nd.x, nd.y, njl);
-        cp_async_commit();
         qb[S - 1] = nd.x;
         qd[S - 1] = nd.y;
         nd = nd2;
         njl = get_col(nd);
         nd2 = get_desc(w + (S + 1) * stride);
-        cp_async_wait<S - 1>();
-        __syncwarp();
-        const unsigned char *base = ring + (n % S) * P::kStage;
+        const int st = n % S;
+        // every lane waits (the wait makes the copied rows visible to it);
+        // the warp gives up together if any lane did
+        if (!__all_sync(kFull, mbar_wait(bar0 + 8 * st, (uint32_t)((n / S) & 1)))) {
+            timed_out = true;
+            break;
+        }
+        const unsigned char *base = ring + st * P::kStage;
         static_assert(V % 2 == 0, "the pipelined kernel runs frame pairs");
         auto load = [&](int k, float2 (&av)[V / 2], float2 (&rv)[V / 2]) {
             const float2 *pa = reinterpret_cast<const float2 *>(base + k * P::kRowA) + lane * (V / 2);
@@ -900,7 +1016,10 @@ __global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 
             if (!first)
                 load_pairs<V, M>(reinterpret_cast<const M *>(base + D * P::kRowA + k * P::kRowR) + lane * V, rv);
         };
-        check_node_pairs<D, V / 2, M, RULE>(qd[0], first, syn, load, r + (size_t)qb[0] * Fp + f0, Fp, a, unsat);
+        if constexpr (RULE == 0)
+            check_node_pairs_masked<D, V / 2, M, first, syn>(qd[0], load, r + (size_t)qb[0] * Fp + f0, Fp, a, unsat);
+        else
+            check_node_pairs<D, V / 2, M, RULE>(qd[0], first, syn, load, r + (size_t)qb[0] * Fp + f0, Fp, a, unsat);
         __syncwarp();
 #pragma unroll
         for (int s = 0; s < S - 1; ++s) {
@@ -908,7 +1027,15 @@ __global__ void __launch_bounds__(kThreads) k_check_pipe(PassArgs a, const int2 
             qd[s] = qd[s + 1];
         }
     }
-    cp_async_wait<0>();
+    if (timed_out) {
+        // flag the call, then give the copies still in flight a bounded time
+        // to land before the warp leaves
+        if (lane == 0) atomicOr(a.status, 1u);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (qd[s] > 0) mbar_wait(bar0 + 8 * ((n + s) % S), (uint32_t)(((n + s) / S) & 1));
+        return;
+    }
     if (a.syndrome) {
         bool bits[V];
 #pragma unroll
@@ -933,6 +1060,23 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
     M *r = reinterpret_cast<M *>(a.r);
     const bool first = a.pass == 0;
     const float *qsrc = first ? a.lamT : a.app;
+
+    // rule 2: the chords of the tabulated phi, copied to shared memory by the
+    // whole CTA before any warp may leave
+    const float2 *tab = nullptr;
+    if constexpr (RULE == 2) {
+        extern __shared__ __align__(16) unsigned char smem[];
+        float2 *t = reinterpret_cast<float2 *>(smem);
+        for (int i = threadIdx.x; i < kPhiTableSize; i += blockDim.x) t[i] = a.phi_table[i];
+        __syncthreads();
+        tab = t;
+    }
+    auto phi_rule = [&](float x) {
+        if constexpr (RULE == 2)
+            return phi_tab(x, a.l_max, a.phi_lmax, tab);
+        else
+            return phi_hat(x, a.l_max, a.phi_lmax);
+    };
 
     bool live[V];
     bool any_live = false;
@@ -989,7 +1133,7 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
                     }
                 } else {
                     float err;
-                    hi[v] = two_sum(hi[v], phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax), err);
+                    hi[v] = two_sum(hi[v], phi_rule(fabsf(qv[v])), err);
                     lo[v] += err;
                 }
                 par[v] ^= qv[v] > 0.0f ? 1u : 0u;
@@ -1019,11 +1163,11 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
                     const float m = idx[v] == k ? lo[v] : hi[v];
                     mm = fminf(fmaxf(fmaf(a.ms_alpha, m, -a.ms_beta), 0.0f), a.l_max);
                 } else {
-                    float own = phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax);
+                    float own = phi_rule(fabsf(qv[v]));
                     float err;
                     float s = two_sum(hi[v], -own, err);
                     float excl = s + (err + lo[v]);
-                    mm = phi_hat(excl, a.l_max, a.phi_lmax);
+                    mm = phi_rule(excl);
                 }
                 uint32_t others = par[v] ^ (qv[v] > 0.0f ? 1u : 0u);
                 out[v] = others ? mm : -mm;
@@ -1139,8 +1283,8 @@ inline dim3 pass_grid(const PassArgs &a, int64_t nodes, int V) {
 }
 
 // Only the (bin, frames-per-lane) pairs launch_check_rule selects are
-// instantiated: V = 4 for bins 0-1, V = 2 for bins 0-2 and the unbounded bin,
-// V = 1 for every bin.
+// instantiated: V = 4 for bins 0-2 (degree <= 8), V = 2 for bins 0-3 and the
+// unbounded bin, V = 1 for every bin.
 template <int V, typename M, int RULE>
 static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t *checks, int32_t count,
                                       cudaStream_t s) {
@@ -1148,11 +1292,13 @@ static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t 
     if (bin == 0) {
         k_check_reg<4, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
     } else if (bin == 1) {
+        k_check_reg<6, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+    } else if (bin == 2) {
         k_check_reg<8, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
     } else if constexpr (V <= 2) {
-        if (bin == 2) {
+        if (bin == 3) {
             k_check_reg<16, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
-        } else if (bin == 3) {
+        } else if (bin == 4) {
             if constexpr (V == 1) k_check_reg<32, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
             else return cudaErrorInvalidValue;
         } else {
@@ -1167,59 +1313,79 @@ static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t 
 // Pipelined kernel: dynamic shared memory above 48 KB needs an opt-in, and
 // the grid is sized to the CTAs that fit on the GPU at once.
 template <int D, int V, typename M, int S, int MODE, int RULE>
-static cudaError_t launch_pipe_mode(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
+static cudaError_t launch_bulk_mode(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
     static int resident_by_device[64] = {0};  // CTAs per SM, once per device
     int dev = 0;
     cudaGetDevice(&dev);
     int &resident = resident_by_device[dev & 63];
-    const size_t smem = (size_t)(kThreads / 32) * S * PipeShape<D, V, M>::kStage;
+    const size_t smem = (size_t)BulkShape<D, V, M, S>::kSmem;
     if (resident == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_check_pipe<D, V, M, S, MODE, RULE>,
+        cudaError_t e = cudaFuncSetAttribute(k_check_bulk<D, V, M, S, MODE, RULE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_pipe<D, V, M, S, MODE, RULE>, kThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_bulk<D, V, M, S, MODE, RULE>, kThreads, smem);
         if (e != cudaSuccess) return e;
         resident = nb > 0 ? nb : 1;
     }
     PassArgs b = a;
     b.grid_ctas = a.sm_count * resident;
     dim3 grid = pass_grid(b, count, V);
-    k_check_pipe<D, V, M, S, MODE, RULE><<<grid, kThreads, smem, s>>>(a, desc, count);
+    k_check_bulk<D, V, M, S, MODE, RULE><<<grid, kThreads, smem, s>>>(a, desc, count);
     return cudaGetLastError();
 }
 
-// Pipelined kernel: dynamic shared memory above 48 KB needs an opt-in, and
-// the grid is sized to the CTAs that fit on the GPU at once.
 template <int D, int V, typename M, int S, int RULE>
-static cudaError_t launch_pipe(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
-    if (a.pass == 0) return launch_pipe_mode<D, V, M, S, 0, RULE>(a, desc, count, s);
-    if (a.syndrome) return launch_pipe_mode<D, V, M, S, 2, RULE>(a, desc, count, s);
-    return launch_pipe_mode<D, V, M, S, 1, RULE>(a, desc, count, s);
+static cudaError_t launch_bulk(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
+    if (a.pass == 0) return launch_bulk_mode<D, V, M, S, 0, RULE>(a, desc, count, s);
+    if (a.syndrome) return launch_bulk_mode<D, V, M, S, 2, RULE>(a, desc, count, s);
+    return launch_bulk_mode<D, V, M, S, 1, RULE>(a, desc, count, s);
 }
 
 template <typename M, int RULE>
 static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *checks, const int2 *desc,
                                      int32_t count, cudaStream_t s) {
-    if (a.check_schedule != 1 && bin <= 2 && a.f_count % 64 == 0 && a.f_begin % 64 == 0) {
+    // Four frames per lane where the check's state fits the registers (degree
+    // <= 6): the per-edge index, copy and control work is then shared by two
+    // frame pairs. Wider checks run two frames per lane.
+    if (a.check_schedule != 1 && bin <= 1 && a.f_count % 128 == 0 && a.f_begin % 128 == 0) {
+        if (bin == 0) return launch_bulk<4, 4, M, 2, RULE>(a, desc, count, s);
+        return launch_bulk<6, 4, M, 2, RULE>(a, desc, count, s);
+    }
+    if (a.check_schedule != 1 && bin <= 3 && a.f_count % 64 == 0 && a.f_begin % 64 == 0) {
         switch (bin) {
-        case 0: return launch_pipe<4, 2, M, 4, RULE>(a, desc, count, s);
-        case 1: return launch_pipe<8, 2, M, 3, RULE>(a, desc, count, s);
-        default: return launch_pipe<16, 2, M, 2, RULE>(a, desc, count, s);
+        case 0: return launch_bulk<4, 2, M, 4, RULE>(a, desc, count, s);
+        case 1: return launch_bulk<6, 2, M, 3, RULE>(a, desc, count, s);
+        case 2: return launch_bulk<8, 2, M, 3, RULE>(a, desc, count, s);
+        default: return launch_bulk<16, 2, M, 2, RULE>(a, desc, count, s);
         }
     }
     // Wider bins keep more messages per frame in registers: fewer frames per
-    // lane there, to stay clear of spills (bins 2-4 run two frames per lane
-    // at most, bin 3 and the unbounded bin one when V is odd).
-    if (a.V == 4 && bin < 2) return launch_check_bin_v<4, M, RULE>(a, bin, checks, count, s);
-    if (a.V >= 2 && bin != 3) return launch_check_bin_v<2, M, RULE>(a, bin, checks, count, s);
+    // lane there, to stay clear of spills (bins 3-5 run two frames per lane
+    // at most, bin 4 and the unbounded bin one when V is odd).
+    if (a.V == 4 && bin < 3) return launch_check_bin_v<4, M, RULE>(a, bin, checks, count, s);
+    if (a.V >= 2 && bin != 4) return launch_check_bin_v<2, M, RULE>(a, bin, checks, count, s);
     return launch_check_bin_v<1, M, RULE>(a, bin, checks, count, s);
+}
+
+// Rule 2 runs every bin through the any-degree kernel with the table in
+// shared memory.
+template <typename M>
+static cudaError_t launch_check_table(const PassArgs &a, const int32_t *checks, int32_t count, cudaStream_t s) {
+    const size_t smem = sizeof(float2) * kPhiTableSize;
+    if (a.V >= 2) {
+        k_check_any<2, M, 2><<<pass_grid(a, count, 2), kThreads, smem, s>>>(a, checks, count);
+    } else {
+        k_check_any<1, M, 2><<<pass_grid(a, count, 1), kThreads, smem, s>>>(a, checks, count);
+    }
+    return cudaGetLastError();
 }
 
 template <typename M>
 cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, const int2 *desc, int32_t count,
                              cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
+    if (a.check_rule == 2) return launch_check_table<M>(a, checks, count, s);
     if (a.check_rule == 1) return launch_check_rule<M, 1>(a, bin, checks, desc, count, s);
     return launch_check_rule<M, 0>(a, bin, checks, desc, count, s);
 }

@@ -58,6 +58,7 @@ __device__ __forceinline__ bool bit_of(const uint32_t *w, int f) { return (w[f >
 
 __global__ void ks_init_done(uint32_t *done, int32_t F, int32_t Fp) {
     int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w == Fp / 32) done[w] = 0u;  // the status word after the frame bits
     if (w >= Fp / 32) return;
     uint32_t bits = 0;
     for (int b = 0; b < 32; ++b)
@@ -119,10 +120,16 @@ __global__ void ks_finalize(const float *__restrict__ app, uint8_t *__restrict__
     }
 }
 
-__global__ void ks_frame_results(const uint32_t *done, const int32_t *stop_iter, const uint32_t *final_unsat,
-                                 int32_t F, int32_t max_iter, int32_t *iters, uint8_t *ok) {
+__global__ void ks_frame_results(const uint32_t *done, const uint32_t *status, const int32_t *stop_iter,
+                                 const uint32_t *final_unsat, int32_t F, int32_t max_iter, int32_t *iters,
+                                 uint8_t *ok) {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= F) return;
+    if (status[0] != 0u) {  // a device wait of the call gave up: no result
+        iters[f] = -1;
+        ok[f] = 0;
+        return;
+    }
     bool stopped = bit_of(done, f);
     iters[f] = stopped ? stop_iter[f] : max_iter;
     ok[f] = stopped ? 1 : (bit_of(final_unsat, f) ? 0 : 1);
@@ -144,7 +151,7 @@ cudaError_t run_static(ldpc_code *c, unsigned char *scratch, const float *llr, i
     float *lamT = reinterpret_cast<float *>(carve(sizeof(float) * (size_t)c->n * Fp));
     float *app = reinterpret_cast<float *>(carve(sizeof(float) * (size_t)c->n * Fp));
     void *r = carve(sizeof(M) * (size_t)c->E * Fp);
-    uint32_t *done = reinterpret_cast<uint32_t *>(carve(sizeof(uint32_t) * words));
+    uint32_t *done = reinterpret_cast<uint32_t *>(carve(sizeof(uint32_t) * (words + 1)));
     uint32_t *unsat = reinterpret_cast<uint32_t *>(carve(sizeof(uint32_t) * words * (max_iter + 1)));
     int32_t *stop_iter = reinterpret_cast<int32_t *>(carve(sizeof(int32_t) * (size_t)Fp));
 
@@ -153,6 +160,7 @@ cudaError_t run_static(ldpc_code *c, unsigned char *scratch, const float *llr, i
     a.col_idx = c->d.col_idx;
     a.col_ptr = c->d.col_ptr;
     a.edge_slot = c->d.edge_slot;
+    a.phi_table = c->d.phi_table;
     a.lamT = lamT;
     a.app = app;
     a.r = r;
@@ -167,7 +175,9 @@ cudaError_t run_static(ldpc_code *c, unsigned char *scratch, const float *llr, i
     a.phi_lmax = (float)std::log1p(2.0 / std::expm1((double)l_max));
     a.c_min = (float)(2.0 / (std::exp((double)l_max) + 1.0));
     a.c_max = (float)(-std::expm1(-(double)l_max));
+    a.t_min = (float)std::exp(-(double)l_max);
     a.done = done;
+    a.status = done + words;
     a.unsat = unsat;
     a.stop_iter = stop_iter;
     a.grid_ctas = std::max(1, c->sm_count) * 4;
@@ -184,7 +194,7 @@ cudaError_t run_static(ldpc_code *c, unsigned char *scratch, const float *llr, i
     cudaError_t e = cudaMemsetAsync(unsat, 0, sizeof(uint32_t) * words * (max_iter + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(app, 0, sizeof(float) * (size_t)c->n * Fp, s);
     if (e != cudaSuccess) return e;
-    ks_init_done<<<(unsigned)((words + 127) / 128), 128, 0, s>>>(done, F, Fp);
+    ks_init_done<<<(unsigned)((words + 1 + 127) / 128), 128, 0, s>>>(done, F, Fp);
     if (c->n > 0) {
         dim3 grid((unsigned)((c->n + 31) / 32), (unsigned)(Fp / 32), 1);
         ks_interleave<<<grid, dim3(32, 8, 1), 0, s>>>(llr, lamT, c->n, F, Fp);
@@ -211,7 +221,8 @@ cudaError_t run_static(ldpc_code *c, unsigned char *scratch, const float *llr, i
         dim3 grid((unsigned)((c->n + 31) / 32), (unsigned)((F + 31) / 32), 1);
         ks_finalize<<<grid, dim3(32, 8, 1), 0, s>>>(app, bits, post, c->n, F, Fp);
     }
-    ks_frame_results<<<(F + 255) / 256, 256, 0, s>>>(done, stop_iter, final_row, F, max_iter, iters, ok);
+    ks_frame_results<<<(F + 255) / 256, 256, 0, s>>>(done, done + words, stop_iter, final_row, F, max_iter, iters,
+                                                      ok);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (o.r_out) return launch_export_r<M>(a, o.r_out, s);
     return cudaSuccess;
@@ -256,8 +267,11 @@ extern "C" int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int
     if (!(l_max <= 80.0f)) return set_error(LDPC_EINVAL, "ldpc_decode_static: l_max=%g outside (0, 80]", (double)o.l_max);
     if (!msg_dtype_valid(o.msg_dtype)) return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown msg_dtype %d", o.msg_dtype);
     if (o.profile) return set_error(LDPC_EINVAL, "ldpc_decode_static: profiling is not available on this entry point");
-    if (o.check_rule != LDPC_RULE_SUM_PRODUCT && o.check_rule != LDPC_RULE_MIN_SUM)
+    if (o.check_rule != LDPC_RULE_SUM_PRODUCT && o.check_rule != LDPC_RULE_MIN_SUM &&
+        o.check_rule != LDPC_RULE_SP_TABLE)
         return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown check_rule %d", o.check_rule);
+    if (o.check_rule == LDPC_RULE_SP_TABLE && !(l_max <= kPhiTableMaxLmax))
+        return set_error(LDPC_EINVAL, "ldpc_decode_static: the tabulated rule needs l_max <= 22");
     if (!(o.rule_beta >= 0.0f) || !std::isfinite(o.rule_alpha))
         return set_error(LDPC_EINVAL, "ldpc_decode_static: rule_beta must be >= 0 and rule_alpha finite");
     if (o.check_schedule < 0 || o.check_schedule > 2)
@@ -275,7 +289,8 @@ extern "C" int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int
     const size_t msg = (size_t)msg_bytes(o.msg_dtype);
     const size_t words = (size_t)Fp / 32;
     const size_t need = align256(4 * (size_t)c->n * Fp) * 2 + align256(msg * (size_t)c->E * Fp) +
-                        align256(4 * words) + align256(4 * words * ((size_t)max_iter + 1)) + align256(4 * (size_t)Fp);
+                        align256(4 * (words + 1)) + align256(4 * words * ((size_t)max_iter + 1)) +
+                        align256(4 * (size_t)Fp);
     if (need > kStaticScratchBytes)
         return set_error(LDPC_EINVAL,
                          "ldpc_decode_static: %d frames of this code need %zu bytes of scratch; the static scratch "

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 LDPC_MSG = {"f32": 0, "f16": 1, "bf16": 2, "i8": 3}
-LDPC_RULE = {"sum_product": 0, "min_sum": 1}
+LDPC_RULE = {"sum_product": 0, "min_sum": 1, "sp_table": 2}
 KERNEL_CLASSES = ("interleave", "check", "bit", "syndrome", "finalize", "other", "passes")
 
 

@@ -82,14 +82,14 @@ def test_code_info_and_degree_bins(ldpc):
     info = ldpc.ldpc_code_info(h)
     assert info["m"] == 32400 and info["n"] == 64800 and info["n_edges"] == 194399
     assert info["max_check_degree"] == 6 and info["max_var_degree"] == 8
-    assert info["check_bin_count"] == [0, 32400, 0, 0, 0]
+    assert info["check_bin_count"] == [0, 32400, 0, 0, 0, 0]
     assert info["device"] == -1
     big = I.ira_code(8192, 6144, {3: 0.7, 4: 0.3}, seed=3, var_degree_overrides={0: 64},
                      check_h1_overrides={5: 94})
     hb = ldpc.ldpc_code_create(big.m, big.n, big.rows, big.cols, device=-1)
     ib = ldpc.ldpc_code_info(hb)
     assert ib["max_check_degree"] == 96 and ib["max_var_degree"] == 64
-    assert ib["check_bin_count"][4] == 1
+    assert ib["check_bin_count"][5] == 1
 
 
 def test_argument_errors(ldpc):

@@ -75,7 +75,7 @@ def test_code_14_7_matches_oracle(ldpc, oracle_mod):
         assert bad.size == 0, (max_iter, bad)
 
 
-@pytest.mark.parametrize("d", [1, 2, 3, 6, 8, 16, 31, 32, 33, 96, 200])
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 6, 7, 8, 9, 16, 31, 32, 33, 96, 200])
 def test_single_parity_check_any_degree(ldpc, oracle_mod, d):
     """One check of degree d: every degree bin, closed-form pinned oracle."""
     code = I.coo_code(1, d, [0] * d, list(range(d)))
@@ -276,7 +276,7 @@ def test_profile_counts_launches(ldpc, n1008):
 
 # --- min-sum family --------------------------------------------------------------
 
-@pytest.mark.parametrize("d", [1, 2, 3, 8, 16, 32, 33, 96])
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 6, 7, 8, 16, 32, 33, 96])
 def test_min_sum_single_check_any_degree(ldpc, oracle_mod, d):
     code = I.coo_code(1, d, [0] * d, list(range(d)))
     h = ldpc.code_from_inputs(code)
@@ -331,3 +331,48 @@ def test_min_sum_schedules_do_not_change_results(ldpc, n1008):
         other = gpu_decode(ldpc, h, llr, 15, frames_per_lane=v, check_schedule=sched, streams=nst, **kw)
         for k in ("bits", "iters", "ok", "post"):
             np.testing.assert_array_equal(other[k], base[k], err_msg=f"V={v} schedule={sched} streams={nst} {k}")
+
+
+# --- sum-product with tabulated phi (rule "sp_table") ------------------------------
+
+@pytest.mark.parametrize("d", [1, 2, 3, 6, 8, 17, 33, 96])
+def test_table_rule_single_check_any_degree(ldpc, oracle_mod, d):
+    code = I.coo_code(1, d, [0] * d, list(range(d)))
+    h = ldpc.code_from_inputs(code)
+    llr = np.random.default_rng(d + 100).normal(0.0, 3.0, size=(70, d)).astype(np.float32)
+    llr[0, 0] = 1e-7
+    llr[0, 1:] = 30.0
+    got = gpu_decode(ldpc, h, llr, 0, early_exit=False, rule="sp_table")
+    ref = oracle_mod.decode(code, llr.astype(np.float64), 0, early_exit=False, rule="sp_table")
+    assert close(got["post"], ref["post"]).all(), np.abs(got["post"] - ref["post"]).max()
+
+
+def test_table_rule_lock_step_n1008(ldpc, oracle_mod, n1008):
+    """Every fifth pass of 51, from the GPU's own previous messages: the
+    tabulated rule on the GPU (float chords, bucket chosen on the float
+    value) equals the oracle's (chords in double)."""
+    code, cw, llr = n1008
+    h = ldpc.code_from_inputs(code)
+    lam = llr.astype(np.float64)
+    prev_r = None
+    for t in range(0, 51, 5):
+        if t > 0:
+            prev_r = gpu_decode(ldpc, h, llr, t - 1, early_exit=False, want_r=True, rule="sp_table")["r"]
+            prev_r = prev_r.astype(np.float64)
+        got = gpu_decode(ldpc, h, llr, t, early_exit=False, want_r=True, rule="sp_table")
+        ref = oracle_mod.sp_pass(code, lam, prev_r, n_threads=8, rule="sp_table")
+        assert close(got["post"], ref["post"]).all(), (t, float(np.abs(got["post"] - ref["post"]).max()))
+        assert close(got["r"], ref["r"], atol=1e-4).all(), (t, float(np.abs(got["r"] - ref["r"]).max()))
+
+
+def test_table_rule_schedules_and_limits(ldpc, n1008):
+    code, cw, llr = n1008
+    h = ldpc.code_from_inputs(code)
+    base = gpu_decode(ldpc, h, llr, 15, frames_per_lane=1, check_schedule=1, streams=1, rule="sp_table")
+    for v, sched, nst in ((4, 2, 2), (2, 0, 1), (8, 0, 0)):
+        other = gpu_decode(ldpc, h, llr, 15, frames_per_lane=v, check_schedule=sched, streams=nst, rule="sp_table")
+        for k in ("bits", "iters", "ok", "post"):
+            np.testing.assert_array_equal(other[k], base[k], err_msg=f"V={v} schedule={sched} streams={nst} {k}")
+    assert (base["ok"] == 1).mean() > 0.7  # 15 iterations at 2 dB
+    with pytest.raises(ldpc.LdpcError):
+        gpu_decode(ldpc, h, llr[:4], 5, rule="sp_table", l_max=30.0)
