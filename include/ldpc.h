@@ -223,6 +223,24 @@ int ldpc_decode_host(ldpc_code_t *code, const float *llr_host, int32_t n_frames,
                      uint8_t *syndrome_ok_host, float *post_llr_host, void *stream);
 
 /*
+ * A sequence of n_batches host batches of n_frames frames each (batch i:
+ * llr_host[i] [n_frames][n] float in, bits_host[i] [n_frames][n] uint8,
+ * iters_host[i] [n_frames] int32, ok_host[i] [n_frames] uint8 out), decoded
+ * as ldpc_decode would, with the copies of each batch overlapping the decode
+ * of its neighbours: two device staging slots alternate, batch i is copied
+ * in on a library stream once batch i - 2 no longer needs its slot, decoded
+ * on `stream`, and copied out on a second library stream. Pinned host memory
+ * is needed for the overlap (pageable memory works, serialised). Returns when
+ * every result is in host memory. opts->r_out and opts->profile must be
+ * unset. Output pointers may repeat across batches (the copies out run in
+ * batch order). The paper decodes one frame set per call; this is the
+ * receive-chain form of the same decode.
+ */
+int ldpc_decode_host_stream(ldpc_code_t *code, int32_t n_batches, const float *const *llr_host, int32_t n_frames,
+                            int32_t max_iter, const ldpc_decode_opts_t *opts, uint8_t *const *bits_host,
+                            int32_t *const *iters_host, uint8_t *const *ok_host, void *stream);
+
+/*
  * Mixed-code batches. A batch holds several (code, frame count) items, all on
  * one device, each with its own decode workspace (allocated here) and
  * stream. ldpc_batch_run decodes every item's frames; the items run as

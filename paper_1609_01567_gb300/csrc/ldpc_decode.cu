@@ -18,21 +18,39 @@ constexpr int32_t kMaxChunkFrames = 8192;
 
 // llr [F][n] (frame-major) -> lamT [n][Fp] (frame-interleaved); padding
 // frames get lambda = 0.
-__global__ void k_interleave(const float *__restrict__ llr, float *__restrict__ lamT, int32_t n, int32_t F,
-                             int32_t Fp) {
-    __shared__ float tile[32][33];
-    const int64_t j0 = (int64_t)blockIdx.x * 32;
-    const int f0 = blockIdx.y * 32;
-    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
-        int f = f0 + yy;
-        int64_t j = j0 + threadIdx.x;
-        tile[yy][threadIdx.x] = (f < F && j < n) ? llr[(size_t)f * n + j] : 0.0f;
+__global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ llr, float *__restrict__ lamT,
+                                                    int32_t n, int32_t F, int32_t Fp) {
+    // tile of 32 frames x 128 variables: frame rows read as float4 when the
+    // rows are 4-aligned, variable rows written 32 frames (128 bytes) at once
+    __shared__ float tile[128][33];
+    const int32_t j0 = blockIdx.x * 128;
+    const int32_t f0 = blockIdx.y * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool vec = (n & 3) == 0 && (reinterpret_cast<uintptr_t>(llr) & 15) == 0;
+#pragma unroll
+    for (int fi = warp; fi < 32; fi += 8) {
+        const int32_t f = f0 + fi, j = j0 + 4 * lane;
+        float x[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (f < F) {
+            const float *src = llr + (size_t)f * n + j;
+            if (vec && j + 3 < n) {
+                const float4 v = *reinterpret_cast<const float4 *>(src);
+                x[0] = v.x;
+                x[1] = v.y;
+                x[2] = v.z;
+                x[3] = v.w;
+            } else {
+                for (int b = 0; b < 4; ++b)
+                    if (j + b < n) x[b] = src[b];
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) tile[4 * lane + b][fi] = x[b];
     }
     __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
-        int64_t j = j0 + yy;
-        int f = f0 + threadIdx.x;
-        if (j < n) lamT[(size_t)j * Fp + f] = tile[threadIdx.x][yy];
+    for (int jj = warp; jj < 128; jj += 8) {
+        const int32_t j = j0 + jj;
+        if (j < n) lamT[(size_t)j * Fp + f0 + lane] = tile[jj][lane];
     }
 }
 
@@ -47,56 +65,81 @@ __global__ void k_init_done(uint32_t *done, uint32_t *status, int32_t F, int32_t
     done[w] = bits;
 }
 
-// Syndrome of the hard decision of the current APP into flag row `row`
-// (Algorithm 6), one warp per check for 32 * V frames.
-template <int V>
-__global__ void __launch_bounds__(kThreads) k_syndrome(PassArgs a, uint32_t *row) {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int g = blockIdx.y;
-    const int f0 = g * 32 * V + lane * V;
-    const size_t Fp = (size_t)a.Fp;
-    bool unsat[V];
+// Syndrome of the final hard decisions (Algorithm 6) from their bit words
+// dec [n][G] (G = Fp / 32 words per variable): thread (check i, word group)
+// xors the words of the check's variables, and each warp ors its checks'
+// unsatisfied-frame words into `row` with one atomic per word.
+template <int W>
+__global__ void k_syndrome_words(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, int32_t m,
+                                 const uint32_t *__restrict__ dec, int32_t G, uint32_t *__restrict__ row) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t w0 = blockIdx.y * W;
+    uint32_t z[W];
 #pragma unroll
-    for (int v = 0; v < V; ++v) unsat[v] = false;
-    for (int i = blockIdx.x * (kThreads / 32) + warp; i < a.m; i += gridDim.x * (kThreads / 32)) {
-        const int b = a.row_ptr[i];
-        const int d = a.row_ptr[i + 1] - b;
-        uint32_t z[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) z[v] = 0u;
-        for (int k = 0; k < d; ++k) {
-            const int j = a.col_idx[b + k];
-            float av[V];
-            load_v<V, float>(a.app + (size_t)j * Fp + f0, av);
-#pragma unroll
-            for (int v = 0; v < V; ++v) z[v] ^= av[v] > 0.0f ? 1u : 0u;
+    for (int q = 0; q < W; ++q) z[q] = 0u;
+    if (i < m) {
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const uint32_t *p = dec + (size_t)col_idx[e] * G + w0;
+            if constexpr (W == 4) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(p);
+                z[0] ^= v.x;
+                z[1] ^= v.y;
+                z[2] ^= v.z;
+                z[3] ^= v.w;
+            } else {
+                z[0] ^= p[0];
+            }
         }
-#pragma unroll
-        for (int v = 0; v < V; ++v) unsat[v] |= z[v] != 0u;
     }
-    or_frame_bits<V>(row, g, lane, unsat);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        const uint32_t u = __reduce_or_sync(0xffffffffu, z[q]);
+        if ((threadIdx.x & 31) == 0 && u) atomicOr(row + w0 + q, u);
+    }
 }
 
-// APP [n][Fp] -> bits [F][n] (1 iff APP > 0) and optional post [F][n].
-__global__ void k_finalize(const float *__restrict__ app, uint8_t *__restrict__ bits, float *__restrict__ post,
-                           int32_t n, int32_t F, int32_t Fp) {
-    __shared__ float tile[32][33];
-    const int64_t j0 = (int64_t)blockIdx.x * 32;
-    const int f0 = blockIdx.y * 32;
-    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
-        int64_t j = j0 + yy;
-        int f = f0 + threadIdx.x;
-        tile[yy][threadIdx.x] = j < n ? app[(size_t)j * Fp + f] : 0.0f;
+// APP [n][Fp] -> bits [F][n] (1 iff APP > 0, Algorithm 5) and optional post
+// [F][n]. A CTA transposes a tile of 128 variables x 32 frames through shared
+// memory and writes each frame's 128 decisions as 32 four-byte words (128
+// posteriors as float4) when rows are 4-aligned, else byte by byte.
+constexpr int kFinVars = 128;
+constexpr int kFinStride = kFinVars + 4;  // float4-aligned rows
+
+__global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ app, uint8_t *__restrict__ bits,
+                                                  float *__restrict__ post, int32_t n, int32_t F, int32_t Fp) {
+    __shared__ __align__(16) float tile[32][kFinStride];
+    const int32_t j0 = blockIdx.x * kFinVars;
+    const int32_t f0 = blockIdx.y * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // all 16 row loads of a warp in flight before the first shared store
+    float v[kFinVars / 8];
+#pragma unroll
+    for (int r = 0; r < kFinVars / 8; ++r) {
+        const int32_t j = j0 + warp + 8 * r;
+        v[r] = j < n ? app[(size_t)j * Fp + f0 + lane] : 0.0f;
     }
+#pragma unroll
+    for (int r = 0; r < kFinVars / 8; ++r) tile[lane][warp + 8 * r] = v[r];
     __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
-        int f = f0 + yy;
-        int64_t j = j0 + threadIdx.x;
-        if (f < F && j < n) {
-            float x = tile[threadIdx.x][yy];
-            bits[(size_t)f * n + j] = x > 0.0f ? 1 : 0;
-            if (post) post[(size_t)f * n + j] = x;
+    const bool vec = (n & 3) == 0 && (reinterpret_cast<uintptr_t>(bits) & 3) == 0 &&
+                     (reinterpret_cast<uintptr_t>(post) & 15) == 0;
+    for (int wi = threadIdx.x; wi < 32 * (kFinVars / 4); wi += blockDim.x) {
+        const int fi = wi / (kFinVars / 4), q = wi % (kFinVars / 4);
+        const int32_t f = f0 + fi, j = j0 + 4 * q;
+        if (f >= F || j >= n) continue;
+        const float4 x = *reinterpret_cast<const float4 *>(&tile[fi][4 * q]);
+        const size_t o = (size_t)f * n + j;
+        if (vec) {
+            const uint32_t word = (x.x > 0.0f ? 1u : 0u) | (x.y > 0.0f ? 1u : 0u) << 8 |
+                                  (x.z > 0.0f ? 1u : 0u) << 16 | (x.w > 0.0f ? 1u : 0u) << 24;
+            *reinterpret_cast<uint32_t *>(bits + o) = word;
+            if (post) *reinterpret_cast<float4 *>(post + o) = x;
+        } else {
+            const float xs[4] = {x.x, x.y, x.z, x.w};
+            for (int b = 0; b < 4 && j + b < n; ++b) {
+                bits[o + b] = xs[b] > 0.0f ? 1 : 0;
+                if (post) post[o + b] = xs[b];
+            }
         }
     }
 }
@@ -167,7 +210,8 @@ static int ensure_workspace_dims(Workspace &w, int32_t n, int64_t E, int32_t Fp,
             (e = grow(&w.app, (size_t)n * cap)) != cudaSuccess ||
             (e = grow(reinterpret_cast<char **>(&w.r), (size_t)E * cap * mb)) != cudaSuccess ||
             (e = grow(&w.done, (size_t)cap / 32 + 1)) != cudaSuccess ||
-            (e = grow(&w.stop_iter, (size_t)cap)) != cudaSuccess) {
+            (e = grow(&w.stop_iter, (size_t)cap)) != cudaSuccess ||
+            (e = grow(&w.dec, (size_t)n * cap / 32)) != cudaSuccess) {
             w.fp_cap = 0;
             w.iter_cap = -1;
             return cuda_error(e, "ldpc_decode: workspace allocation");
@@ -289,8 +333,8 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     if (e != cudaSuccess) return e;
     if (c->n > 0) {
         e = L(LDPC_K_INTERLEAVE, 1, [&] {
-            dim3 grid((unsigned)((c->n + 31) / 32), (unsigned)(Fp / 32), 1);
-            k_interleave<<<grid, dim3(32, 8, 1), 0, s>>>(llr, w.lamT, c->n, F, Fp);
+            dim3 grid((unsigned)((c->n + 127) / 128), (unsigned)(Fp / 32), 1);
+            k_interleave<<<grid, 256, 0, s>>>(llr, w.lamT, c->n, F, Fp);
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
@@ -333,6 +377,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
         for (int32_t t = 0; t <= max_iter; ++t) {
             at.pass = t;
             at.syndrome = (t > 0 && at.early_exit) ? 1 : 0;
+            at.dec = t == max_iter ? w.dec : nullptr;
             for (int b = 0; b < kNumCheckBins; ++b) {
                 int32_t count = c->bin_off[b + 1] - c->bin_off[b];
                 if (count == 0) continue;
@@ -366,21 +411,20 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     uint32_t *final_row = w.unsat + (size_t)max_iter * words;
     if (c->m > 0 && c->E > 0) {
         e = L(LDPC_K_SYNDROME, 1, [&] {
-            dim3 grid = pass_grid(a, c->m, std::min(V, 4));
-            if (V >= 4)
-                k_syndrome<4><<<grid, kThreads, 0, s>>>(a, final_row);
-            else if (V == 2)
-                k_syndrome<2><<<grid, kThreads, 0, s>>>(a, final_row);
+            if (words % 4 == 0)
+                k_syndrome_words<4><<<dim3((unsigned)((c->m + 255) / 256), (unsigned)(words / 4)), 256, 0, s>>>(
+                    c->d.row_ptr, c->d.col_idx, c->m, w.dec, words, final_row);
             else
-                k_syndrome<1><<<grid, kThreads, 0, s>>>(a, final_row);
+                k_syndrome_words<1><<<dim3((unsigned)((c->m + 255) / 256), (unsigned)words), 256, 0, s>>>(
+                    c->d.row_ptr, c->d.col_idx, c->m, w.dec, words, final_row);
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
     }
     e = L(LDPC_K_FINALIZE, c->n > 0 ? 2 : 1, [&] {
         if (c->n > 0) {
-            dim3 grid((unsigned)((c->n + 31) / 32), (unsigned)((F + 31) / 32), 1);
-            k_finalize<<<grid, dim3(32, 8, 1), 0, s>>>(w.app, bits, post, c->n, F, Fp);
+            dim3 grid((unsigned)((c->n + kFinVars - 1) / kFinVars), (unsigned)((F + 31) / 32), 1);
+            k_finalize<<<grid, 256, 0, s>>>(w.app, bits, post, c->n, F, Fp);
         }
         k_frame_results<<<(F + 255) / 256, 256, 0, s>>>(w.done, a.status, w.stop_iter, final_row, F, max_iter, iters,
                                                         ok);
@@ -562,6 +606,7 @@ void free_workspace(Workspace &w) {
     cudaFree(w.done);
     cudaFree(w.unsat);
     cudaFree(w.stop_iter);
+    cudaFree(w.dec);
     cudaFree(w.h_llr);
     cudaFree(w.h_bits);
     cudaFree(w.h_iters);

@@ -21,6 +21,7 @@ struct Workspace {
     void *r = nullptr;
     uint32_t *done = nullptr;
     uint32_t *unsat = nullptr;
+    uint32_t *dec = nullptr;  // [n][Fp/32] final hard-decision words
     int32_t *stop_iter = nullptr;
     // staging for ldpc_decode_host
     int32_t host_cap = 0;
@@ -41,6 +42,8 @@ struct ProfRecord {
 };
 
 void free_workspace(Workspace &w);
+struct HostStream;
+void free_host_stream(ldpc_code *c);
 int workspace_reserve(Workspace &w, int32_t n, int64_t E, int32_t Fp, int32_t max_iter, int msg_bytes);
 cudaError_t enqueue_decode(ldpc_code *c, Workspace &w, const float *llr, int32_t F, int32_t max_iter,
                            const ldpc_decode_opts_t &o, float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok,
@@ -79,4 +82,5 @@ struct ldpc_code {
     std::vector<ldpc::ProfRecord> prof;
     std::vector<cudaEvent_t> event_pool;
     int64_t kernels_launched = 0;  // library kernels enqueued since the last profile reset
+    ldpc::HostStream *host_stream = nullptr;  // staging of ldpc_decode_host_stream
 };

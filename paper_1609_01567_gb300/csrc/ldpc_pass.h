@@ -95,6 +95,7 @@ struct PassArgs {
     float c_max;         // 1 - e^-l_max: complement of the smallest |r|
     float t_min;         // e^-l_max: the smallest t = e^-|q| of the product form
     uint32_t *done;      // [Fp/32]
+    uint32_t *dec;       // [n][Fp/32] hard-decision words, written by the last bit pass (else null)
     uint32_t *status;    // one word, nonzero once a device wait of the call gave up
     uint32_t *unsat;     // [max_iter + 1][Fp/32]
     int32_t *stop_iter;  // [Fp] iteration at which a frame stopped

@@ -470,6 +470,20 @@ __device__ __forceinline__ void or_frame_bits(uint32_t *row, int g, int lane, co
     }
 }
 
+// Store the per-lane frame bits as the words of a decision row (plain store:
+// the warp owns these words).
+template <int V>
+__device__ __forceinline__ void store_frame_bits(uint32_t *row, int g, int lane, const bool (&bits)[V]) {
+    uint32_t mine = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) mine |= (bits[v] ? 1u : 0u) << v;
+    constexpr int kLanesPerWord = 32 / V;
+    uint32_t w = mine << ((lane % kLanesPerWord) * V);
+#pragma unroll
+    for (int o = 1; o < kLanesPerWord; o <<= 1) w |= __shfl_xor_sync(kFull, w, o);
+    if (lane % kLanesPerWord == 0) row[g * V + lane / kLanesPerWord] = w;
+}
+
 // ---------------------------------------------------------------------------
 // Check-node kernels
 // ---------------------------------------------------------------------------
@@ -1243,6 +1257,14 @@ __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
             for (int v = 0; v < V; ++v)
                 if (live[v]) dst[v] = acc[v];
         }
+        if (a.dec) {
+            // last pass: the hard decisions (Algorithm 5) as bit words for
+            // the final syndrome
+            bool bits[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) bits[v] = acc[v] > 0.0f;
+            store_frame_bits<V>(a.dec + (size_t)j * (Fp / 32), g, lane, bits);
+        }
     }
 }
 
@@ -1392,7 +1414,11 @@ cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, 
 
 template <typename M>
 cudaError_t launch_bit(const PassArgs &a, cudaStream_t s) {
-    dim3 grid = pass_grid(a, a.n, a.V);
+    // The bit kernel is bound by row gathers: 8 CTAs per SM (64 warps) keep
+    // more rows in flight than the default 4.
+    PassArgs b = a;
+    b.grid_ctas = a.sm_count * 8;
+    dim3 grid = pass_grid(b, a.n, a.V);
     if (a.V == 8)
         k_bit<8, M><<<grid, kThreads, 0, s>>>(a);
     else if (a.V == 4)

@@ -60,7 +60,8 @@ class ldpc_prof_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 7), ("total_ms", ctypes.c_double * 7), ("kernels", ctypes.c_int64)]
 
 
-EXPORTS = ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira", "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
+EXPORTS = ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira", "ldpc_decode_host_stream",
+           "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
            "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_count_errors", "ldpc_batch_create",
            "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info", "ldpc_batch_destroy", "ldpc_server_create",
            "ldpc_server_submit", "ldpc_server_wait", "ldpc_server_stats", "ldpc_server_destroy", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
@@ -84,6 +85,8 @@ def library():
             lib.ldpc_code_create_qc.argtypes = [i32, i32, i32, i64, vp, vp, vp, ctypes.POINTER(ldpc_code_opts_t),
                                                 ctypes.POINTER(vp)]
             lib.ldpc_gen_bits.argtypes = [u64, i64, i32, i32, vp, vp]
+            lib.ldpc_decode_host_stream.argtypes = [vp, i32, vp, i32, i32, ctypes.POINTER(ldpc_decode_opts_t), vp, vp,
+                                                    vp, vp]
             lib.ldpc_encode_ira.argtypes = [vp, vp, i32, vp, vp]
             lib.ldpc_code_destroy.argtypes = [vp]
             lib.ldpc_code_destroy.restype = None
@@ -111,7 +114,8 @@ def library():
             lib.ldpc_prof_read.argtypes = [vp, ctypes.POINTER(ldpc_prof_t), i32]
             lib.ldpc_last_error.restype = ctypes.c_char_p
             lib.ldpc_version.restype = ctypes.c_char_p
-            for name in ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode", "ldpc_decode_host",
+            for name in ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira",
+                         "ldpc_decode_host_stream", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode", "ldpc_decode_host",
                          "ldpc_decode_static",
                          "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_count_errors",
                          "ldpc_batch_create", "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info",
@@ -309,6 +313,40 @@ def ldpc_decode_host(code: Code, llr: np.ndarray, max_iter: int, *, early_exit: 
                                       ptr(o["iters"]), ptr(o["ok"]), ptr(o["post"]) if want_post else None,
                                       _stream_handle(stream)))
     return o
+
+
+def ldpc_decode_host_stream(code: Code, llrs, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
+                            msg_dtype: str = "f32", outs=None, stream=None, frames_per_lane: int = 0,
+                            check_schedule: int = 0, streams: int = 0, rule: str = "sum_product",
+                            rule_alpha: float = 1.0, rule_beta: float = 0.0) -> list:
+    """Decode a list of host batches (contiguous float32 CPU tensors [F, n],
+    pinned for overlap) with copies overlapping decodes; returns (or fills
+    ``outs``) one dict of host tensors ``bits``, ``iters``, ``ok`` per batch.
+    Output dicts may be shared between batches."""
+    import torch
+    if not llrs:
+        return []
+    f, n = llrs[0].shape
+    if n != code.n:
+        raise ValueError("llr has the wrong code length")
+    for t in llrs:
+        if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != (f, n):
+            raise ValueError("every batch must be a contiguous float32 host tensor of the same shape")
+    if outs is None:
+        pin = llrs[0].is_pinned()
+        outs = [{"bits": torch.empty((f, n), dtype=torch.uint8, pin_memory=pin),
+                 "iters": torch.empty((f,), dtype=torch.int32, pin_memory=pin),
+                 "ok": torch.empty((f,), dtype=torch.uint8, pin_memory=pin)} for _ in llrs]
+    if len(outs) != len(llrs):
+        raise ValueError("one output dict per batch")
+    vp = ctypes.c_void_p
+    arr = lambda ts: (vp * len(ts))(*[t.data_ptr() for t in ts])  # noqa: E731
+    opts = _opts(early_exit, l_max, msg_dtype, False, None, frames_per_lane, check_schedule, streams, 0, rule,
+                 rule_alpha, rule_beta)
+    _check(library().ldpc_decode_host_stream(code.handle, len(llrs), arr(llrs), f, max_iter, ctypes.byref(opts),
+                                             arr([o["bits"] for o in outs]), arr([o["iters"] for o in outs]),
+                                             arr([o["ok"] for o in outs]), _stream_handle(stream)))
+    return outs
 
 
 def ldpc_decode_static(code: Code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,

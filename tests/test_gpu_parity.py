@@ -376,3 +376,23 @@ def test_table_rule_schedules_and_limits(ldpc, n1008):
     assert (base["ok"] == 1).mean() > 0.7  # 15 iterations at 2 dB
     with pytest.raises(ldpc.LdpcError):
         gpu_decode(ldpc, h, llr[:4], 5, rule="sp_table", l_max=30.0)
+
+
+def test_unaligned_caller_buffers(ldpc, n1008):
+    """LLRs, decisions and posteriors at odd offsets take the scalar paths of
+    the layout kernels and give the same results as aligned buffers."""
+    code, cw, llr = n1008
+    h = ldpc.code_from_inputs(code)
+    sub = np.ascontiguousarray(llr[:70], dtype=np.float32)
+    f, n = sub.shape
+    base = gpu_decode(ldpc, h, sub, 12)
+    lbuf = torch.zeros(f * n + 1, dtype=torch.float32, device="cuda")
+    lbuf[1:] = torch.from_numpy(sub.reshape(-1)).cuda()
+    out = {"bits": torch.zeros(f * n + 1, dtype=torch.uint8, device="cuda")[1:].view(f, n),
+           "iters": torch.zeros(f, dtype=torch.int32, device="cuda"),
+           "ok": torch.zeros(f, dtype=torch.uint8, device="cuda"),
+           "post": torch.zeros(f * n + 1, dtype=torch.float32, device="cuda")[1:].view(f, n)}
+    got = ldpc.ldpc_decode(h, lbuf[1:].view(f, n), 12, out=out)
+    torch.cuda.synchronize()
+    for k in ("bits", "iters", "ok", "post"):
+        np.testing.assert_array_equal(got[k].cpu().numpy(), base[k], err_msg=k)

@@ -1,0 +1,49 @@
+"""Streaming decode of host batches (copies overlapping decodes) returns what
+per-batch device decodes return."""
+import numpy as np
+import pytest
+
+from paper_1609_01567_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ldpc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_01567_gb300 import build
+    build.build()
+    from paper_1609_01567_gb300 import ldpc as mod
+    return mod
+
+
+@pytest.mark.parametrize("n_batches,frames", [(1, 64), (2, 33), (5, 100)])
+def test_stream_equals_device_decodes(ldpc, n_batches, frames):
+    code = I.small_code_n1008()
+    h = ldpc.code_from_inputs(code)
+    s2 = I.sigma2_from_ebn0(1.75, code.rate)
+    llrs = [torch.from_numpy(I.gaussian_llr(np.zeros((frames, code.n), np.uint8), s2, seed=b)).pin_memory()
+            for b in range(n_batches)]
+    outs = ldpc.ldpc_decode_host_stream(h, llrs, 20, early_exit=True)
+    for b in range(n_batches):
+        ref = ldpc.ldpc_decode(h, llrs[b].cuda(), 20, early_exit=True, want_post=False)
+        torch.cuda.synchronize()
+        for k in ("bits", "iters", "ok"):
+            np.testing.assert_array_equal(outs[b][k].numpy(), ref[k].cpu().numpy(), err_msg=f"batch {b} {k}")
+
+
+def test_stream_shared_outputs_hold_the_last_batch(ldpc):
+    code = I.small_code_n1008()
+    h = ldpc.code_from_inputs(code)
+    s2 = I.sigma2_from_ebn0(1.5, code.rate)
+    llrs = [torch.from_numpy(I.gaussian_llr(np.zeros((40, code.n), np.uint8), s2, seed=50 + b)) for b in range(4)]
+    shared = {"bits": torch.empty((40, code.n), dtype=torch.uint8), "iters": torch.empty(40, dtype=torch.int32),
+              "ok": torch.empty(40, dtype=torch.uint8)}
+    ldpc.ldpc_decode_host_stream(h, llrs, 10, early_exit=False, outs=[shared] * 4, rule="min_sum", rule_alpha=0.8)
+    ref = ldpc.ldpc_decode(h, llrs[-1].cuda(), 10, early_exit=False, want_post=False, rule="min_sum", rule_alpha=0.8)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(shared["bits"].numpy(), ref["bits"].cpu().numpy())
+    np.testing.assert_array_equal(shared["iters"].numpy(), ref["iters"].cpu().numpy())
+    assert ldpc.ldpc_decode_host_stream(h, [], 10) == []
