@@ -745,7 +745,7 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
 // flow per edge. Slots k >= d become neutral inputs (D_k = 0, no sign, no
 // syndrome term) and their outputs are not stored. Same operations, same
 // order, same results as check_node_pairs for the real inputs.
-template <int D, int P, typename M, bool kFirst, bool kSyn, typename Load>
+template <int D, int P, typename M, bool kFirst, bool kSyn, bool kFull, typename Load>
 __device__ __forceinline__ void check_node_pairs_masked(int d, Load &&load, M *out, size_t Fp, const PassArgs &a,
                                                         bool (&unsat)[2 * P]) {
     const float t_min = a.t_min, c_min = a.c_min;
@@ -756,7 +756,7 @@ __device__ __forceinline__ void check_node_pairs_masked(int d, Load &&load, M *o
     for (int v = 0; v < 2 * P; ++v) ones[v] = z[v] = 0u;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        const bool real = k < d;
+        const bool real = kFull || k < d;  // kFull: the caller knows d == D
         float2 av[P], rv[P];
         load(k, av, rv);
 #pragma unroll
@@ -814,7 +814,7 @@ __device__ __forceinline__ void check_node_pairs_masked(int d, Load &&load, M *o
                 pp[q] = mul2(pp[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
             }
         }
-        if (k < d) store_pairs<M, P>(out + (size_t)k * Fp, o);
+        if (kFull || k < d) store_pairs<M, P>(out + (size_t)k * Fp, o);
     }
 }
 
@@ -1030,9 +1030,16 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 
             if (!first)
                 load_pairs<V, M>(reinterpret_cast<const M *>(base + D * P::kRowA + k * P::kRowR) + lane * V, rv);
         };
-        if constexpr (RULE == 0)
-            check_node_pairs_masked<D, V / 2, M, first, syn>(qd[0], load, r + (size_t)qb[0] * Fp + f0, Fp, a, unsat);
-        else
+        if constexpr (RULE == 0) {
+            // checks of the bin's full degree (most of them) skip the masking;
+            // the widest bin keeps one path (registers)
+            if (D <= 8 && qd[0] == D)
+                check_node_pairs_masked<D, V / 2, M, first, syn, true>(D, load, r + (size_t)qb[0] * Fp + f0, Fp, a,
+                                                                      unsat);
+            else
+                check_node_pairs_masked<D, V / 2, M, first, syn, false>(qd[0], load, r + (size_t)qb[0] * Fp + f0, Fp,
+                                                                       a, unsat);
+        } else
             check_node_pairs<D, V / 2, M, RULE>(qd[0], first, syn, load, r + (size_t)qb[0] * Fp + f0, Fp, a, unsat);
         __syncwarp();
 #pragma unroll
