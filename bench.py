@@ -49,6 +49,7 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=50)
+    p.add_argument("--early-exit-steps", type=int, default=10)
     p.add_argument("--streams", type=int, default=0, help="decode tuning: 1 or 2 streams (0 = library choice)")
     p.add_argument("--frames-per-lane", type=int, default=0, help="decode tuning (0 = library choice)")
     return p.parse_args()
@@ -368,6 +369,31 @@ def run_ours(args):
                    "entry_point": "ldpc_decode_host_stream (pinned host batches, copies overlap decodes)",
                    "one_call_per_step": {"value": world * F * K_BITS / call_s / 1e9, "ms_per_step": call_s * 1e3,
                                          "entry_point": "ldpc_decode_host"}}
+
+    # context: the same batch with max_iter 50 and early exit (per-frame
+    # stopping; a 128-frame warp group runs until its slowest frame stops)
+    if args.early_exit_steps > 0:
+        early = {}
+        for eb in (0.8, 1.0, 1.2, 1.4, 1.6):
+            s2e = inputs.sigma2_from_ebn0(eb, code.rate)
+            bufs = [ldpc.ldpc_gen_awgn(31 + b, rank * F, F, code.n, s2e, cw, device=local) for b in range(n_buf)]
+            o2 = None
+            for i in range(2):
+                o2 = ldpc.ldpc_decode(h, bufs[i], 50, out=o2, want_post=False, early_exit=True, msg_dtype=args.msg)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for i in range(args.early_exit_steps):
+                o2 = ldpc.ldpc_decode(h, bufs[i % n_buf], 50, out=o2, want_post=False, early_exit=True,
+                                      msg_dtype=args.msg)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / args.early_exit_steps
+            its = [float(ldpc.ldpc_decode(h, b, 50, want_post=False, early_exit=True,
+                                          msg_dtype=args.msg)["iters"].float().mean().item()) for b in bufs]
+            early[f"{eb} dB"] = {"value": world * F * K_BITS / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                                 "mean_iters": sum(its) / len(its)}
+        line["early_exit_max_iter_50"] = early
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         frames, threads, wall, t_frame = oracle_sample(code, cw_host, args, args.cpu_seconds, F)

@@ -160,8 +160,9 @@ typedef struct {
                            size                                              */
     int32_t check_schedule;  /* tuning: check-node kernel schedule; 0 = auto,
                            1 = inputs loaded straight from global memory,
-                           2 = rows staged through a shared-memory pipeline
-                           (when the batch allows)                           */
+                           2 = rows staged through a shared-memory ring by
+                           bulk copies (when the batch allows: degree <= 16,
+                           frame groups of 64 or 128)                        */
     int32_t streams;    /* tuning: 1 = all passes on `stream`; 2 = the two
                            halves of the batch on two library streams, half a
                            pass apart, so that the check pass of one half
@@ -199,7 +200,9 @@ enum { LDPC_RULE_SUM_PRODUCT = 0, LDPC_RULE_MIN_SUM = 1, LDPC_RULE_SP_TABLE = 2 
  *   bits      device [n_frames][n] uint8 hard decisions (0/1)
  *   iters     device [n_frames] int32: 0 when the first pass already gives a
  *             codeword, else the iteration at which the frame stopped, or
- *             max_iter (always max_iter without early exit)
+ *             max_iter (always max_iter without early exit); -1 for every
+ *             frame of a call in which a device wait of the pipelined check
+ *             kernel gave up (a bounded wait for row copies; not expected)
  *   syndrome_ok device [n_frames] uint8: 1 iff H * bits = 0
  *   post_llr  optional device [n_frames][n] float posterior LLRs; NULL to skip
  * The code's decode workspace (device scratch sized for the largest batch

@@ -111,6 +111,12 @@ def test_argument_errors(ldpc):
     assert lib.ldpc_gen_awgn(1, 0, 1, 4, ctypes.c_float(0.0), None, None, None) == -1
     assert lib.ldpc_gen_awgn(1, 0, -1, 4, ctypes.c_float(1.0), None, None, None) == -1
     assert lib.ldpc_philox4x64_10(0, 0, 0, 0, -1, None, None) == -1
+    # the entry points added beside the decoder refuse the same way
+    assert lib.ldpc_decode_host_stream(h.handle, 1, None, 1, 5, None, None, None, None, None) == -7
+    assert lib.ldpc_encode_ira(h.handle, None, 1, None, None) == -7
+    assert lib.ldpc_gen_bits(1, 0, -1, 4, None, None) == -1
+    assert lib.ldpc_gen_bits(1, -1, 1, 4, None, None) == -1
+    assert lib.ldpc_gen_bits(1, 0, 0, 4, None, None) == 0  # nothing to do
 
 
 def test_qc_lifting_matches_the_expanded_matrix(ldpc, oracle_mod):

@@ -396,3 +396,16 @@ def test_unaligned_caller_buffers(ldpc, n1008):
     torch.cuda.synchronize()
     for k in ("bits", "iters", "ok", "post"):
         np.testing.assert_array_equal(got[k].cpu().numpy(), base[k], err_msg=k)
+
+
+def test_batches_larger_than_one_chunk(ldpc, oracle_mod):
+    """More frames than one device chunk (8192): the decode runs in chunks
+    that reuse the workspace; every frame still equals the oracle."""
+    code = I.small_code_n1008()
+    h = ldpc.code_from_inputs(code)
+    F = 8192 + 300
+    llr = I.gaussian_llr(np.zeros((F, code.n), np.uint8), I.sigma2_from_ebn0(2.5, code.rate), seed=77)
+    got = gpu_decode(ldpc, h, llr, 4)
+    ref = oracle_mod.decode(code, llr.astype(np.float64), 4, n_threads=8)
+    bad, _ = compare_decodes(got, ref)
+    assert bad.size == 0, bad[:10]
