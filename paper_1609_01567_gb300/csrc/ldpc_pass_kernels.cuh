@@ -1377,7 +1377,7 @@ static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *
     // Four frames per lane where the check's state fits the registers (degree
     // <= 6): the per-edge index, copy and control work is then shared by two
     // frame pairs. Wider checks run two frames per lane.
-    if (a.check_schedule != 1 && bin <= 1 && a.f_count % 128 == 0 && a.f_begin % 128 == 0) {
+    if (a.check_schedule != 1 && bin <= 1 && a.V >= 4 && a.f_count % 128 == 0 && a.f_begin % 128 == 0) {
         if (bin == 0) return launch_bulk<4, 4, M, 2, RULE>(a, desc, count, s);
         return launch_bulk<6, 4, M, 2, RULE>(a, desc, count, s);
     }
