@@ -117,28 +117,55 @@ struct MsgIO<__nv_bfloat16> {
     static __device__ __forceinline__ void store1(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
 };
 
+// int8 levels are converted with FP32 arithmetic instead of the int<->float
+// conversion instructions, which share the transcendental unit with the
+// check rule's ex2/lg2/rcp: adding 1.5 * 2^23 to a float of magnitude below
+// 2^22 leaves round(value) (ties to even) in the low mantissa bits, whose low
+// byte is the two's-complement level, and subtracting it back from a float
+// with such a pattern recovers the level exactly.
+constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
+constexpr uint32_t kRoundMagicBits = 0x4B400000u;
+
 template <>
 struct MsgIO<int8_t> {
-    static __device__ __forceinline__ int8_t quantize(float x) {
-        int q = __float2int_rn(x * kI8Inv);
-        return (int8_t)max(-127, min(127, q));
+    // the level of x (clamped to +-127 steps) in the low byte of the result
+    static __device__ __forceinline__ uint32_t level_bits(float x) {
+        x = fminf(fmaxf(x, -127.0f * kI8Step), 127.0f * kI8Step);
+        return __float_as_uint(fmaf(x, kI8Inv, kRoundMagic));
+    }
+    // byte b of w, sign-extended, as level * step
+    template <int B>
+    static __device__ __forceinline__ float value(uint32_t w) {
+        // prmt with the sign-replicate bit set in the upper three selectors
+        constexpr uint32_t sel = (0x8u | B) << 12 | (0x8u | B) << 8 | (0x8u | B) << 4 | B;
+        int k;
+        asm("prmt.b32 %0, %1, 0, %2;" : "=r"(k) : "r"(w), "n"(sel));
+        return (__int_as_float((int)kRoundMagicBits + k) - kRoundMagic) * kI8Step;
     }
     static __device__ __forceinline__ void load4(const int8_t *p, float (&x)[4]) {
-        char4 v = *reinterpret_cast<const char4 *>(p);
-        x[0] = v.x * kI8Step; x[1] = v.y * kI8Step; x[2] = v.z * kI8Step; x[3] = v.w * kI8Step;
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(p);
+        x[0] = value<0>(w);
+        x[1] = value<1>(w);
+        x[2] = value<2>(w);
+        x[3] = value<3>(w);
     }
     static __device__ __forceinline__ void store4(int8_t *p, const float (&x)[4]) {
-        *reinterpret_cast<char4 *>(p) = make_char4(quantize(x[0]), quantize(x[1]), quantize(x[2]), quantize(x[3]));
+        const uint32_t lo = __byte_perm(level_bits(x[0]), level_bits(x[1]), 0x0040u);
+        const uint32_t hi = __byte_perm(level_bits(x[2]), level_bits(x[3]), 0x0040u);
+        *reinterpret_cast<uint32_t *>(p) = __byte_perm(lo, hi, 0x5410u);
     }
     static __device__ __forceinline__ void load2(const int8_t *p, float (&x)[2]) {
-        char2 v = *reinterpret_cast<const char2 *>(p);
-        x[0] = v.x * kI8Step; x[1] = v.y * kI8Step;
+        const uint32_t w = *reinterpret_cast<const uint16_t *>(p);
+        x[0] = value<0>(w);
+        x[1] = value<1>(w);
     }
     static __device__ __forceinline__ void store2(int8_t *p, const float (&x)[2]) {
-        *reinterpret_cast<char2 *>(p) = make_char2(quantize(x[0]), quantize(x[1]));
+        *reinterpret_cast<uint16_t *>(p) = (uint16_t)__byte_perm(level_bits(x[0]), level_bits(x[1]), 0x0040u);
     }
-    static __device__ __forceinline__ float load1(const int8_t *p) { return *p * kI8Step; }
-    static __device__ __forceinline__ void store1(int8_t *p, float x) { *p = quantize(x); }
+    static __device__ __forceinline__ float load1(const int8_t *p) {
+        return value<0>((uint32_t)(uint8_t)*p);
+    }
+    static __device__ __forceinline__ void store1(int8_t *p, float x) { *p = (int8_t)(level_bits(x) & 0xFFu); }
 };
 
 template <int V, typename M>
