@@ -777,10 +777,12 @@ __device__ __forceinline__ void check_node_pairs_masked(int d, Load &&load, M *o
                                                         bool (&unsat)[2 * P]) {
     const float t_min = a.t_min, c_min = a.c_min;
     float2 dc[D][P];
-    uint32_t ones[2 * P];
+    // sign bits of the inputs, input k at bit D - 1 - k (shifted in by one
+    // funnel shift per input; padding slots shift in 0)
+    uint32_t sb[2 * P];
     uint32_t z[2 * P];
 #pragma unroll
-    for (int v = 0; v < 2 * P; ++v) ones[v] = z[v] = 0u;
+    for (int v = 0; v < 2 * P; ++v) sb[v] = z[v] = 0u;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         const bool real = kFull || k < d;  // kFull: the caller knows d == D
@@ -793,8 +795,9 @@ __device__ __forceinline__ void check_node_pairs_masked(int d, Load &&load, M *o
                 z[2 * q + 1] ^= (real && av[q].y > 0.0f) ? 1u : 0u;
             }
             if constexpr (!kFirst) av[q] = fma2(rv[q], f2(-1.0f), av[q]);
-            ones[2 * q] |= ((real && av[q].x > 0.0f) ? 1u : 0u) << k;
-            ones[2 * q + 1] |= ((real && av[q].y > 0.0f) ? 1u : 0u) << k;
+            const uint32_t bx = real ? __float_as_uint(av[q].x) : 0u, by = real ? __float_as_uint(av[q].y) : 0u;
+            sb[2 * q] = __funnelshift_l(bx, sb[2 * q], 1);
+            sb[2 * q + 1] = __funnelshift_l(by, sb[2 * q + 1], 1);
             const float2 t = tanh_complement2(make_float2(fabsf(av[q].x), fabsf(av[q].y)), t_min);
             dc[k][q] = make_float2(real ? t.x : 0.0f, real ? t.y : 0.0f);
         }
@@ -826,16 +829,22 @@ __device__ __forceinline__ void check_node_pairs_masked(int d, Load &&load, M *o
         cp[q] = f2(0.0f);
         pp[q] = f2(1.0f);
     }
+    // r_k > 0 iff an odd number of the other real inputs are > 0. With s_j
+    // the sign bit of q_j, that count is (d - 1) - sum_{j != k} s_j, so r_k
+    // is negative iff d + S + s_k is odd (S = sum of all s_j): bit D - 1 - k
+    // of neg. A zero input counts as positive here, which only changes the
+    // sign of outputs whose magnitude that input has already made zero.
+    const uint32_t dpar = (uint32_t)(kFull ? D : d) & 1u;
 #pragma unroll
-    for (int v = 0; v < 2 * P; ++v) neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
+    for (int v = 0; v < 2 * P; ++v) neg[v] = ((dpar ^ __popc(sb[v])) & 1u) ? ~sb[v] : sb[v];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         float2 o[P];
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             o[q] = mag_of_complement2(fma2(pp[q], csuf[k][q], cp[q]), c_min);
-            o[q].x = __int_as_float(__float_as_int(o[q].x) | (int)((neg[2 * q] << (31 - k)) & 0x80000000u));
-            o[q].y = __int_as_float(__float_as_int(o[q].y) | (int)((neg[2 * q + 1] << (31 - k)) & 0x80000000u));
+            o[q].x = __int_as_float(__float_as_int(o[q].x) | (int)((neg[2 * q] << (32 - D + k)) & 0x80000000u));
+            o[q].y = __int_as_float(__float_as_int(o[q].y) | (int)((neg[2 * q + 1] << (32 - D + k)) & 0x80000000u));
             if (k + 1 < D) {
                 cp[q] = fma2(pp[q], dc[k][q], cp[q]);
                 pp[q] = mul2(pp[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
