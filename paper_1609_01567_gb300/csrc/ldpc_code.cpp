@@ -50,6 +50,7 @@ static void free_device_tables(ldpc_code *c) {
     cudaFree(c->d.bin_desc);
     cudaFree(c->d.phi_table);
     free_host_stream(c);
+    free_decode_graphs(c);
     free_workspace(c->ws);
     for (auto &p : c->prof) {
         cudaEventDestroy(p.start);

@@ -220,6 +220,7 @@ static int ensure_workspace_dims(Workspace &w, int32_t n, int64_t E, int32_t Fp,
         if ((e = cudaMemset(w.app, 0, sizeof(float) * std::max<size_t>((size_t)n * cap, 1))) != cudaSuccess)
             return cuda_error(e, "ldpc_decode: workspace init");
         w.fp_cap = cap;
+        w.generation += 1;
         w.msg_bytes = mb;
     }
     int32_t icap = std::max(max_iter, w.iter_cap);
@@ -228,6 +229,7 @@ static int ensure_workspace_dims(Workspace &w, int32_t n, int64_t E, int32_t Fp,
         return cuda_error(e, "ldpc_decode: workspace allocation");
     }
     w.iter_cap = icap;
+    w.generation += 1;
     return LDPC_OK;
 }
 
@@ -475,6 +477,95 @@ static ldpc_decode_opts_t default_opts() {
 }
 
 // Decode with the code's lock held.
+// Enqueue the chunks of one decode on `s` (no synchronisation, no
+// allocation: capturable).
+static cudaError_t enqueue_chunks(ldpc_code *c, const float *llr, int32_t F, int32_t chunk, int32_t max_iter,
+                                  const ldpc_decode_opts_t &o, float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok,
+                                  float *post, cudaStream_t s) {
+    for (int32_t f0 = 0; f0 < F; f0 += chunk) {
+        int32_t fc = std::min(chunk, F - f0);
+        const float *l = llr + (size_t)f0 * c->n;
+        uint8_t *bb = bits + (size_t)f0 * c->n;
+        float *pp = post ? post + (size_t)f0 * c->n : nullptr;
+        float *rr = o.r_out ? o.r_out + (size_t)f0 * c->E : nullptr;
+        cudaError_t e = with_msg_type(o.msg_dtype, [&](auto tag) {
+            using M = typename decltype(tag)::type;
+            return run_chunk<M>(c, c->ws, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
+        });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Graph replay. A decode whose shape, options and buffers repeat the
+// previous call's is captured into a CUDA graph on a library stream (so any
+// caller stream works, the legacy default stream included) and replayed by
+// later calls with the same key: one launch instead of ~4 per pass, which
+// is what small codes are bound by. A key is captured the second time it is
+// seen among the last four; up to kGraphCache graphs per code; a workspace
+// reallocation changes the key.
+constexpr size_t kGraphCache = 4;
+
+static int decode_graph(ldpc_code *c, const GraphKey &key, int32_t chunk, cudaStream_t s, bool *done) {
+    *done = false;
+    for (auto &g : c->graphs) {
+        if (g.key == key) {
+            cudaError_t e = cudaGraphLaunch(g.exec, s);
+            if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: graph launch");
+            g.used = ++c->graph_tick;
+            c->kernels_launched += g.kernels;
+            *done = true;
+            return LDPC_OK;
+        }
+    }
+    bool seen = false;
+    for (int i = 0; i < c->n_seen; ++i) seen |= c->seen_keys[i] == key;
+    if (!seen) {  // first sighting: run directly, remember the key
+        c->seen_keys[c->next_seen] = key;
+        c->next_seen = (c->next_seen + 1) % 4;
+        c->n_seen = std::min(c->n_seen + 1, 4);
+        return LDPC_OK;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!c->capture_stream) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = ensure_half_streams(c->ws);
+    if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: graph set-up");
+    cudaStream_t cap = c->capture_stream;
+    const int64_t k0 = c->kernels_launched;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: begin capture");
+    cudaError_t ee = enqueue_chunks(c, key.llr, key.F, chunk, key.max_iter, key.o, key.l_max, key.bits, key.iters,
+                                    key.ok, key.post, cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap, &graph);
+    const int64_t kernels = c->kernels_launched - k0;
+    c->kernels_launched = k0;
+    if (ee != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return LDPC_OK;  // not capturable here: the caller runs it directly
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LDPC_OK;
+    }
+    if (c->graphs.size() >= kGraphCache) {
+        auto lru = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                    [](const DecodeGraph &x, const DecodeGraph &y) { return x.used < y.used; });
+        cudaGraphExecDestroy(lru->exec);
+        c->graphs.erase(lru);
+    }
+    c->graphs.push_back(DecodeGraph{key, exec, kernels, ++c->graph_tick});
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: graph launch");
+    c->kernels_launched += kernels;
+    *done = true;
+    return LDPC_OK;
+}
+
 static int decode_locked(ldpc_code *c, const float *llr, int32_t F, int32_t max_iter, const ldpc_decode_opts_t &o,
                          float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok, float *post, cudaStream_t s) {
     int32_t chunk = std::min(F, kMaxChunkFrames);
@@ -484,16 +575,25 @@ static int decode_locked(ldpc_code *c, const float *llr, int32_t F, int32_t max_
     if (st != LDPC_OK) return st;
     cudaError_t e = cudaStreamWaitEvent(s, c->ws.last_use, 0);
     if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: cudaStreamWaitEvent");
-    for (int32_t f0 = 0; f0 < F; f0 += chunk) {
-        int32_t fc = std::min(chunk, F - f0);
-        const float *l = llr + (size_t)f0 * c->n;
-        uint8_t *bb = bits + (size_t)f0 * c->n;
-        float *pp = post ? post + (size_t)f0 * c->n : nullptr;
-        float *rr = o.r_out ? o.r_out + (size_t)f0 * c->E : nullptr;
-        e = with_msg_type(o.msg_dtype, [&](auto tag) {
-            using M = typename decltype(tag)::type;
-            return run_chunk<M>(c, c->ws, l, fc, max_iter, o, l_max, bb, iters + f0, ok + f0, pp, rr, s);
-        });
+    bool done = false;
+    if (!o.profile) {
+        GraphKey key;
+        key.llr = llr;
+        key.bits = bits;
+        key.iters = iters;
+        key.ok = ok;
+        key.post = post;
+        key.r_out = o.r_out;
+        key.F = F;
+        key.max_iter = max_iter;
+        key.l_max = l_max;
+        key.o = o;
+        key.ws_generation = c->ws.generation;
+        st = decode_graph(c, key, chunk, s, &done);
+        if (st != LDPC_OK) return st;
+    }
+    if (!done) {
+        e = enqueue_chunks(c, llr, F, chunk, max_iter, o, l_max, bits, iters, ok, post, s);
         if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: kernel launch");
     }
     e = cudaEventRecord(c->ws.last_use, s);
@@ -597,6 +697,24 @@ extern "C" int ldpc_prof_read(ldpc_code_t *c, ldpc_prof_t *out, int32_t reset) {
 // ---------------------------------------------------------------------------
 
 namespace ldpc {
+
+bool GraphKey::operator==(const GraphKey &b) const {
+    return llr == b.llr && bits == b.bits && iters == b.iters && ok == b.ok && post == b.post && r_out == b.r_out &&
+           F == b.F && max_iter == b.max_iter && l_max == b.l_max && ws_generation == b.ws_generation &&
+           o.early_exit == b.o.early_exit && o.l_max == b.o.l_max && o.msg_dtype == b.o.msg_dtype &&
+           o.profile == b.o.profile && o.r_out == b.o.r_out && o.frames_per_lane == b.o.frames_per_lane &&
+           o.check_schedule == b.o.check_schedule && o.streams == b.o.streams && o.tile_frames == b.o.tile_frames &&
+           o.check_rule == b.o.check_rule && o.rule_alpha == b.o.rule_alpha && o.rule_beta == b.o.rule_beta;
+}
+
+void free_decode_graphs(ldpc_code *c) {
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+    c->n_seen = 0;
+    c->next_seen = 0;
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    c->capture_stream = nullptr;
+}
 
 void free_workspace(Workspace &w) {
     if (w.last_use) cudaEventSynchronize(w.last_use);

@@ -13,6 +13,7 @@
 namespace ldpc {
 
 struct Workspace {
+    uint64_t generation = 0;  // bumped whenever the buffers are (re)allocated
     int32_t fp_cap = 0;       // frames (padded) the buffers hold
     int32_t iter_cap = -1;    // max_iter the unsat rows hold
     int32_t msg_bytes = 0;    // bytes per stored message of the current buffer
@@ -42,6 +43,28 @@ struct ProfRecord {
 };
 
 void free_workspace(Workspace &w);
+
+// A captured decode: the call's shape, options and buffers, and its graph.
+struct GraphKey {
+    const float *llr = nullptr;
+    uint8_t *bits = nullptr;
+    int32_t *iters = nullptr;
+    uint8_t *ok = nullptr;
+    float *post = nullptr;
+    float *r_out = nullptr;
+    int32_t F = 0, max_iter = 0;
+    float l_max = 0.0f;
+    ldpc_decode_opts_t o{};
+    uint64_t ws_generation = 0;
+    bool operator==(const GraphKey &b) const;
+};
+struct DecodeGraph {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;  // library kernels in the graph
+    uint64_t used = 0;    // last use (for eviction)
+};
+void free_decode_graphs(ldpc_code *c);
 struct HostStream;
 void free_host_stream(ldpc_code *c);
 int workspace_reserve(Workspace &w, int32_t n, int64_t E, int32_t Fp, int32_t max_iter, int msg_bytes);
@@ -83,4 +106,10 @@ struct ldpc_code {
     std::vector<cudaEvent_t> event_pool;
     int64_t kernels_launched = 0;  // library kernels enqueued since the last profile reset
     ldpc::HostStream *host_stream = nullptr;  // staging of ldpc_decode_host_stream
+    // graph replay of repeated decodes (ldpc_decode, ldpc_decode_host)
+    std::vector<ldpc::DecodeGraph> graphs;
+    ldpc::GraphKey seen_keys[4];  // keys run once directly (captured when they recur)
+    int n_seen = 0, next_seen = 0;
+    uint64_t graph_tick = 0;
+    cudaStream_t capture_stream = nullptr;
 };

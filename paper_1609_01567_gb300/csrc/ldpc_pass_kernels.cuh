@@ -235,10 +235,9 @@ __device__ __forceinline__ float rcp_approx(float x) {
 //    inputs are made of.
 //  * otherwise phi = ln((1 + t) / (1 - t)), with 1 - t = 1 - e^-x from its
 //    Taylor series below x = 1/4 (where 1 - t would cancel).
-// The scalar form and the two-frame form below execute the same operations
-// in the same order (the packed FP32 instructions round element-wise like
-// their scalar counterparts), so results do not depend on how many frames a
-// lane carries.
+// phi^ serves the any-degree kernel, which carries one or two frames per
+// lane with the same scalar operations, so its results do not depend on the
+// frame layout either.
 constexpr float kL2E = 1.44269502162933349609375f;  // log2(e) rounded to float
 constexpr float kL2ELo = 1.925963033500011e-08f;    // log2(e) - kL2E
 constexpr float kLn2 = 0.693147180559945309f;
@@ -271,55 +270,6 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-// phi^ of two frames at once. Must be called by all 32 lanes of the warp
-// (the logarithm branch is skipped when no lane of the warp needs it).
-__device__ __forceinline__ float2 phi_hat2(float2 x, float l_max, float phi_lmax) {
-    x.x = fminf(fmaxf(x.x, phi_lmax), l_max);
-    x.y = fminf(fmaxf(x.y, phi_lmax), l_max);
-    // t = e^-x
-    float2 pn = mul2(x, f2(-kL2E));                 // -fl(x log2 e)
-    float2 e = fma2(x, f2(kL2E), pn);               // x log2 e - fl(x log2 e), exact
-    e = fma2(x, f2(kL2ELo), e);
-    float2 t = make_float2(ex2_approx(pn.x), ex2_approx(pn.y));
-    t = fma2(t, mul2(e, f2(-kLn2)), t);
-    // small t: 2 atanh(t)
-    float2 t2 = mul2(t, t);
-    float2 poly = fma2(t2, fma2(t2, fma2(t2, f2(1.0f / 7.0f), f2(1.0f / 5.0f)), f2(1.0f / 3.0f)), f2(1.0f));
-    float2 res = mul2(add2(t, t), poly);
-    const bool big_x = t.x >= 0.0625f, big_y = t.y >= 0.0625f;
-    if (__any_sync(kFull, big_x || big_y)) {
-        float2 us = mul2(
-            x, fma2(x, fma2(x, fma2(x, fma2(x, fma2(x, f2(-1.0f / 720.0f), f2(1.0f / 120.0f)), f2(-1.0f / 24.0f)),
-                                    f2(1.0f / 6.0f)),
-                            f2(-0.5f)),
-                    f2(1.0f)));
-        float2 u1 = fma2(t, f2(-1.0f), f2(1.0f));
-        float2 u = make_float2(x.x < 0.25f ? us.x : u1.x, x.y < 0.25f ? us.y : u1.y);
-        float2 num = fma2(u, f2(-1.0f), f2(2.0f));
-        float2 ratio = mul2(num, make_float2(rcp_approx(u.x), rcp_approx(u.y)));
-        float2 lg = mul2(make_float2(lg2_approx(ratio.x), lg2_approx(ratio.y)), f2(kLn2));
-        res.x = big_x ? lg.x : res.x;
-        res.y = big_y ? lg.y : res.y;
-    }
-    return res;
-}
-
-// phi^ of V frames (pairs when V is even).
-template <int V>
-__device__ __forceinline__ void phi_hat_v(float (&x)[V], float l_max, float phi_lmax) {
-    if constexpr (V % 2 == 0) {
-#pragma unroll
-        for (int v = 0; v < V; v += 2) {
-            float2 y = phi_hat2(make_float2(x[v], x[v + 1]), l_max, phi_lmax);
-            x[v] = y.x;
-            x[v + 1] = y.y;
-        }
-    } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) x[v] = phi_hat(x[v], l_max, phi_lmax);
-    }
-}
 
 // Tabulated phi^: x clamped to [phi(L), L] (L <= 22, so x lies in
 // [2^-32, 2^5)), then the chord a + b x of its bucket, the bucket being the
