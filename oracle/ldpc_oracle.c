@@ -46,8 +46,8 @@
  *   same sign rule; alpha < 1 is the normalised, beta > 0 the offset variant.
  *   An empty minimum (degree-1 check) is L_MAX.
  *
- *   Tabulated phi (rule 2; the paper's "look-up tables" direction for further
- *   speed-up): phi is replaced by its chords on a log-spaced grid. The bucket
+ *   Tabulated phi (rule 2; the look-up-table direction the paper names for
+ *   further speed-up): phi is replaced by its chords on a log-spaced grid. The bucket
  *   of x >= 0 is the top 15 bits of the IEEE single-precision pattern of x
  *   (sign, 8 exponent bits, 6 mantissa bits): 64 buckets per octave, bucket
  *   key k spanning [e_k, e_(k+1)) with e_k the float whose bits are k << 17.
@@ -55,7 +55,7 @@
  *   (e_(k+1) - e_k), a continuous piecewise-linear function; the check rule
  *   is the sum-product rule with phi_T in place of phi (same saturation).
  *
- *   Quantised message storage (the paper's "lower precision" direction for
+ *   Quantised message storage (the reduced-precision direction the paper names for
  *   further speed-up; its own decoder keeps FP64): when qstep > 0 every
  *   check-to-bit message is stored as r = k * qstep, k = r / qstep rounded to
  *   the nearest integer (ties to even) and clamped to [-qlevels, qlevels].
