@@ -30,6 +30,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 #include "ldpc_pass.h"
 
 namespace ldpc {
@@ -202,6 +204,88 @@ __device__ __forceinline__ void store_v(M *p, const float (&x)[V]) {
     } else {
 #pragma unroll
         for (int v = 0; v < V; ++v) MsgIO<M>::store1(p + v, x[v]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2 residency. Between passes the posteriors (APP, 4n bytes per frame) are
+// the data worth keeping in L2: the bit kernel writes them and the next
+// check pass gathers them. Messages and channel LLRs stream through once per
+// kernel. So APP traffic carries an evict-last policy and message / LLR
+// reads an evict-first one (createpolicy + .L2::cache_hint).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+
+// B bytes from global memory (B-aligned) into dst, with an L2 policy.
+template <int B>
+__device__ __forceinline__ void ld_hint(void *dst, const void *src, uint64_t pol) {
+    if constexpr (B == 32) {
+        ld_hint<16>(dst, src, pol);
+        ld_hint<16>(static_cast<char *>(dst) + 16, static_cast<const char *>(src) + 16, pol);
+    } else if constexpr (B == 16) {
+        uint4 v;
+        asm volatile("ld.global.L2::cache_hint.v4.b32 {%0,%1,%2,%3}, [%4], %5;\n"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "l"(src), "l"(pol));
+        *static_cast<uint4 *>(dst) = v;
+    } else if constexpr (B == 8) {
+        uint2 v;
+        asm volatile("ld.global.L2::cache_hint.v2.b32 {%0,%1}, [%2], %3;\n" : "=r"(v.x), "=r"(v.y) : "l"(src), "l"(pol));
+        *static_cast<uint2 *>(dst) = v;
+    } else if constexpr (B == 4) {
+        uint32_t v;
+        asm volatile("ld.global.L2::cache_hint.b32 %0, [%1], %2;\n" : "=r"(v) : "l"(src), "l"(pol));
+        *static_cast<uint32_t *>(dst) = v;
+    } else if constexpr (B == 2) {
+        unsigned short v;
+        asm volatile("ld.global.L2::cache_hint.b16 %0, [%1], %2;\n" : "=h"(v) : "l"(src), "l"(pol));
+        *static_cast<unsigned short *>(dst) = v;
+    } else {
+        static_assert(B == 1, "1, 2, 4, 8, 16 or 32 bytes");
+        unsigned short v;
+        asm volatile("ld.global.L2::cache_hint.b8 %0, [%1], %2;\n" : "=h"(v) : "l"(src), "l"(pol));
+        *static_cast<unsigned char *>(dst) = (unsigned char)v;
+    }
+}
+
+// V messages of type M (or floats) with an L2 policy.
+template <int V, typename M>
+__device__ __forceinline__ void load_v_hint(const M *p, float (&x)[V], uint64_t pol) {
+    alignas(16) M raw[V];
+    ld_hint<V * (int)sizeof(M)>(raw, p, pol);
+    load_v<V, M>(raw, x);
+}
+
+// V floats to global memory with an L2 policy.
+template <int V>
+__device__ __forceinline__ void store_v_hint(float *p, const float (&x)[V], uint64_t pol) {
+    if constexpr (V == 8) {
+        asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;\n" ::"l"(p), "f"(x[0]), "f"(x[1]),
+                     "f"(x[2]), "f"(x[3]), "l"(pol)
+                     : "memory");
+        asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;\n" ::"l"(p + 4), "f"(x[4]), "f"(x[5]),
+                     "f"(x[6]), "f"(x[7]), "l"(pol)
+                     : "memory");
+    } else if constexpr (V == 4) {
+        asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;\n" ::"l"(p), "f"(x[0]), "f"(x[1]),
+                     "f"(x[2]), "f"(x[3]), "l"(pol)
+                     : "memory");
+    } else if constexpr (V == 2) {
+        asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1,%2}, %3;\n" ::"l"(p), "f"(x[0]), "f"(x[1]), "l"(pol)
+                     : "memory");
+    } else {
+        static_assert(V == 1, "V is 1, 2, 4 or 8");
+        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;\n" ::"l"(p), "f"(x[0]), "l"(pol) : "memory");
     }
 }
 
@@ -911,10 +995,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+        : "memory");
 }
 
 template <int D, int V, typename M, int S>
@@ -960,6 +1046,7 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 
     const int stride = gridDim.x * (kThreads / 32);
     const int w0 = blockIdx.x * (kThreads / 32) + warp;
     constexpr uint32_t kTx = (uint32_t)P::kRowA + (first ? 0u : (uint32_t)P::kRowR);  // bytes per input
+    const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
 
     // Copy the rows of one check (first slot b, degree d, lane k holding the
     // column of input k) into stage st.
@@ -971,9 +1058,10 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 
         if (lane < d) {
             const uint32_t base = smem_u32(ring + st * P::kStage);
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            bulk_g2s(base + lane * P::kRowA, qsrc + (size_t)jl * Fp + fbase, P::kRowA, bar);
+            bulk_g2s(base + lane * P::kRowA, qsrc + (size_t)jl * Fp + fbase, P::kRowA, bar, pol_keep);
             if (!first)
-                bulk_g2s(base + D * P::kRowA + lane * P::kRowR, r + (size_t)(b + lane) * Fp + fbase, P::kRowR, bar);
+                bulk_g2s(base + D * P::kRowA + lane * P::kRowR, r + (size_t)(b + lane) * Fp + fbase, P::kRowR, bar,
+                         pol_stream);
         }
     };
     auto get_desc = [&](int w) { return w < count ? desc[w] : make_int2(0, 0); };
@@ -1229,22 +1317,23 @@ __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
     }
     if (!__any_sync(kFull, any_live)) return;
 
+    const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
     for (int j = blockIdx.x * (kThreads / 32) + warp; j < a.n; j += gridDim.x * (kThreads / 32)) {
         const int e0 = a.col_ptr[j];
         const int e1 = a.col_ptr[j + 1];
         float acc[V];
-        load_v<V, float>(a.lamT + (size_t)j * Fp + f0, acc);
+        load_v_hint<V, float>(a.lamT + (size_t)j * Fp + f0, acc, pol_stream);
 #pragma unroll 4
         for (int e = e0; e < e1; ++e) {
             const int slot = a.edge_slot[e];
             float rv[V];
-            load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
+            load_v_hint<V, M>(r + (size_t)slot * Fp + f0, rv, pol_stream);
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] += rv[v];
         }
         float *dst = a.app + (size_t)j * Fp + f0;
         if (all_live) {
-            store_v<V, float>(dst, acc);
+            store_v_hint<V>(dst, acc, pol_keep);
         } else if (any_live) {
 #pragma unroll
             for (int v = 0; v < V; ++v)
@@ -1329,22 +1418,26 @@ static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t 
 // the grid is sized to the CTAs that fit on the GPU at once.
 template <int D, int V, typename M, int S, int MODE, int RULE>
 static cudaError_t launch_bulk_mode(const PassArgs &a, const int2 *desc, int32_t count, cudaStream_t s) {
-    static int resident_by_device[64] = {0};  // CTAs per SM, once per device
+    // CTAs per SM, set up once per device; concurrent first calls may both
+    // set it up (same attribute, same value), hence the atomic
+    static std::atomic<int> resident_by_device[64];
     int dev = 0;
     cudaGetDevice(&dev);
-    int &resident = resident_by_device[dev & 63];
+    std::atomic<int> &resident = resident_by_device[dev & 63];
     const size_t smem = (size_t)BulkShape<D, V, M, S>::kSmem;
-    if (resident == 0) {
+    int nres = resident.load(std::memory_order_acquire);
+    if (nres == 0) {
         cudaError_t e = cudaFuncSetAttribute(k_check_bulk<D, V, M, S, MODE, RULE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_bulk<D, V, M, S, MODE, RULE>, kThreads, smem);
         if (e != cudaSuccess) return e;
-        resident = nb > 0 ? nb : 1;
+        nres = nb > 0 ? nb : 1;
+        resident.store(nres, std::memory_order_release);
     }
     PassArgs b = a;
-    b.grid_ctas = a.sm_count * resident;
+    b.grid_ctas = a.sm_count * nres;
     dim3 grid = pass_grid(b, count, V);
     k_check_bulk<D, V, M, S, MODE, RULE><<<grid, kThreads, smem, s>>>(a, desc, count);
     return cudaGetLastError();
