@@ -309,6 +309,9 @@ typedef struct {
     int32_t early_exit;         /* as in ldpc_decode_opts_t                      */
     float l_max;                /* <= 0 = 20                                     */
     int32_t msg_dtype;          /* ldpc_msg_dtype                                */
+    int32_t check_rule;         /* as in ldpc_decode_opts_t (0 = sum-product)    */
+    float rule_alpha;           /* min-sum scale; <= 0 selects 1                 */
+    float rule_beta;            /* min-sum offset, >= 0                          */
 } ldpc_server_opts_t;
 
 typedef struct {

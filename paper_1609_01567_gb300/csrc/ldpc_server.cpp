@@ -248,6 +248,9 @@ extern "C" int ldpc_server_create(int32_t n_codes, ldpc_code_t *const *codes, co
     d.early_exit = o.early_exit;
     d.l_max = o.l_max > 0.0f ? o.l_max : 20.0f;
     d.msg_dtype = o.msg_dtype;
+    d.check_rule = o.check_rule;
+    d.rule_alpha = o.rule_alpha;
+    d.rule_beta = o.rule_beta;
     d.streams = 1;
     const int32_t max_batch = o.max_batch_frames > 0 ? o.max_batch_frames : 1024;
     if (max_batch > 8192) return set_error(LDPC_EINVAL, "ldpc_server_create: max_batch_frames above 8192");

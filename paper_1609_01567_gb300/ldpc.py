@@ -48,7 +48,8 @@ class ldpc_decode_opts_t(ctypes.Structure):
 class ldpc_server_opts_t(ctypes.Structure):
     _fields_ = [("max_batch_frames", ctypes.c_int32), ("max_slots", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
                 ("max_pending_frames", ctypes.c_int64), ("max_iter", ctypes.c_int32), ("early_exit", ctypes.c_int32),
-                ("l_max", ctypes.c_float), ("msg_dtype", ctypes.c_int32)]
+                ("l_max", ctypes.c_float), ("msg_dtype", ctypes.c_int32), ("check_rule", ctypes.c_int32),
+                ("rule_alpha", ctypes.c_float), ("rule_beta", ctypes.c_float)]
 
 
 class ldpc_server_stats_t(ctypes.Structure):
@@ -491,11 +492,13 @@ def _ptr_array(tensors):
 
 
 def ldpc_batch_create(codes, n_frames, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
-                      msg_dtype: str = "f32", frames_per_lane: int = 0, check_schedule: int = 0) -> Batch:
+                      msg_dtype: str = "f32", frames_per_lane: int = 0, check_schedule: int = 0,
+                      rule: str = "sum_product", rule_alpha: float = 1.0, rule_beta: float = 0.0) -> Batch:
     """A mixed-code batch over ``codes`` (``Code`` handles on one device)."""
     hs = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
     fr = (ctypes.c_int32 * len(codes))(*[int(f) for f in n_frames])
-    opts = _opts(early_exit, l_max, msg_dtype, False, None, frames_per_lane, check_schedule)
+    opts = _opts(early_exit, l_max, msg_dtype, False, None, frames_per_lane, check_schedule, 0, 0, rule, rule_alpha,
+                 rule_beta)
     h = ctypes.c_void_p()
     _check(library().ldpc_batch_create(len(codes), hs, fr, max_iter, ctypes.byref(opts), ctypes.byref(h)))
     return Batch(h, codes, n_frames)
@@ -565,11 +568,13 @@ class Server:
 
 def ldpc_server_create(codes, *, max_batch_frames: int = 1024, max_slots: int = 4, memory_budget: int = 0,
                        max_pending_frames: int = 0, max_iter: int = 50, early_exit: bool = True, l_max: float = 20.0,
-                       msg_dtype: str = "f16") -> Server:
+                       msg_dtype: str = "f16", rule: str = "sum_product", rule_alpha: float = 1.0,
+                       rule_beta: float = 0.0) -> Server:
     hs = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
     o = ldpc_server_opts_t(max_batch_frames=max_batch_frames, max_slots=max_slots, memory_budget=memory_budget,
                            max_pending_frames=max_pending_frames, max_iter=max_iter, early_exit=1 if early_exit else 0,
-                           l_max=float(l_max), msg_dtype=LDPC_MSG[msg_dtype])
+                           l_max=float(l_max), msg_dtype=LDPC_MSG[msg_dtype], check_rule=LDPC_RULE[rule],
+                           rule_alpha=float(rule_alpha), rule_beta=float(rule_beta))
     h = ctypes.c_void_p()
     _check(library().ldpc_server_create(len(codes), hs, ctypes.byref(o), ctypes.byref(h)))
     return Server(h, codes)

@@ -83,3 +83,21 @@ def test_unbounded_degree_code_matches_oracle(ldpc, oracle_mod):
     ref = oracle_mod.decode(code, llr.astype(np.float64), 12, early_exit=False, n_threads=8)
     bad, exempt = compare_decodes(got, ref)
     assert bad.size == 0, bad
+
+
+@pytest.mark.parametrize("msg,rule", [("i8", "sum_product"), ("f32", "sp_table"), ("bf16", "min_sum")])
+def test_batch_other_formats_and_rules(ldpc, mixed, msg, rule):
+    """The graph batch gives per-code decodes' results for every message
+    format and check rule."""
+    codes, frames, handles, llrs, sent = mixed
+    kw = dict(rule=rule, rule_alpha=0.8) if rule == "min_sum" else dict(rule=rule)
+    refs = [host(ldpc.ldpc_decode(h, l, 30, want_post=False, msg_dtype=msg, **kw)) for h, l in zip(handles, llrs)]
+    b = ldpc.ldpc_batch_create(handles, frames, 30, msg_dtype=msg, **kw)
+    outs = ldpc.ldpc_batch_run(b, llrs)
+    outs = ldpc.ldpc_batch_run(b, llrs, outs)  # captured graph
+    torch.cuda.synchronize()
+    for i, (o, ref) in enumerate(zip(outs, refs)):
+        got = host(o)
+        for k in ("bits", "iters", "ok"):
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"item {i} {msg} {rule} {k}")
+    b.close()

@@ -40,10 +40,12 @@ def host(o):
     return {k: v.cpu().numpy() for k, v in o.items()}
 
 
-@pytest.mark.parametrize("msg", ["f32", "f16"])
-def test_same_result_alone_and_in_the_mix(ldpc, setup, msg):
+@pytest.mark.parametrize("msg,rule", [("f32", "sum_product"), ("f16", "sum_product"), ("i8", "sum_product"),
+                                      ("f32", "min_sum")])
+def test_same_result_alone_and_in_the_mix(ldpc, setup, msg, rule):
     codes, handles, reqs = setup
-    srv = ldpc.ldpc_server_create(handles, max_batch_frames=256, max_slots=3, msg_dtype=msg, max_iter=30)
+    kw = dict(rule=rule, rule_alpha=0.8) if rule == "min_sum" else {}
+    srv = ldpc.ldpc_server_create(handles, max_batch_frames=256, max_slots=3, msg_dtype=msg, max_iter=30, **kw)
     alone = []
     for ci, llr in reqs:  # one request at a time
         rid, o = ldpc.ldpc_server_submit(srv, ci, llr, want_post=True)
@@ -60,7 +62,7 @@ def test_same_result_alone_and_in_the_mix(ldpc, setup, msg):
         for k in ("bits", "iters", "ok", "post"):
             np.testing.assert_array_equal(got[k], a[k], err_msg=f"code {ci} {k}")
         if msg == "f32":
-            ref = host(ldpc.ldpc_decode(handles[ci], llr, 30, msg_dtype=msg, streams=1))
+            ref = host(ldpc.ldpc_decode(handles[ci], llr, 30, msg_dtype=msg, streams=1, **kw))
             for k in ("bits", "iters", "ok", "post"):
                 np.testing.assert_array_equal(got[k], ref[k])
 
