@@ -46,6 +46,11 @@
  *   same sign rule; alpha < 1 is the normalised, beta > 0 the offset variant.
  *   An empty minimum (degree-1 check) is L_MAX.
  *
+ *   Degree-adaptive min-sum (rule 3; the paper names adaptive MS only by
+ *   citation, read here as one scale and offset per check degree): check i
+ *   of degree d uses alpha_d = alpha_by_degree[min(d, n_degrees - 1)] and
+ *   beta_d likewise in the min-sum rule above.
+ *
  *   Tabulated phi (rule 2; the look-up-table direction the paper names for
  *   further speed-up): phi is replaced by its chords on a log-spaced grid. The bucket
  *   of x >= 0 is the top 15 bits of the IEEE single-precision pattern of x
@@ -169,10 +174,12 @@ static double phi_chord_hat(double x, double l_max) {
 }
 
 /* Check rule selection: 0 = sum-product, 1 = min-sum family, 2 = sum-product
- * with tabulated phi. */
+ * with tabulated phi, 3 = min-sum with a scale and offset per check degree. */
 typedef struct {
     int rule;
     double alpha, beta;
+    const double *alpha_d, *beta_d;  /* rule 3: [n_deg], indexed by check degree */
+    int32_t n_deg;
     double qstep;     /* > 0: stored messages are quantised to this step */
     int32_t qlevels;  /* largest stored |k| */
 } orc_rule;
@@ -189,6 +196,12 @@ static double quantise(double r, const orc_rule *rule) {
 static void check_update_min_sum(const orc_graph *g, int32_t i, const double *q, double *r, double l_max,
                                  const orc_rule *rule, int *one) {
     int64_t b = g->cstart[i], d = g->cstart[i + 1] - b;
+    double alpha = rule->alpha, beta = rule->beta;
+    if (rule->rule == 3) {
+        int64_t t = d < rule->n_deg ? d : rule->n_deg - 1;
+        alpha = rule->alpha_d[t];
+        beta = rule->beta_d[t];
+    }
     for (int64_t k = 0; k < d; ++k) one[k] = q[g->cedge[b + k]] > 0.0;
     for (int64_t k = 0; k < d; ++k) {
         double m = l_max;
@@ -199,7 +212,7 @@ static void check_update_min_sum(const orc_graph *g, int32_t i, const double *q,
             if (a < m) m = a;
             parity ^= one[k2];
         }
-        double a = rule->alpha * m - rule->beta;
+        double a = alpha * m - beta;
         if (a < 0.0) a = 0.0;
         if (a > l_max) a = l_max;
         r[g->cedge[b + k]] = parity ? a : -a;
@@ -246,7 +259,7 @@ static int64_t sp_pass(const orc_graph *g, const double *lam, const double *r_pr
         }
     }
     for (int32_t i = 0; i < g->m; ++i) {
-        if (rule && rule->rule == 1)
+        if (rule && (rule->rule == 1 || rule->rule == 3))
             check_update_min_sum(g, i, q, r_next, l_max, rule, one);
         else
             check_update(g, i, q, r_next, l_max, mag, one, rule && rule->rule == 2);
@@ -279,6 +292,22 @@ static int64_t max_check_degree(const orc_graph *g) {
 /* Public entry points (called through ctypes from oracle.py)               */
 /* ------------------------------------------------------------------------ */
 
+/* Nonzero when a rule's parameters are out of range: alpha > 0 and beta >= 0
+ * (each table entry too, rule 3, which needs at least one entry); rule 2
+ * needs l_max <= 22, since the bucket grid spans [2^-32, 2^5). */
+static int rule_invalid(int32_t check_rule, double alpha, double beta, double l_max, const double *alpha_d,
+                        const double *beta_d, int32_t n_deg) {
+    if (check_rule < 0 || check_rule > 3 || !(alpha > 0.0) || !(beta >= 0.0)) return 1;
+    if (check_rule == 2 && !(l_max <= 22.0)) return 1;
+    if (check_rule == 3) {
+        if (n_deg < 1 || !alpha_d || !beta_d) return 1;
+        for (int32_t t = 0; t < n_deg; ++t)
+            if (!(alpha_d[t] > 0.0) || !(beta_d[t] >= 0.0) || !isfinite(alpha_d[t]) || !isfinite(beta_d[t]))
+                return 1;
+    }
+    return 0;
+}
+
 /* Decode n_frames frames of LLRs lam [F][n] (FP64).
  * Outputs: bits [F][n], iters [F], ok [F]; optional post [F][n] (APP LLRs)
  * and r_out [F][E] (last check-to-bit messages, edge order).
@@ -286,12 +315,12 @@ static int64_t max_check_degree(const orc_graph *g) {
 int orc_decode(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t *cols,
                const double *lam, int32_t n_frames, int32_t max_iter, int32_t early_exit, double l_max,
                uint8_t *bits, int32_t *iters, uint8_t *ok, double *post, double *r_out, int32_t n_threads,
-               int32_t check_rule, double alpha, double beta, double qstep, int32_t qlevels) {
+               int32_t check_rule, double alpha, double beta, double qstep, int32_t qlevels,
+               const double *alpha_by_degree, const double *beta_by_degree, int32_t n_degrees) {
     if (m < 0 || n < 0 || E < 0 || n_frames < 0 || max_iter < 0 || !(l_max > 0.0)) return -1;
-    if (check_rule < 0 || check_rule > 2 || !(alpha > 0.0) || beta < 0.0) return -1;
-    if (check_rule == 2 && !(l_max <= 22.0)) return -1; /* the bucket grid spans [2^-32, 2^5) */
+    if (rule_invalid(check_rule, alpha, beta, l_max, alpha_by_degree, beta_by_degree, n_degrees)) return -1;
     if (qstep < 0.0 || (qstep > 0.0 && qlevels < 1)) return -1;
-    orc_rule rule = {check_rule, alpha, beta, qstep, qlevels};
+    orc_rule rule = {check_rule, alpha, beta, alpha_by_degree, beta_by_degree, n_degrees, qstep, qlevels};
     orc_graph g;
     if (graph_build(m, n, E, rows, cols, &g)) return -1;
     int64_t dmax = max_check_degree(&g);
@@ -343,12 +372,12 @@ int orc_decode(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32
 int orc_pass(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t *cols,
              const double *lam, int32_t n_frames, const double *r_prev, double l_max,
              double *r_next, double *app, uint8_t *bits, int64_t *weight, int32_t n_threads,
-             int32_t check_rule, double alpha, double beta, double qstep, int32_t qlevels) {
+             int32_t check_rule, double alpha, double beta, double qstep, int32_t qlevels,
+             const double *alpha_by_degree, const double *beta_by_degree, int32_t n_degrees) {
     if (m < 0 || n < 0 || E < 0 || n_frames < 0 || !(l_max > 0.0)) return -1;
-    if (check_rule < 0 || check_rule > 2 || !(alpha > 0.0) || beta < 0.0) return -1;
-    if (check_rule == 2 && !(l_max <= 22.0)) return -1; /* the bucket grid spans [2^-32, 2^5) */
+    if (rule_invalid(check_rule, alpha, beta, l_max, alpha_by_degree, beta_by_degree, n_degrees)) return -1;
     if (qstep < 0.0 || (qstep > 0.0 && qlevels < 1)) return -1;
-    orc_rule rule = {check_rule, alpha, beta, qstep, qlevels};
+    orc_rule rule = {check_rule, alpha, beta, alpha_by_degree, beta_by_degree, n_degrees, qstep, qlevels};
     orc_graph g;
     if (graph_build(m, n, E, rows, cols, &g)) return -1;
     int64_t dmax = max_check_degree(&g);

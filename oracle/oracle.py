@@ -41,9 +41,10 @@ def _lib():
         i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
         vp = ctypes.c_void_p
         lib.orc_decode.argtypes = [i32, i32, i64, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp, vp, vp, i32, i32, dbl, dbl,
-                                   dbl, i32]
+                                   dbl, i32, vp, vp, i32]
         lib.orc_decode.restype = ctypes.c_int
-        lib.orc_pass.argtypes = [i32, i32, i64, vp, vp, vp, i32, vp, dbl, vp, vp, vp, vp, i32, i32, dbl, dbl, dbl, i32]
+        lib.orc_pass.argtypes = [i32, i32, i64, vp, vp, vp, i32, vp, dbl, vp, vp, vp, vp, i32, i32, dbl, dbl, dbl, i32,
+                                 vp, vp, i32]
         lib.orc_pass.restype = ctypes.c_int
         lib.orc_phi.argtypes = [dbl]
         lib.orc_phi.restype = dbl
@@ -75,7 +76,7 @@ def default_threads() -> int:
     return int(os.environ.get("LDPC_ORACLE_THREADS", "1"))
 
 
-RULES = {"sp": 0, "min_sum": 1, "sp_table": 2}
+RULES = {"sp": 0, "min_sum": 1, "sp_table": 2, "min_sum_adaptive": 3}
 
 # Stored-message formats: (quantisation step, largest |level|); "f64" keeps
 # the messages unrounded, "i8" stores k * 20/127 with |k| <= 127.
@@ -88,11 +89,27 @@ def _msg(msg):
     return MSG[msg]
 
 
+def _degree_tables(rule, alpha_by_degree, beta_by_degree):
+    """The per-check-degree scale and offset of rule "min_sum_adaptive"
+    (index = check degree; degrees past the end take the last entry), as
+    FP64 arrays kept alive by the caller, plus their length."""
+    if rule != "min_sum_adaptive":
+        return None, None, 0
+    a = np.ascontiguousarray(alpha_by_degree, dtype=np.float64)
+    b = np.ascontiguousarray(beta_by_degree if beta_by_degree is not None else np.zeros_like(a), dtype=np.float64)
+    if a.ndim != 1 or a.shape != b.shape:
+        raise ValueError("alpha_by_degree and beta_by_degree must be 1-D and of one length")
+    return a, b, int(a.shape[0])
+
+
 def decode(code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 20.0,
            want_post: bool = True, want_r: bool = False, n_threads: int | None = None,
-           rule: str = "sp", alpha: float = 1.0, beta: float = 0.0, msg="f64"):
+           rule: str = "sp", alpha: float = 1.0, beta: float = 0.0, msg="f64", alpha_by_degree=None,
+           beta_by_degree=None):
     """Sum-product decode (Algorithm 2) of LLRs ``llr`` [F, n] in FP64
     (``rule="min_sum"``: the min-sum family, |r| = clamp(alpha min - beta);
+    ``rule="min_sum_adaptive"``: the same with alpha and beta taken per check
+    degree d from ``alpha_by_degree[min(d, len - 1)]`` and ``beta_by_degree``;
     ``rule="sp_table"``: sum-product with phi on the chords of a log-spaced
     grid, 64 buckets per octave;
     ``msg``: a key of :data:`MSG` or a (step, levels) pair for quantised
@@ -112,10 +129,11 @@ def decode(code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 
     ok = np.zeros(f, dtype=np.uint8)
     post = np.zeros((f, n), dtype=np.float64) if want_post else None
     r = np.zeros((f, e), dtype=np.float64) if want_r else None
+    ad, bd, nd = _degree_tables(rule, alpha_by_degree, beta_by_degree)
     rc = _lib().orc_decode(code.m, code.n, e, _ptr(rows), _ptr(cols), _ptr(lam), f, max_iter,
                            1 if early_exit else 0, l_max, _ptr(bits), _ptr(iters), _ptr(ok), _ptr(post),
                            _ptr(r), n_threads if n_threads is not None else default_threads(), RULES[rule],
-                           alpha, beta, *_msg(msg))
+                           alpha, beta, *_msg(msg), _ptr(ad), _ptr(bd), nd)
     if rc != 0:
         raise ValueError("oracle decode rejected its input")
     out = {"bits": bits, "iters": iters, "ok": ok}
@@ -127,7 +145,7 @@ def decode(code, llr, max_iter: int, *, early_exit: bool = True, l_max: float = 
 
 
 def sp_pass(code, llr, r_prev=None, *, l_max: float = 20.0, n_threads: int | None = None, rule: str = "sp",
-            alpha: float = 1.0, beta: float = 0.0, msg="f64"):
+            alpha: float = 1.0, beta: float = 0.0, msg="f64", alpha_by_degree=None, beta_by_degree=None):
     """One flooding pass from messages ``r_prev`` [F, E] (None: first pass).
 
     Returns ``r`` [F, E], ``post`` [F, n], ``bits`` [F, n], ``weight`` [F].
@@ -141,9 +159,10 @@ def sp_pass(code, llr, r_prev=None, *, l_max: float = 20.0, n_threads: int | Non
     app = np.zeros((f, n), dtype=np.float64)
     bits = np.zeros((f, n), dtype=np.uint8)
     w = np.zeros(f, dtype=np.int64)
+    ad, bd, nd = _degree_tables(rule, alpha_by_degree, beta_by_degree)
     rc = _lib().orc_pass(code.m, code.n, e, _ptr(rows), _ptr(cols), _ptr(lam), f, _ptr(rp), l_max, _ptr(r),
                          _ptr(app), _ptr(bits), _ptr(w), n_threads if n_threads is not None else default_threads(),
-                         RULES[rule], alpha, beta, *_msg(msg))
+                         RULES[rule], alpha, beta, *_msg(msg), _ptr(ad), _ptr(bd), nd)
     if rc != 0:
         raise ValueError("oracle pass rejected its input")
     return {"r": r, "post": app, "bits": bits, "weight": w}

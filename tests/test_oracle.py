@@ -315,6 +315,59 @@ def test_min_sum_variants_and_bounds(oracle_mod):
     assert np.all(np.abs(plain) >= np.abs(exact) - 1e-12)
 
 
+def _scaled_max_log(lam, alpha, beta):
+    ml = max_log_parity(lam)
+    return np.sign(ml) * np.maximum(alpha * np.abs(ml) - beta, 0.0)
+
+
+def test_adaptive_min_sum_scales_each_check_by_its_own_degree(oracle_mod):
+    """Two disjoint checks of degrees 3 and 5: after the first check pass each
+    bit's extrinsic LLR is its check's brute-force max-log value with that
+    degree's scale and offset. The neighbouring table entries (degrees 2, 4,
+    6) hold other values, so reading the table at d - 1, d + 1 or at a
+    variable's degree fails."""
+    rows = [0, 0, 0] + [1] * 5
+    cols = list(range(8))
+    code = I.coo_code(2, 8, rows, cols)
+    alpha = [9.0, 9.0, 0.3, 0.6, 0.45, 0.8, 0.2]
+    beta = [0.0, 0.0, 0.7, 0.1, 0.5, 0.25, 1.3]
+    lam = np.random.default_rng(7).normal(0.0, 3.0, size=(40, 8))
+    out = oracle_mod.decode(code, lam, 0, early_exit=False, l_max=60.0, rule="min_sum_adaptive",
+                            alpha_by_degree=alpha, beta_by_degree=beta)
+    ext = out["post"] - lam
+    np.testing.assert_allclose(ext[:, :3], _scaled_max_log(lam[:, :3], 0.6, 0.1), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(ext[:, 3:], _scaled_max_log(lam[:, 3:], 0.8, 0.25), rtol=1e-12, atol=1e-12)
+
+
+def test_adaptive_min_sum_degrees_past_the_table_take_its_last_entry(oracle_mod):
+    code = I.coo_code(1, 6, [0] * 6, list(range(6)))
+    lam = np.random.default_rng(8).normal(0.0, 3.0, size=(30, 6))
+    out = oracle_mod.decode(code, lam, 0, early_exit=False, l_max=60.0, rule="min_sum_adaptive",
+                            alpha_by_degree=[1.0, 1.0, 0.5, 0.7], beta_by_degree=[0.0, 0.0, 0.0, 0.4])
+    np.testing.assert_allclose(out["post"] - lam, _scaled_max_log(lam, 0.7, 0.4), rtol=1e-12, atol=1e-12)
+
+
+def test_adaptive_min_sum_with_one_value_for_every_degree_is_the_plain_variant(oracle_mod, n1008):
+    """A table holding one (alpha, beta) for every degree reduces the adaptive
+    rule to the normalised/offset rule, pass for pass and bit for bit."""
+    code, cw = n1008
+    lam = I.gaussian_llr(cw[:6], I.sigma2_from_ebn0(1.5, 0.5), seed=9).astype(np.float64)
+    fixed = oracle_mod.decode(code, lam, 12, early_exit=False, rule="min_sum", alpha=0.75, beta=0.25)
+    adapt = oracle_mod.decode(code, lam, 12, early_exit=False, rule="min_sum_adaptive",
+                              alpha_by_degree=[0.75] * 3, beta_by_degree=[0.25] * 3)
+    np.testing.assert_array_equal(adapt["post"], fixed["post"])
+    np.testing.assert_array_equal(adapt["iters"], fixed["iters"])
+
+
+@pytest.mark.parametrize("alpha,beta", [([], []), ([0.5, 0.0], [0.0, 0.0]), ([0.5, 0.5], [0.0, -0.1]),
+                                        ([0.5, np.inf], [0.0, 0.0]), ([0.5, 0.5], [0.0, np.nan])])
+def test_adaptive_min_sum_rejects_bad_tables(oracle_mod, alpha, beta):
+    code = I.coo_code(1, 3, [0, 0, 0], [0, 1, 2])
+    with pytest.raises(ValueError):
+        oracle_mod.decode(code, np.zeros((1, 3)), 1, rule="min_sum_adaptive", alpha_by_degree=alpha,
+                          beta_by_degree=beta)
+
+
 # --- quantised message storage (int8: step 20/127, |k| <= 127) ----------------
 
 def test_quantised_messages_lie_on_the_int8_lattice_and_round_to_nearest(oracle_mod, n1008):
