@@ -184,12 +184,37 @@ typedef struct {
                            direction): phi replaced by its chords on 64
                            buckets per octave, the bucket of x being the top
                            15 bits of its float pattern (edges: the floats
-                           with bits key << 17); needs l_max <= 22        */
+                           with bits key << 17); needs l_max <= 22;
+                           LDPC_RULE_MIN_SUM_ADAPTIVE (3): the min-sum rule
+                           with alpha and beta chosen by the check's degree
+                           from the code's table (ldpc_code_set_rule_table;
+                           adaptive min-sum, which the paper names by
+                           citation only, read as degree-adaptive); needs
+                           that table set, ignores rule_alpha/rule_beta    */
     float rule_alpha;   /* min-sum scale; <= 0 selects 1                   */
     float rule_beta;    /* min-sum offset, >= 0                            */
 } ldpc_decode_opts_t;
 
-enum { LDPC_RULE_SUM_PRODUCT = 0, LDPC_RULE_MIN_SUM = 1, LDPC_RULE_SP_TABLE = 2 };
+enum { LDPC_RULE_SUM_PRODUCT = 0, LDPC_RULE_MIN_SUM = 1, LDPC_RULE_SP_TABLE = 2, LDPC_RULE_MIN_SUM_ADAPTIVE = 3 };
+
+/*
+ * Set the per-check-degree scale and offset of LDPC_RULE_MIN_SUM_ADAPTIVE
+ * (Section III-A names adaptive min-sum among the derived algorithms the
+ * edge-level scheme carries): a check of degree d uses
+ * |r| = clamp(alpha_d m - beta_d, 0, L_MAX), m the smallest other |q|, with
+ * (alpha_d, beta_d) = entry min(d, n_degrees - 1) of the tables.
+ *   n_degrees        >= 1 entries, indexed by check degree (0, 1, 2, ...)
+ *   alpha_by_degree  host [n_degrees] floats, each finite and > 0
+ *   beta_by_degree   host [n_degrees] floats, each finite and >= 0; NULL
+ *                    selects 0 for every degree
+ * The library copies the tables (synchronously) into device memory the code
+ * owns; the caller keeps its buffers. Call it while no decode of this code is
+ * in flight; later decodes (graph replays included) read the new values.
+ * Returns LDPC_EINVAL for a bad entry or a host-only code, LDPC_ECUDA on a
+ * failed copy.
+ */
+int ldpc_code_set_rule_table(ldpc_code_t *code, int32_t n_degrees, const float *alpha_by_degree,
+                             const float *beta_by_degree);
 
 /*
  * Decode n_frames frames.

@@ -9,6 +9,8 @@ runs split across batches or ranks see the same channel.
 
     python -m paper_1609_01567_gb300.ber --code n64800 --ebn0 1.0 1.2 1.4 \
         --frames 1000000 --batch 1024 --msg f32 f16 bf16 i8
+    python -m paper_1609_01567_gb300.ber --code n16200_r1/3 --ebn0 1.0 \
+        --rule min_sum_adaptive --degree-alpha 1 1 1 0.94 0.88
 """
 from __future__ import annotations
 
@@ -89,7 +91,8 @@ def summary(c: Counts, n: int) -> dict:
             "mean_iters": c.iterations / max(c.frames, 1)}
 
 
-CODES = {"n1008": inputs.small_code_n1008, "n64800": inputs.large_code_n64800}
+CODES = {"n1008": inputs.small_code_n1008, "n64800": inputs.large_code_n64800,
+         **{name: (lambda i=i: inputs.mixed_code(i)) for i, (_, _, name) in enumerate(inputs.MIXED_SPECS)}}
 
 
 def main(argv=None):
@@ -101,18 +104,32 @@ def main(argv=None):
     p.add_argument("--max-iter", type=int, default=50)
     p.add_argument("--msg", nargs="+", default=["f32", "f16", "bf16"])
     p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--rule", default="sum_product", help="sum_product, min_sum, sp_table or min_sum_adaptive")
+    p.add_argument("--alpha", type=float, default=1.0, help="min-sum scale")
+    p.add_argument("--beta", type=float, default=0.0, help="min-sum offset")
+    p.add_argument("--degree-alpha", type=float, nargs="+", help="min_sum_adaptive: scale by check degree 0, 1, ...")
+    p.add_argument("--degree-beta", type=float, nargs="+", help="min_sum_adaptive: offset by check degree 0, 1, ...")
     args = p.parse_args(argv)
 
     from . import ldpc
 
     code = CODES[args.code]()
     h = ldpc.code_from_inputs(code)
+    rule_kw = dict(rule=args.rule, rule_alpha=args.alpha, rule_beta=args.beta)
+    rule_desc = {"rule": args.rule}
+    if args.rule == "min_sum":
+        rule_desc.update(alpha=args.alpha, beta=args.beta)
+    if args.rule == "min_sum_adaptive":
+        if not args.degree_alpha:
+            raise SystemExit("min_sum_adaptive needs --degree-alpha")
+        ldpc.ldpc_code_set_rule_table(h, args.degree_alpha, args.degree_beta)
+        rule_desc.update(degree_alpha=args.degree_alpha, degree_beta=args.degree_beta)
     for eb in args.ebn0:
         for msg in args.msg:
             t0 = time.perf_counter()
             c = simulate(h, code, eb, args.frames, batch=args.batch, max_iter=args.max_iter, msg_dtype=msg,
-                         seed=args.seed)
-            line = {"code": args.code, "ebn0_db": eb, "msg_dtype": msg, "max_iter": args.max_iter,
+                         seed=args.seed, **rule_kw)
+            line = {"code": args.code, "ebn0_db": eb, "msg_dtype": msg, "max_iter": args.max_iter, **rule_desc,
                     "seconds": time.perf_counter() - t0, **summary(c, code.n)}
             print(json.dumps(line), flush=True)
 

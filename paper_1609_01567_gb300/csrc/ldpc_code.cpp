@@ -49,6 +49,7 @@ static void free_device_tables(ldpc_code *c) {
     cudaFree(c->d.bin_checks);
     cudaFree(c->d.bin_desc);
     cudaFree(c->d.phi_table);
+    cudaFree(c->d.ms_table);
     free_host_stream(c);
     free_decode_graphs(c);
     free_workspace(c->ws);
@@ -216,6 +217,8 @@ extern "C" int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t
             (e = upload(&c->d.bin_checks, c->bin_checks)) != cudaSuccess ||
             (e = upload(&c->d.bin_desc, c->bin_desc)) != cudaSuccess ||
             (e = upload(&c->d.phi_table, phi_chords())) != cudaSuccess ||
+            (e = upload(&c->d.ms_table, std::vector<float2>((size_t)c->max_cdeg + 1, make_float2(1.0f, 0.0f)))) !=
+                cudaSuccess ||
             (e = cudaEventCreateWithFlags(&c->ws.last_use, cudaEventDisableTiming)) != cudaSuccess) {
             int st = cuda_error(e, "ldpc_code_create: device upload");
             free_device_tables(c);
@@ -267,6 +270,36 @@ extern "C" void ldpc_code_destroy(ldpc_code_t *code) {
     if (!code) return;
     free_device_tables(code);
     delete code;
+}
+
+extern "C" int ldpc_code_set_rule_table(ldpc_code_t *c, int32_t n_degrees, const float *alpha_by_degree,
+                                        const float *beta_by_degree) {
+    if (!c) return set_error(LDPC_EINVAL, "ldpc_code_set_rule_table: code is NULL");
+    if (n_degrees < 1 || !alpha_by_degree)
+        return set_error(LDPC_EINVAL, "ldpc_code_set_rule_table: need n_degrees >= 1 and alpha_by_degree");
+    for (int32_t t = 0; t < n_degrees; ++t) {
+        const float a = alpha_by_degree[t], b = beta_by_degree ? beta_by_degree[t] : 0.0f;
+        if (!(a > 0.0f) || !std::isfinite(a) || !(b >= 0.0f) || !std::isfinite(b))
+            return set_error(LDPC_EINVAL, "ldpc_code_set_rule_table: entry %d = (%g, %g) needs alpha > 0, beta >= 0",
+                             t, (double)a, (double)b);
+    }
+    if (c->device < 0) return set_error(LDPC_EINVAL, "ldpc_code_set_rule_table: host-only code");
+    // one entry per degree 0 .. max check degree; degrees past the caller's
+    // table take its last entry
+    std::vector<float2> tab((size_t)c->max_cdeg + 1);
+    for (size_t d = 0; d < tab.size(); ++d) {
+        const int32_t t = (int64_t)d < n_degrees ? (int32_t)d : n_degrees - 1;
+        tab[d] = make_float2(alpha_by_degree[t], beta_by_degree ? beta_by_degree[t] : 0.0f);
+    }
+    std::lock_guard<std::mutex> lock(c->mu);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaMemcpy(c->d.ms_table, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_error(e, "ldpc_code_set_rule_table: cudaMemcpy");
+    c->ms_table_set = true;
+    return LDPC_OK;
 }
 
 extern "C" int ldpc_code_info(const ldpc_code_t *c, ldpc_code_info_t *info) {

@@ -322,6 +322,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     a.check_rule = o.check_rule;
     a.ms_alpha = o.rule_alpha > 0.0f ? o.rule_alpha : 1.0f;
     a.ms_beta = o.rule_beta;
+    a.ms_table = o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE ? c->d.ms_table : nullptr;
 
     Launcher L{c, s, o.profile != 0};
     cudaError_t e;
@@ -456,8 +457,10 @@ static int check_decode_args(const ldpc_code *c, int32_t F, int32_t max_iter, co
     if (o.streams < 0 || o.streams > 2) return set_error(LDPC_EINVAL, "%s: streams=%d not in {0, 1, 2}", fn, o.streams);
     if (o.tile_frames < 0) return set_error(LDPC_EINVAL, "%s: tile_frames=%d < 0", fn, o.tile_frames);
     if (o.check_rule != LDPC_RULE_SUM_PRODUCT && o.check_rule != LDPC_RULE_MIN_SUM &&
-        o.check_rule != LDPC_RULE_SP_TABLE)
+        o.check_rule != LDPC_RULE_SP_TABLE && o.check_rule != LDPC_RULE_MIN_SUM_ADAPTIVE)
         return set_error(LDPC_EINVAL, "%s: unknown check_rule %d", fn, o.check_rule);
+    if (o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE && !c->ms_table_set)
+        return set_error(LDPC_EINVAL, "%s: the adaptive min-sum rule needs ldpc_code_set_rule_table first", fn);
     if (o.check_rule == LDPC_RULE_SP_TABLE && !(l_max <= kPhiTableMaxLmax))
         return set_error(LDPC_EINVAL, "%s: the tabulated rule needs l_max <= 22 (got %g)", fn, (double)l_max);
     if (!(o.rule_beta >= 0.0f) || !std::isfinite(o.rule_alpha))

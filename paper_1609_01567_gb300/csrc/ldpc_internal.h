@@ -3,6 +3,7 @@
 // ldpc_pass.h.
 #pragma once
 
+#include <atomic>
 #include <climits>
 #include <mutex>
 #include <string>
@@ -85,6 +86,7 @@ struct ldpc_code {
     int64_t E = 0;
     int32_t max_cdeg = 0, max_vdeg = 0;
     int32_t ira_k = -1;  // k when columns k .. n-1 form the staircase (IRA form), else -1
+    std::atomic<bool> ms_table_set{false};  // ldpc_code_set_rule_table has filled d.ms_table
     // host tables
     std::vector<int32_t> var_of_edge;   // v  [E]
     std::vector<int32_t> chk_of_edge;   // c  [E]

@@ -64,6 +64,7 @@ struct DeviceTables {
     int32_t *bin_checks = nullptr; // [m']  checks grouped by degree bin
     int2 *bin_desc = nullptr;      // [m']  (first slot, degree) of each binned check
     float2 *phi_table = nullptr;   // [kPhiTableSize] chords (a, b) of the tabulated phi
+    float2 *ms_table = nullptr;    // [max check degree + 1] (alpha_d, beta_d) of the degree-adaptive min-sum
 };
 
 // Tabulated phi: bucket key = float bits >> 17 (64 buckets per octave) over
@@ -104,10 +105,12 @@ struct PassArgs {
     int32_t check_schedule;  // 0 auto, 1 direct loads, 2 shared-memory pipeline
     int32_t f_begin;     // first frame of the range this launch covers (a multiple of 32 V)
     int32_t f_count;     // frames in that range (a multiple of 32 V)
-    int32_t check_rule;  // 0 sum-product, 1 min-sum family, 2 sum-product with tabulated phi
+    int32_t check_rule;  // 0 sum-product, 1 min-sum family, 2 sum-product with tabulated phi,
+                         // 3 min-sum with (alpha, beta) per check degree from ms_table
     const float2 *phi_table;  // device chords of the tabulated phi (rule 2)
     float ms_alpha;      // min-sum scale
     float ms_beta;       // min-sum offset
+    const float2 *ms_table;   // degree-adaptive min-sum: (alpha, beta) indexed by check degree, else null
 };
 
 template <typename M>

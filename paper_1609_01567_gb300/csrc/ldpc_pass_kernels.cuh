@@ -558,10 +558,17 @@ __device__ __forceinline__ void store_frame_bits(uint32_t *row, int g, int lane,
 // paper names, not its exact rule): |r_k| = clamp(alpha m_k - beta, 0, L_MAX)
 // with m_k the smallest |q| of the other inputs (L_MAX when there is none),
 // found from the two smallest magnitudes and the position of the smallest;
-// same sign rule as sum-product.
+// same sign rule as sum-product. The degree-adaptive variant takes alpha and
+// beta from the table entry of the check's degree d.
 template <int D, int V, typename M, typename Load>
 __device__ __forceinline__ void min_sum_node(int d, bool first, bool syn, Load &&load, M *out, size_t Fp,
                                              const PassArgs &a, bool (&unsat)[V]) {
+    float alpha = a.ms_alpha, beta = a.ms_beta;
+    if (a.ms_table) {
+        const float2 t = __ldg(a.ms_table + d);
+        alpha = t.x;
+        beta = t.y;
+    }
     float m1[V], m2[V];
     int idx[V];
     uint32_t ones[V], z[V];
@@ -605,7 +612,7 @@ __device__ __forceinline__ void min_sum_node(int d, bool first, bool syn, Load &
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const float m = idx[v] == k ? m2[v] : m1[v];
-                const float mag = fminf(fmaxf(fmaf(a.ms_alpha, m, -a.ms_beta), 0.0f), a.l_max);
+                const float mag = fminf(fmaxf(fmaf(alpha, m, -beta), 0.0f), a.l_max);
                 o[v] = __int_as_float(__float_as_int(mag) | (int)((neg[v] << (31 - k)) & 0x80000000u));
             }
             store_v<V, M>(out + (size_t)k * Fp, o);
@@ -1189,6 +1196,12 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
         const int i = checks[w];
         const int b = a.row_ptr[i];
         const int d = a.row_ptr[i + 1] - b;
+        float alpha = a.ms_alpha, beta = a.ms_beta;
+        if (RULE == 1 && a.ms_table) {
+            const float2 t = __ldg(a.ms_table + d);
+            alpha = t.x;
+            beta = t.y;
+        }
         float hi[V], lo[V];  // sum-product: compensated total; min-sum: two smallest |q|
         int idx[V];
         uint32_t par[V], z[V];
@@ -1256,7 +1269,7 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
                 float mm;
                 if constexpr (RULE == 1) {
                     const float m = idx[v] == k ? lo[v] : hi[v];
-                    mm = fminf(fmaxf(fmaf(a.ms_alpha, m, -a.ms_beta), 0.0f), a.l_max);
+                    mm = fminf(fmaxf(fmaf(alpha, m, -beta), 0.0f), a.l_max);
                 } else {
                     float own = phi_rule(fabsf(qv[v]));
                     float err;
@@ -1494,7 +1507,7 @@ cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, 
                              cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     if (a.check_rule == 2) return launch_check_table<M>(a, checks, count, s);
-    if (a.check_rule == 1) return launch_check_rule<M, 1>(a, bin, checks, desc, count, s);
+    if (a.check_rule == 1 || a.check_rule == 3) return launch_check_rule<M, 1>(a, bin, checks, desc, count, s);
     return launch_check_rule<M, 0>(a, bin, checks, desc, count, s);
 }
 

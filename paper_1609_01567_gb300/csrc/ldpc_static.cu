@@ -188,6 +188,7 @@ cudaError_t run_static(ldpc_code *c, unsigned char *scratch, const float *llr, i
     a.check_rule = o.check_rule;
     a.ms_alpha = o.rule_alpha > 0.0f ? o.rule_alpha : 1.0f;
     a.ms_beta = o.rule_beta;
+    a.ms_table = o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE ? c->d.ms_table : nullptr;
 
     // what must start at zero: the syndrome flag rows, and posteriors (the
     // padding frames' columns are read but never written)
@@ -268,8 +269,10 @@ extern "C" int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int
     if (!msg_dtype_valid(o.msg_dtype)) return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown msg_dtype %d", o.msg_dtype);
     if (o.profile) return set_error(LDPC_EINVAL, "ldpc_decode_static: profiling is not available on this entry point");
     if (o.check_rule != LDPC_RULE_SUM_PRODUCT && o.check_rule != LDPC_RULE_MIN_SUM &&
-        o.check_rule != LDPC_RULE_SP_TABLE)
+        o.check_rule != LDPC_RULE_SP_TABLE && o.check_rule != LDPC_RULE_MIN_SUM_ADAPTIVE)
         return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown check_rule %d", o.check_rule);
+    if (o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE && !c->ms_table_set)
+        return set_error(LDPC_EINVAL, "ldpc_decode_static: the adaptive min-sum rule needs ldpc_code_set_rule_table first");
     if (o.check_rule == LDPC_RULE_SP_TABLE && !(l_max <= kPhiTableMaxLmax))
         return set_error(LDPC_EINVAL, "ldpc_decode_static: the tabulated rule needs l_max <= 22");
     if (!(o.rule_beta >= 0.0f) || !std::isfinite(o.rule_alpha))

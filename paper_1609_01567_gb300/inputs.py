@@ -352,13 +352,16 @@ def mixed_codes() -> list[Code]:
     one information bit of degree 64 and one check of degree 96 (94 H1
     sockets plus its two staircase ones).
     """
-    codes = []
-    for idx, (n, k, name) in enumerate(MIXED_SPECS):
-        over_v = {0: 64} if n == 8192 else None
-        over_c = {5: 94} if n == 8192 else None
-        codes.append(ira_code(n, k, {3: 0.8, 4: 0.2}, seed=100 + idx, var_degree_overrides=over_v,
-                              check_h1_overrides=over_c, name=name))
-    return codes
+    return [mixed_code(idx) for idx in range(len(MIXED_SPECS))]
+
+
+def mixed_code(idx: int) -> Code:
+    """Code ``idx`` of :func:`mixed_codes` alone (seed 100 + idx)."""
+    n, k, name = MIXED_SPECS[idx]
+    over_v = {0: 64} if n == 8192 else None
+    over_c = {5: 94} if n == 8192 else None
+    return ira_code(n, k, {3: 0.8, 4: 0.2}, seed=100 + idx, var_degree_overrides=over_v,
+                    check_h1_overrides=over_c, name=name)
 
 
 def zipf_frames(total: int, count: int, s: float = 1.1) -> list[int]:

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 LDPC_MSG = {"f32": 0, "f16": 1, "bf16": 2, "i8": 3}
-LDPC_RULE = {"sum_product": 0, "min_sum": 1, "sp_table": 2}
+LDPC_RULE = {"sum_product": 0, "min_sum": 1, "sp_table": 2, "min_sum_adaptive": 3}
 KERNEL_CLASSES = ("interleave", "check", "bit", "syndrome", "finalize", "other", "passes")
 
 
@@ -62,7 +62,7 @@ class ldpc_prof_t(ctypes.Structure):
 
 
 EXPORTS = ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira", "ldpc_decode_host_stream",
-           "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode",
+           "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_set_rule_table", "ldpc_code_tables", "ldpc_decode",
            "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_count_errors", "ldpc_batch_create",
            "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info", "ldpc_batch_destroy", "ldpc_server_create",
            "ldpc_server_submit", "ldpc_server_wait", "ldpc_server_stats", "ldpc_server_destroy", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
@@ -93,6 +93,7 @@ def library():
             lib.ldpc_code_destroy.restype = None
             lib.ldpc_code_info.argtypes = [vp, ctypes.POINTER(ldpc_code_info_t)]
             lib.ldpc_code_tables.argtypes = [vp] + [vp] * 11
+            lib.ldpc_code_set_rule_table.argtypes = [vp, i32, vp, vp]
             lib.ldpc_decode.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ldpc_decode_opts_t), vp, vp, vp, vp, vp]
             lib.ldpc_decode_host.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ldpc_decode_opts_t), vp, vp, vp, vp, vp]
             lib.ldpc_decode_static.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ldpc_decode_opts_t), vp, vp, vp, vp,
@@ -116,7 +117,8 @@ def library():
             lib.ldpc_last_error.restype = ctypes.c_char_p
             lib.ldpc_version.restype = ctypes.c_char_p
             for name in ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira",
-                         "ldpc_decode_host_stream", "ldpc_code_info", "ldpc_code_tables", "ldpc_decode", "ldpc_decode_host",
+                         "ldpc_decode_host_stream", "ldpc_code_info", "ldpc_code_set_rule_table", "ldpc_code_tables",
+                         "ldpc_decode", "ldpc_decode_host",
                          "ldpc_decode_static",
                          "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_count_errors",
                          "ldpc_batch_create", "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info",
@@ -218,6 +220,18 @@ def ldpc_code_info(code: Code) -> dict:
             "mean_var_degree": info.mean_var_degree, "check_bin_max_degree": list(info.check_bin_max_degree[:nb]),
             "check_bin_count": list(info.check_bin_count[:nb]), "device": info.device,
             "ira_k": info.ira_k}
+
+
+def ldpc_code_set_rule_table(code: Code, alpha_by_degree, beta_by_degree=None) -> None:
+    """Scale and offset per check degree for ``rule="min_sum_adaptive"``
+    (index = check degree; degrees past the end take the last entry)."""
+    a = np.ascontiguousarray(alpha_by_degree, dtype=np.float32)
+    b = None if beta_by_degree is None else np.ascontiguousarray(beta_by_degree, dtype=np.float32)
+    if a.ndim != 1 or (b is not None and b.shape != a.shape):
+        raise ValueError("alpha_by_degree and beta_by_degree must be 1-D and of one length")
+    vp = ctypes.c_void_p
+    _check(library().ldpc_code_set_rule_table(code.handle, a.shape[0], a.ctypes.data_as(vp),
+                                              None if b is None else b.ctypes.data_as(vp)))
 
 
 TABLE_NAMES = ("v", "c", "t", "s", "u", "ebar", "vbar", "cbar", "tbar", "sbar", "ubar")

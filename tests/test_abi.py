@@ -165,3 +165,18 @@ def test_ira_form_is_detected(ldpc):
     cols = np.where(code.cols == last, 0, np.where(code.cols == 0, last, code.cols))
     h = ldpc.ldpc_code_create(code.m, code.n, code.rows, cols, device=-1)
     assert ldpc.ldpc_code_info(h)["ira_k"] == -1
+
+
+def test_rule_table_validation(ldpc):
+    code = I.code_14_7()
+    h = ldpc.ldpc_code_create(code.m, code.n, code.rows, code.cols, device=-1)
+    for alpha, beta in (([], None), ([0.5, 0.0], None), ([0.5, -1.0], None), ([0.5], [-0.1]),
+                        ([float("inf")], None), ([0.5], [float("nan")])):
+        with pytest.raises(ldpc.LdpcError) as e:
+            ldpc.ldpc_code_set_rule_table(h, alpha, beta)
+        assert e.value.status == -1 and ("entry" in str(e.value) or "n_degrees" in str(e.value)), str(e.value)
+    with pytest.raises(ldpc.LdpcError) as e:  # a valid table needs device tables to land in
+        ldpc.ldpc_code_set_rule_table(h, [0.8, 0.7], [0.0, 0.1])
+    assert "host-only" in str(e.value)
+    with pytest.raises(ValueError):
+        ldpc.ldpc_code_set_rule_table(h, [0.8, 0.7], [0.1])

@@ -85,12 +85,16 @@ def test_unbounded_degree_code_matches_oracle(ldpc, oracle_mod):
     assert bad.size == 0, bad
 
 
-@pytest.mark.parametrize("msg,rule", [("i8", "sum_product"), ("f32", "sp_table"), ("bf16", "min_sum")])
+@pytest.mark.parametrize("msg,rule", [("i8", "sum_product"), ("f32", "sp_table"), ("bf16", "min_sum"),
+                                      ("f32", "min_sum_adaptive")])
 def test_batch_other_formats_and_rules(ldpc, mixed, msg, rule):
     """The graph batch gives per-code decodes' results for every message
-    format and check rule."""
+    format and check rule (the adaptive rule with each code's own table)."""
     codes, frames, handles, llrs, sent = mixed
     kw = dict(rule=rule, rule_alpha=0.8) if rule == "min_sum" else dict(rule=rule)
+    if rule == "min_sum_adaptive":
+        for i, h in enumerate(handles):
+            ldpc.ldpc_code_set_rule_table(h, [0.9 - 0.02 * ((d + i) % 7) for d in range(100)], [0.05 * (d % 3) for d in range(100)])
     refs = [host(ldpc.ldpc_decode(h, l, 30, want_post=False, msg_dtype=msg, **kw)) for h, l in zip(handles, llrs)]
     b = ldpc.ldpc_batch_create(handles, frames, 30, msg_dtype=msg, **kw)
     outs = ldpc.ldpc_batch_run(b, llrs)

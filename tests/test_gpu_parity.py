@@ -333,6 +333,91 @@ def test_min_sum_schedules_do_not_change_results(ldpc, n1008):
             np.testing.assert_array_equal(other[k], base[k], err_msg=f"V={v} schedule={sched} streams={nst} {k}")
 
 
+# --- degree-adaptive min-sum (rule "min_sum_adaptive") ---------------------------
+
+def degree_tables(n):
+    """A scale and an offset for every degree below n, each differing from its
+    neighbours', so that a table read at the wrong degree shows."""
+    d = np.arange(n)
+    return 0.55 + 0.04 * ((d * 37) % 11), 0.1 * (d % 4) + 0.02 * (d % 3)
+
+
+def test_adaptive_min_sum_checks_of_every_bin(ldpc, oracle_mod):
+    """Disjoint checks of degrees spanning every degree bin (and past the
+    table's end) after the first check pass, for each frames-per-lane width."""
+    degs = [1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 16, 17, 31, 32, 33, 64, 96]
+    rows = np.repeat(np.arange(len(degs)), degs)
+    cols = np.arange(rows.size)
+    code = I.coo_code(len(degs), int(rows.size), rows.tolist(), cols.tolist())
+    h = ldpc.code_from_inputs(code)
+    alpha, beta = degree_tables(40)
+    ldpc.ldpc_code_set_rule_table(h, alpha, beta)
+    llr = np.random.default_rng(11).normal(0.0, 3.0, size=(300, code.n)).astype(np.float32)
+    ref = oracle_mod.decode(code, llr.astype(np.float64), 0, early_exit=False, rule="min_sum_adaptive",
+                            alpha_by_degree=alpha.astype(np.float32), beta_by_degree=beta.astype(np.float32))
+    for v in (1, 2, 4):
+        got = gpu_decode(ldpc, h, llr, 0, early_exit=False, rule="min_sum_adaptive", frames_per_lane=v)
+        assert close(got["post"], ref["post"]).all(), (v, np.abs(got["post"] - ref["post"]).max())
+
+
+def test_adaptive_min_sum_lock_step_n1008(ldpc, oracle_mod, n1008):
+    """Check degrees 5 and 6 with their own scale and offset, pass by pass
+    from the GPU's own messages, and end to end on frames that stop early."""
+    code, cw, llr = n1008
+    h = ldpc.code_from_inputs(code)
+    alpha, beta = [1.0] * 5 + [0.8, 0.9], [0.0] * 5 + [0.05, 0.15]
+    ldpc.ldpc_code_set_rule_table(h, alpha, beta)
+    kw = dict(rule="min_sum_adaptive")
+    okw = dict(rule="min_sum_adaptive", alpha_by_degree=np.float32(alpha), beta_by_degree=np.float32(beta))
+    lam = llr.astype(np.float64)
+    prev_r = None
+    for t in range(0, 31, 5):
+        if t > 0:
+            prev_r = gpu_decode(ldpc, h, llr, t - 1, early_exit=False, want_r=True, **kw)["r"].astype(np.float64)
+        got = gpu_decode(ldpc, h, llr, t, early_exit=False, want_r=True, **kw)
+        ref = oracle_mod.sp_pass(code, lam, prev_r, n_threads=8, **okw)
+        assert close(got["post"], ref["post"]).all(), (t, float(np.abs(got["post"] - ref["post"]).max()))
+        assert close(got["r"], ref["r"], atol=1e-4).all(), (t, float(np.abs(got["r"] - ref["r"]).max()))
+    got = gpu_decode(ldpc, h, llr, 50, **kw)
+    ref = oracle_mod.decode(code, lam, 50, n_threads=8, **okw)
+    same = (got["bits"] == ref["bits"]).all(axis=1) & (got["iters"] == ref["iters"]) & (got["ok"] == ref["ok"])
+    short = ref["iters"] <= 20
+    exempt = near_zero_frames(ref["post"])
+    assert np.all(same | exempt | ~short), np.flatnonzero(~same & ~exempt & short)[:10]
+    assert short.sum() >= 200, short.sum()  # enough frames compared end to end
+    # a constant table is the plain normalised/offset rule, bit for bit
+    ldpc.ldpc_code_set_rule_table(h, [0.8], [0.2])
+    a = gpu_decode(ldpc, h, llr, 12, early_exit=False, **kw)
+    b = gpu_decode(ldpc, h, llr, 12, early_exit=False, rule="min_sum", rule_alpha=0.8, rule_beta=0.2)
+    for k in ("bits", "iters", "ok", "post"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def test_adaptive_min_sum_n64800_sampled_frames(ldpc, oracle_mod, n64800):
+    """The large workload's launch shape (256 frames), two passes, sampled
+    frames against the oracle from the GPU's own messages."""
+    code, cw, llr = n64800
+    h = ldpc.code_from_inputs(code)
+    alpha, beta = [1.0] * 5 + [0.9, 0.75], [0.0] * 5 + [0.3, 0.05]
+    ldpc.ldpc_code_set_rule_table(h, alpha, beta)
+    okw = dict(rule="min_sum_adaptive", alpha_by_degree=np.float32(alpha), beta_by_degree=np.float32(beta))
+    sample = np.array([0, 77, 200, 255])
+    prev_r = None
+    for t in range(2):
+        got = gpu_decode(ldpc, h, llr, t, early_exit=False, want_r=True, rule="min_sum_adaptive")
+        ref = oracle_mod.sp_pass(code, llr[sample].astype(np.float64), prev_r, n_threads=8, **okw)
+        assert close(got["post"][sample], ref["post"]).all(), (t, np.abs(got["post"][sample] - ref["post"]).max())
+        prev_r = got["r"][sample].astype(np.float64)
+
+
+def test_adaptive_min_sum_needs_a_table(ldpc, n1008):
+    code, cw, llr = n1008
+    h = ldpc.code_from_inputs(code)
+    with pytest.raises(ldpc.LdpcError) as e:
+        gpu_decode(ldpc, h, llr[:32], 5, rule="min_sum_adaptive")
+    assert "ldpc_code_set_rule_table" in str(e.value)
+
+
 # --- sum-product with tabulated phi (rule "sp_table") ------------------------------
 
 @pytest.mark.parametrize("d", [1, 2, 3, 6, 8, 17, 33, 96])

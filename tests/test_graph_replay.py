@@ -90,3 +90,18 @@ def test_host_entry_replays_and_counts_kernels(ldpc):
     ldpc.ldpc_decode_host(h, host, 15)
     k1 = ldpc.ldpc_prof_read(h, reset=True)["kernels"]
     assert k1 > 0 and k3 == 3 * k1
+
+
+def test_replays_read_the_current_rule_table(ldpc):
+    """A captured decode reads the code's degree table at replay time, so a
+    new table shows in the next replay."""
+    code = I.small_code_n1008()
+    h = ldpc.code_from_inputs(code)
+    buf = llrs(code, 300, 1.5, seed=21)
+    out = None
+    for rnd, (a5, a6) in enumerate(((0.7, 0.9), (0.7, 0.9), (0.7, 0.9), (0.95, 0.6), (0.6, 0.8))):
+        ldpc.ldpc_code_set_rule_table(h, [1.0] * 5 + [a5, a6], [0.0] * 5 + [0.1, 0.2])
+        out = ldpc.ldpc_decode(h, buf, 25, out=out, rule="min_sum_adaptive")
+        torch.cuda.synchronize()
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        same(got, direct(ldpc, h, buf, 25, rule="min_sum_adaptive"))
