@@ -78,7 +78,9 @@ __global__ void k_syndrome_words(const int32_t *__restrict__ row_ptr, const int3
 #pragma unroll
     for (int q = 0; q < W; ++q) z[q] = 0u;
     if (i < m) {
-        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        const int32_t e1 = row_ptr[i + 1];
+#pragma unroll 4
+        for (int32_t e = row_ptr[i]; e < e1; ++e) {
             const uint32_t *p = dec + (size_t)col_idx[e] * G + w0;
             if constexpr (W == 4) {
                 const uint4 v = *reinterpret_cast<const uint4 *>(p);
@@ -140,6 +142,38 @@ __global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ app,
                 bits[o + b] = xs[b] > 0.0f ? 1 : 0;
                 if (post) post[o + b] = xs[b];
             }
+        }
+    }
+}
+
+// Fixed-iteration decodes without posteriors: bits [F][n] from the decision
+// words dec [n][Fp/32] of the last bit pass (bit f % 32 of word f / 32 of row
+// j is APP_j > 0 for frame f, written for every frame when no frame retires
+// early): 2 MB of words read instead of the 66 MB APP array at n = 64800 and
+// 256 frames. A CTA covers 128 variables of one 32-frame word.
+__global__ void __launch_bounds__(256) k_finalize_words(const uint32_t *__restrict__ dec, uint8_t *__restrict__ bits,
+                                                        int32_t n, int32_t F, int32_t G) {
+    __shared__ __align__(16) uint32_t wt[kFinVars];
+    const int32_t j0 = blockIdx.x * kFinVars;
+    const int32_t g = blockIdx.y;
+    for (int t = threadIdx.x; t < kFinVars; t += blockDim.x) {
+        const int32_t j = j0 + t;
+        wt[t] = j < n ? dec[(size_t)j * G + g] : 0u;
+    }
+    __syncthreads();
+    const bool vec = (n & 3) == 0 && (reinterpret_cast<uintptr_t>(bits) & 3) == 0;
+    for (int wi = threadIdx.x; wi < 32 * (kFinVars / 4); wi += blockDim.x) {
+        const int fi = wi / (kFinVars / 4), q = wi % (kFinVars / 4);
+        const int32_t f = g * 32 + fi, j = j0 + 4 * q;
+        if (f >= F || j >= n) continue;
+        const uint4 x = reinterpret_cast<const uint4 *>(wt)[q];
+        const uint32_t b0 = (x.x >> fi) & 1u, b1 = (x.y >> fi) & 1u, b2 = (x.z >> fi) & 1u, b3 = (x.w >> fi) & 1u;
+        const size_t o = (size_t)f * n + j;
+        if (vec) {
+            *reinterpret_cast<uint32_t *>(bits + o) = b0 | b1 << 8 | b2 << 16 | b3 << 24;
+        } else {
+            const uint32_t bs[4] = {b0, b1, b2, b3};
+            for (int k = 0; k < 4 && j + k < n; ++k) bits[o + k] = (uint8_t)bs[k];
         }
     }
 }
@@ -427,7 +461,10 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     e = L(LDPC_K_FINALIZE, c->n > 0 ? 2 : 1, [&] {
         if (c->n > 0) {
             dim3 grid((unsigned)((c->n + kFinVars - 1) / kFinVars), (unsigned)((F + 31) / 32), 1);
-            k_finalize<<<grid, 256, 0, s>>>(w.app, bits, post, c->n, F, Fp);
+            if (!a.early_exit && !post)
+                k_finalize_words<<<grid, 256, 0, s>>>(w.dec, bits, c->n, F, Fp / 32);
+            else
+                k_finalize<<<grid, 256, 0, s>>>(w.app, bits, post, c->n, F, Fp);
         }
         k_frame_results<<<(F + 255) / 256, 256, 0, s>>>(w.done, a.status, w.stop_iter, final_row, F, max_iter, iters,
                                                         ok);

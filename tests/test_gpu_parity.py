@@ -251,6 +251,21 @@ def test_n64800_full_size_sampled_frames(ldpc, oracle_mod, n64800):
     np.testing.assert_array_equal(flip["ok"], got["ok"])
 
 
+def test_fixed_decodes_without_posteriors_give_the_same_bits(ldpc, n1008, n64800):
+    """Fixed-iteration decodes that skip the posteriors take their hard
+    decisions from the last bit pass's decision words instead of the APP
+    array; both give the same bits (the benchmark's configuration, ragged
+    batches, every frames-per-lane width, one or two streams)."""
+    for code, llr in ((n64800[0], n64800[2]), (n1008[0], n1008[2])):
+        h = ldpc.code_from_inputs(code)
+        for f, kw in ((256, {}), (256, dict(streams=1)), (37, {}), (300, dict(frames_per_lane=1)),
+                      (200, dict(frames_per_lane=2, streams=2)), (1, {})):
+            with_post = gpu_decode(ldpc, h, llr[:f], 7, early_exit=False, **kw)
+            words = gpu_decode(ldpc, h, llr[:f], 7, early_exit=False, want_post=False, **kw)
+            for k in ("bits", "iters", "ok"):
+                np.testing.assert_array_equal(words[k], with_post[k], err_msg=f"{code.name} F={f} {kw} {k}")
+
+
 def test_n64800_lock_step_two_passes(ldpc, oracle_mod, n64800):
     code, cw, llr = n64800
     h = ldpc.code_from_inputs(code)
