@@ -105,3 +105,24 @@ def test_replays_read_the_current_rule_table(ldpc):
         torch.cuda.synchronize()
         got = {k: v.cpu().numpy() for k, v in out.items()}
         same(got, direct(ldpc, h, buf, 25, rule="min_sum_adaptive"))
+
+
+@pytest.mark.parametrize("code_fn,F", [(I.small_code_n1008, 512), (I.large_code_n64800, 256)])
+def test_replays_with_halves_that_stop_far_apart(ldpc, code_fn, F):
+    """One half of the batch at high SNR (stops within a few iterations), the
+    other near the threshold (runs long), so the two pass streams retire their
+    warps at very different passes: replays equal direct decodes bit for bit,
+    for max_iter 50 and 23."""
+    code = code_fn()
+    h = ldpc.code_from_inputs(code)
+    lo = {1008: 1.2, 64800: 1.0}[code.n]
+    buf = torch.cat([llrs(code, F // 2, 4.0, seed=31), llrs(code, F // 2, lo, seed=32)])
+    for max_iter in (50, 23):
+        out = None
+        for _ in range(4):  # direct, captured, replayed, replayed
+            out = ldpc.ldpc_decode(h, buf, max_iter, out=out)
+        torch.cuda.synchronize()
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        ref = direct(ldpc, h, buf, max_iter)
+        same(got, ref)
+        assert ref["iters"][: F // 2].max() < 16 and ref["iters"][F // 2:].max() >= 20, ref["iters"]
