@@ -352,8 +352,10 @@ def run_ours(args):
     # (b) the streaming entry point: every step's LLRs copied in and results
     # copied out, overlapping the neighbouring steps' decodes
     outs2 = [host_out, {k: torch.empty_like(v, pin_memory=True) for k, v in host_out.items()}]
-    ldpc.ldpc_decode_host_stream(h, [llr_host[i % n_buf] for i in range(3)], args.max_iter,
-                                 outs=[outs2[i % 2] for i in range(3)], **kw)
+    # warm-up: each of the two staging slots' decodes is seen twice, so both
+    # are captured as graphs before the timed calls
+    ldpc.ldpc_decode_host_stream(h, [llr_host[i % n_buf] for i in range(4)], args.max_iter,
+                                 outs=[outs2[i % 2] for i in range(4)], **kw)
     if dist:
         dist.barrier()
     t0 = time.perf_counter()

@@ -266,6 +266,29 @@ def test_fixed_decodes_without_posteriors_give_the_same_bits(ldpc, n1008, n64800
                 np.testing.assert_array_equal(words[k], with_post[k], err_msg=f"{code.name} F={f} {kw} {k}")
 
 
+def test_offsets_past_two_to_the_32(ldpc, oracle_mod):
+    """Message offsets past 2^32: n = 262144 (E = 1,048,575) with 8192 frames
+    in one chunk puts slot * Fp up to 8.6e9 (about 71 GB on the device). Three
+    passes; sampled frames, the last one included (highest offsets), against
+    the oracle."""
+    from paper_1609_01567_gb300 import sweep
+    code = sweep.stand_in_code(262144)
+    h = ldpc.code_from_inputs(code)
+    F = 8192
+    assert code.n_edges * F > 2 ** 32
+    llr = ldpc.ldpc_gen_awgn(5, 0, F, code.n, I.sigma2_from_ebn0(1.5, code.rate))
+    out = ldpc.ldpc_decode(h, llr, 2, early_exit=False)
+    torch.cuda.synchronize()
+    sample = torch.tensor([0, 1, 4095, 8190, 8191])
+    got = {k: v[sample.to(v.device)].cpu().numpy() for k, v in out.items()}
+    lam = llr[sample.to(llr.device)].cpu().numpy().astype(np.float64)
+    del out, llr
+    torch.cuda.empty_cache()
+    ref = oracle_mod.decode(code, lam, 2, early_exit=False, n_threads=8)
+    bad, exempt = compare_decodes(got, ref, frames=sample.numpy())
+    assert bad.size == 0, (bad, exempt)
+
+
 def test_n64800_lock_step_two_passes(ldpc, oracle_mod, n64800):
     code, cw, llr = n64800
     h = ldpc.code_from_inputs(code)
