@@ -649,7 +649,7 @@ extern "C" int ldpc_decode(ldpc_code_t *c, const float *llr, int32_t F, int32_t 
                            const ldpc_decode_opts_t *opts, uint8_t *bits, int32_t *iters, uint8_t *ok, float *post,
                            void *stream) {
     ldpc_decode_opts_t o = opts ? *opts : default_opts();
-    float l_max;
+    float l_max = 20.0f;
     int st = check_decode_args(c, F, max_iter, o, &l_max, "ldpc_decode");
     if (st != LDPC_OK) return st;
     if (F == 0) return LDPC_OK;
@@ -664,7 +664,7 @@ extern "C" int ldpc_decode_host(ldpc_code_t *c, const float *llr_host, int32_t F
                                 const ldpc_decode_opts_t *opts, uint8_t *bits_host, int32_t *iters_host,
                                 uint8_t *ok_host, float *post_host, void *stream) {
     ldpc_decode_opts_t o = opts ? *opts : default_opts();
-    float l_max;
+    float l_max = 20.0f;
     int st = check_decode_args(c, F, max_iter, o, &l_max, "ldpc_decode_host");
     if (st != LDPC_OK) return st;
     if (o.r_out) return set_error(LDPC_EINVAL, "ldpc_decode_host: r_out must be NULL");
@@ -838,7 +838,7 @@ extern "C" int ldpc_batch_create(int32_t n_items, ldpc_code_t *const *codes, con
     *out = nullptr;
     if (n_items <= 0 || !codes || !n_frames) return set_error(LDPC_EINVAL, "ldpc_batch_create: empty batch");
     ldpc_decode_opts_t o = opts ? *opts : default_opts();
-    float l_max;
+    float l_max = 20.0f;
     for (int32_t i = 0; i < n_items; ++i) {
         int st = check_decode_args(codes[i], n_frames[i], max_iter, o, &l_max, "ldpc_batch_create");
         if (st != LDPC_OK) return st;

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_1609_01567_gb300 import inputs as I
-from tests.parity import ATOL, RTOL, close, compare_decodes, near_zero_frames
+from tests.parity import close, compare_decodes, near_zero_frames
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu

@@ -9,7 +9,6 @@ import os
 import socket
 
 import numpy as np
-import pytest
 
 from paper_1609_01567_gb300 import inputs as I
 from paper_1609_01567_gb300.shard import Counts, frame_range
