@@ -68,6 +68,15 @@
  *   the stored values; node arithmetic stays FP64. int8 storage is
  *   qstep = 20/127, qlevels = 127.
  *
+ *   Floating-point message storage (the same direction, 16-bit formats): each
+ *   message is rounded to the nearest value of a binary format with p
+ *   significand bits and minimum normal exponent emin, ties to even, as IEEE
+ *   754 defines round-to-nearest: at exponent e (2^e <= |r| < 2^(e+1)) the
+ *   values are spaced 2^(max(e, emin) - p + 1), so magnitudes below 2^emin
+ *   keep the subnormal spacing. binary16: p = 11, emin = -14; bfloat16:
+ *   p = 8, emin = -126. Stored messages stay far below either format's
+ *   largest value (|r| <= L_MAX), so overflow does not arise.
+ *
  *   Channel (BER-simulator section, Eqs. 3-4): x = 2c - 1, y = x + sigma z,
  *   lambda = 2 y / sigma^2, with z from Philox-4x64-10 (Salmon et al., SC'11)
  *   and the Box-Muller transform.
@@ -180,12 +189,28 @@ typedef struct {
     double alpha, beta;
     const double *alpha_d, *beta_d;  /* rule 3: [n_deg], indexed by check degree */
     int32_t n_deg;
-    double qstep;     /* > 0: stored messages are quantised to this step */
-    int32_t qlevels;  /* largest stored |k| */
+    int32_t qformat;  /* stored messages: 0 unrounded, 1 the lattice k * qstep,
+                         2 binary16, 3 bfloat16 */
+    double qstep;     /* format 1: the lattice step */
+    int32_t qlevels;  /* format 1: largest stored |k| */
 } orc_rule;
 
-/* The stored value of a message under quantised storage. */
+/* r rounded to the nearest value of a binary floating-point format with p
+ * significand bits and minimum normal exponent emin (ties to even). */
+static double round_to_format(double r, int p, int emin) {
+    if (r == 0.0 || !isfinite(r)) return r;
+    int e2;
+    frexp(r, &e2); /* |r| = m 2^e2, 1/2 <= m < 1: the leading bit has exponent e2 - 1 */
+    int e = e2 - 1;
+    if (e < emin) e = emin;
+    double spacing = ldexp(1.0, e - p + 1);
+    return nearbyint(r / spacing) * spacing; /* exact scaling by a power of two */
+}
+
+/* The stored value of a message under the rule's storage format. */
 static double quantise(double r, const orc_rule *rule) {
+    if (rule->qformat == 2) return round_to_format(r, 11, -14);
+    if (rule->qformat == 3) return round_to_format(r, 8, -126);
     double k = nearbyint(r / rule->qstep);
     if (k > rule->qlevels) k = rule->qlevels;
     if (k < -rule->qlevels) k = -rule->qlevels;
@@ -264,7 +289,7 @@ static int64_t sp_pass(const orc_graph *g, const double *lam, const double *r_pr
         else
             check_update(g, i, q, r_next, l_max, mag, one, rule && rule->rule == 2);
     }
-    if (rule && rule->qstep > 0.0)
+    if (rule && rule->qformat != 0)
         for (int64_t e = 0; e < g->E; ++e) r_next[e] = quantise(r_next[e], rule);
     for (int32_t j = 0; j < g->n; ++j) {
         double v = lam[j];
@@ -315,12 +340,12 @@ static int rule_invalid(int32_t check_rule, double alpha, double beta, double l_
 int orc_decode(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t *cols,
                const double *lam, int32_t n_frames, int32_t max_iter, int32_t early_exit, double l_max,
                uint8_t *bits, int32_t *iters, uint8_t *ok, double *post, double *r_out, int32_t n_threads,
-               int32_t check_rule, double alpha, double beta, double qstep, int32_t qlevels,
+               int32_t check_rule, double alpha, double beta, int32_t qformat, double qstep, int32_t qlevels,
                const double *alpha_by_degree, const double *beta_by_degree, int32_t n_degrees) {
     if (m < 0 || n < 0 || E < 0 || n_frames < 0 || max_iter < 0 || !(l_max > 0.0)) return -1;
     if (rule_invalid(check_rule, alpha, beta, l_max, alpha_by_degree, beta_by_degree, n_degrees)) return -1;
-    if (qstep < 0.0 || (qstep > 0.0 && qlevels < 1)) return -1;
-    orc_rule rule = {check_rule, alpha, beta, alpha_by_degree, beta_by_degree, n_degrees, qstep, qlevels};
+    if (qformat < 0 || qformat > 3 || (qformat == 1 && (!(qstep > 0.0) || qlevels < 1))) return -1;
+    orc_rule rule = {check_rule, alpha, beta, alpha_by_degree, beta_by_degree, n_degrees, qformat, qstep, qlevels};
     orc_graph g;
     if (graph_build(m, n, E, rows, cols, &g)) return -1;
     int64_t dmax = max_check_degree(&g);
@@ -372,12 +397,12 @@ int orc_decode(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32
 int orc_pass(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t *cols,
              const double *lam, int32_t n_frames, const double *r_prev, double l_max,
              double *r_next, double *app, uint8_t *bits, int64_t *weight, int32_t n_threads,
-             int32_t check_rule, double alpha, double beta, double qstep, int32_t qlevels,
+             int32_t check_rule, double alpha, double beta, int32_t qformat, double qstep, int32_t qlevels,
              const double *alpha_by_degree, const double *beta_by_degree, int32_t n_degrees) {
     if (m < 0 || n < 0 || E < 0 || n_frames < 0 || !(l_max > 0.0)) return -1;
     if (rule_invalid(check_rule, alpha, beta, l_max, alpha_by_degree, beta_by_degree, n_degrees)) return -1;
-    if (qstep < 0.0 || (qstep > 0.0 && qlevels < 1)) return -1;
-    orc_rule rule = {check_rule, alpha, beta, alpha_by_degree, beta_by_degree, n_degrees, qstep, qlevels};
+    if (qformat < 0 || qformat > 3 || (qformat == 1 && (!(qstep > 0.0) || qlevels < 1))) return -1;
+    orc_rule rule = {check_rule, alpha, beta, alpha_by_degree, beta_by_degree, n_degrees, qformat, qstep, qlevels};
     orc_graph g;
     if (graph_build(m, n, E, rows, cols, &g)) return -1;
     int64_t dmax = max_check_degree(&g);
@@ -401,6 +426,17 @@ int orc_pass(int32_t m, int32_t n, int64_t E, const int32_t *rows, const int32_t
     }
     graph_free(&g);
     return failed ? -1 : 0;
+}
+
+/* The stored value of r under storage format qformat (1 needs qstep and
+ * qlevels), exported for the pins of the storage formats. */
+double orc_store(double r, int32_t qformat, double qstep, int32_t qlevels) {
+    orc_rule rule;
+    memset(&rule, 0, sizeof(rule));
+    rule.qformat = qformat;
+    rule.qstep = qstep;
+    rule.qlevels = qlevels;
+    return qformat == 0 ? r : quantise(r, &rule);
 }
 
 /* phi and its tabulated form, exported for the pins of rule 2. */

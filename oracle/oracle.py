@@ -41,10 +41,12 @@ def _lib():
         i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
         vp = ctypes.c_void_p
         lib.orc_decode.argtypes = [i32, i32, i64, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp, vp, vp, i32, i32, dbl, dbl,
-                                   dbl, i32, vp, vp, i32]
+                                   i32, dbl, i32, vp, vp, i32]
         lib.orc_decode.restype = ctypes.c_int
-        lib.orc_pass.argtypes = [i32, i32, i64, vp, vp, vp, i32, vp, dbl, vp, vp, vp, vp, i32, i32, dbl, dbl, dbl, i32,
-                                 vp, vp, i32]
+        lib.orc_pass.argtypes = [i32, i32, i64, vp, vp, vp, i32, vp, dbl, vp, vp, vp, vp, i32, i32, dbl, dbl, i32, dbl,
+                                 i32, vp, vp, i32]
+        lib.orc_store.argtypes = [dbl, i32, dbl, i32]
+        lib.orc_store.restype = dbl
         lib.orc_pass.restype = ctypes.c_int
         lib.orc_phi.argtypes = [dbl]
         lib.orc_phi.restype = dbl
@@ -78,15 +80,21 @@ def default_threads() -> int:
 
 RULES = {"sp": 0, "min_sum": 1, "sp_table": 2, "min_sum_adaptive": 3}
 
-# Stored-message formats: (quantisation step, largest |level|); "f64" keeps
-# the messages unrounded, "i8" stores k * 20/127 with |k| <= 127.
-MSG = {"f64": (0.0, 0), "i8": (20.0 / 127.0, 127)}
+# Stored-message formats: (format, lattice step, largest |level|). "f64"
+# keeps the messages unrounded, "i8" stores k * 20/127 with |k| <= 127,
+# "f16" and "bf16" round to IEEE binary16 and bfloat16 (nearest, ties to even).
+MSG = {"f64": (0, 0.0, 0), "i8": (1, 20.0 / 127.0, 127), "f16": (2, 0.0, 0), "bf16": (3, 0.0, 0)}
 
 
 def _msg(msg):
-    if isinstance(msg, tuple):
-        return float(msg[0]), int(msg[1])
+    if isinstance(msg, tuple):  # a lattice (step, levels)
+        return 1, float(msg[0]), int(msg[1])
     return MSG[msg]
+
+
+def store(r: float, msg) -> float:
+    """The stored value of one message under storage format ``msg``."""
+    return _lib().orc_store(float(r), *_msg(msg))
 
 
 def _degree_tables(rule, alpha_by_degree, beta_by_degree):

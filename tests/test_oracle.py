@@ -422,6 +422,109 @@ def test_quantised_decoder_keeps_codeword_symmetry(oracle_mod, n1008):
     assert base["ok"].mean() > 0.5
 
 
+# --- 16-bit floating-point message storage (binary16, bfloat16) ---------------------
+
+def _nearest_by_patterns(x, fmt):
+    """The value of ``fmt`` nearest to x > 0 found by enumerating bit patterns
+    around x (ties to the even pattern): binary16 patterns through numpy's
+    float16 type, bfloat16 patterns as float32 patterns with 16 zero low bits."""
+    import struct
+    if fmt == "f16":
+        b0 = int(np.array([x], dtype=np.float64).astype(np.float16).view(np.uint16)[0])
+        cands = [(float(np.array([b], dtype=np.uint16).view(np.float16)[0]), b) for b in range(max(b0 - 3, 0), b0 + 4)
+                 if b < 0x7c00]
+    else:
+        b0 = struct.unpack("<I", struct.pack("<f", float(np.float32(x))))[0] >> 16
+        cands = [(struct.unpack("<f", struct.pack("<I", b << 16))[0], b) for b in range(max(b0 - 3, 0), b0 + 4)]
+    best = min(abs(x - v) for v, _ in cands)
+    ties = [(v, b) for v, b in cands if abs(x - v) == best]
+    return next(v for v, b in ties if b % 2 == 0) if len(ties) > 1 else ties[0][0]
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+def test_16_bit_storage_rounds_to_nearest_even(oracle_mod, fmt):
+    """The oracle's binary16/bfloat16 rounding against a brute-force search
+    over bit patterns: random magnitudes from 1e-9 (binary16 subnormals and
+    underflow) to 30, exact midpoints between neighbouring values (ties go to
+    the even pattern), representable values (unchanged), zero and odd
+    symmetry; binary16 also against numpy's float16 conversion."""
+    rng = np.random.default_rng(16)
+    xs = list(np.exp(rng.uniform(np.log(1e-9), np.log(30.0), 3000)))
+    for x in xs[:200]:  # a value, its successor (next bit pattern) and their midpoint, a tie
+        lo = _nearest_by_patterns(x, fmt)
+        hi = _next_up(lo, fmt)
+        xs += [lo, hi, (lo + hi) / 2.0]
+    ties = 0
+    for x in xs:
+        want = _nearest_by_patterns(x, fmt)
+        got = oracle_mod.store(x, fmt)
+        ties += abs(x - _next_up(got, fmt)) == abs(x - got) or (got > 0 and abs(x - got) == abs(x - _next_down(got, fmt)))
+        assert got == want, (fmt, x, got, want)
+        assert oracle_mod.store(-x, fmt) == -got
+        if fmt == "f16":
+            assert got == float(np.float16(x)), (x, got)
+    assert oracle_mod.store(0.0, fmt) == 0.0
+    assert ties >= 150, ties  # the midpoints are exact ties
+
+
+def _pattern(v, fmt):
+    import struct
+    if fmt == "f16":
+        return int(np.array([v], dtype=np.float64).astype(np.float16).view(np.uint16)[0])
+    return struct.unpack("<I", struct.pack("<f", float(np.float32(v))))[0] >> 16
+
+
+def _value(b, fmt):
+    import struct
+    if fmt == "f16":
+        return float(np.array([b], dtype=np.uint16).view(np.float16)[0])
+    return struct.unpack("<f", struct.pack("<I", b << 16))[0]
+
+
+def _next_up(v, fmt):
+    return _value(_pattern(v, fmt) + 1, fmt)
+
+
+def _next_down(v, fmt):
+    return _value(_pattern(v, fmt) - 1, fmt)
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+def test_16_bit_stored_messages_and_posteriors(oracle_mod, n1008, fmt):
+    """Stored messages are values of the format, each the nearest one to the
+    unrounded message from the same inputs; the APP sums the stored messages;
+    the decoder keeps the exact codeword sign symmetry (rounding to nearest
+    even is odd-symmetric)."""
+    code, cw = n1008
+    lam = I.gaussian_llr(cw[:8], I.sigma2_from_ebn0(1.5, 0.5), seed=5).astype(np.float64)
+    prev = oracle_mod.sp_pass(code, lam, msg=fmt)["r"]
+    v = oracle_mod.address_iterators(code)["v"]
+    for r_prev in (None, prev):
+        exact = oracle_mod.sp_pass(code, lam, r_prev)
+        stored = oracle_mod.sp_pass(code, lam, r_prev, msg=fmt)
+        r = stored["r"]
+        if fmt == "f16":
+            np.testing.assert_array_equal(r.astype(np.float16).astype(np.float64), r)
+        else:
+            bits = r.astype(np.float32).view(np.uint32)
+            np.testing.assert_array_equal(r.astype(np.float32).astype(np.float64), r)
+            assert not np.any(bits & 0xFFFF)
+        sample = np.random.default_rng(1).choice(r.size, 300, replace=False)
+        for i in sample:
+            u = exact["r"].flat[i]
+            assert r.flat[i] == np.sign(u) * _nearest_by_patterns(abs(u), fmt) or u == 0.0
+        app = lam.copy()
+        for f in range(lam.shape[0]):
+            np.add.at(app[f], v, r[f])
+        np.testing.assert_allclose(stored["post"], app, rtol=1e-12, atol=1e-12)
+    lam0 = I.gaussian_llr(np.zeros_like(cw), I.sigma2_from_ebn0(1.5, 0.5), seed=3).astype(np.float64)
+    base = oracle_mod.decode(code, lam0, 30, msg=fmt)
+    flip = oracle_mod.decode(code, lam0 * (1.0 - 2.0 * cw), 30, msg=fmt)
+    np.testing.assert_array_equal(flip["iters"], base["iters"])
+    np.testing.assert_array_equal(flip["bits"], base["bits"] ^ cw)
+    np.testing.assert_array_equal(flip["post"], base["post"] * (1.0 - 2.0 * cw))
+
+
 # --- tabulated phi (rule "sp_table") ------------------------------------------------
 
 def test_tabulated_phi_is_the_chord_of_a_convex_function(oracle_mod):
