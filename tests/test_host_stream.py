@@ -47,3 +47,28 @@ def test_stream_shared_outputs_hold_the_last_batch(ldpc):
     np.testing.assert_array_equal(shared["bits"].numpy(), ref["bits"].cpu().numpy())
     np.testing.assert_array_equal(shared["iters"].numpy(), ref["iters"].cpu().numpy())
     assert ldpc.ldpc_decode_host_stream(h, [], 10) == []
+
+
+@pytest.mark.parametrize("msg", ["f32", "bf16"])
+def test_stream_at_the_benchmark_configuration(ldpc, msg):
+    """The end-to-end configuration of the benchmark: n = 64800, 256 frames,
+    10 fixed iterations, six batches through the two staging slots (each
+    slot's decode captured as a graph and replayed), and the one-call host
+    entry point; every batch equals the device decode bit for bit."""
+    code = I.large_code_n64800()
+    h = ldpc.code_from_inputs(code)
+    s2 = I.sigma2_from_ebn0(1.0, code.rate)
+    llrs = [ldpc.ldpc_gen_awgn(70 + b, 0, 256, code.n, s2).cpu().pin_memory() for b in range(3)]
+    batches = [llrs[b % 3] for b in range(6)]
+    outs = ldpc.ldpc_decode_host_stream(h, batches, 10, early_exit=False, msg_dtype=msg)
+    refs = []
+    for b in range(3):
+        ref = ldpc.ldpc_decode(h, llrs[b].cuda(), 10, early_exit=False, want_post=False, msg_dtype=msg)
+        torch.cuda.synchronize()
+        refs.append({k: v.cpu().numpy() for k, v in ref.items()})
+    for b in range(6):
+        for k in ("bits", "iters", "ok"):
+            np.testing.assert_array_equal(outs[b][k].numpy(), refs[b % 3][k], err_msg=f"batch {b} {k}")
+    one = ldpc.ldpc_decode_host(h, llrs[1], 10, early_exit=False, msg_dtype=msg)
+    for k in ("bits", "iters", "ok"):
+        np.testing.assert_array_equal(one[k].numpy(), refs[1][k], err_msg=f"one call {k}")

@@ -127,3 +127,17 @@ def test_16_bit_full_decode_n1008(ldpc, oracle_mod, n1008, fmt):
     same = (got["bits"] == ref["bits"]).all(axis=1) & (got["iters"] == ref["iters"]) & (got["ok"] == ref["ok"])
     assert same.mean() >= 0.97, np.flatnonzero(~same)[:10]
     assert (ref["ok"] == 1).mean() > 0.8
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+def test_16_bit_fer_against_the_oracle_with_the_same_storage(ldpc, oracle_mod, fmt):
+    from paper_1609_01567_gb300 import ber
+    code = I.small_code_n1008()
+    h = ldpc.code_from_inputs(code)
+    frames, ebn0, seed = 3000, 1.5, 9
+    lam = oracle_mod.gen_awgn(seed, 0, frames, code.n, I.sigma2_from_ebn0(ebn0, code.rate))
+    ref = oracle_mod.decode(code, lam, 50, want_post=False, n_threads=16, msg=fmt)
+    k_ref = int(ref["bits"].any(axis=1).sum())
+    c = ber.simulate(h, code, ebn0, frames, batch=512, max_iter=50, msg_dtype=fmt, seed=seed)
+    assert 30 < k_ref < frames - 30
+    assert abs(c.frame_errors - k_ref) <= max(4, k_ref // 20), (c.frame_errors, k_ref)
