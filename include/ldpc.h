@@ -51,8 +51,10 @@ typedef enum {
 
 typedef enum {
     LDPC_MSG_F32 = 0,   /* check-to-bit messages stored as float              */
-    LDPC_MSG_F16 = 1,   /* stored as IEEE half; all node sums stay in float   */
-    LDPC_MSG_BF16 = 2,  /* stored as bfloat16; all node sums stay in float    */
+    LDPC_MSG_F16 = 1,   /* stored as IEEE binary16, rounded to nearest (ties
+                           to even, subnormals kept); node sums stay float  */
+    LDPC_MSG_BF16 = 2,  /* stored as bfloat16, rounded to nearest (ties to
+                           even); node sums stay in float                   */
     LDPC_MSG_I8 = 3     /* stored as int8 in steps of 20/127, saturating at
                            +-20 (L_MAX above 20 acts as 20 for the stored
                            messages); all node arithmetic stays in float    */
