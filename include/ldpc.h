@@ -152,8 +152,13 @@ typedef struct {
                            <= 0 select the default 20. Check inputs and outputs
                            are clamped to [phi(L_MAX), L_MAX] in magnitude    */
     int32_t msg_dtype;  /* ldpc_msg_dtype of the stored check-to-bit messages */
-    int32_t profile;    /* nonzero: time every kernel launch with CUDA events
-                           on `stream` (read with ldpc_prof_read)             */
+    int32_t profile;    /* nonzero: time the decode with CUDA events on
+                           `stream` (read with ldpc_prof_read) and run it
+                           directly, never from a captured graph; 2 times
+                           only the region of the flooding passes, so the
+                           kernels keep their programmatic (overlapped)
+                           launches; any other nonzero value also times
+                           every kernel launch                             */
     float *r_out;       /* optional device [n_frames][n_edges] float: the last
                            check-to-bit messages in edge order (for checking
                            one iteration at a time); NULL to skip            */

@@ -20,6 +20,7 @@ constexpr int32_t kMaxChunkFrames = 8192;
 // frames get lambda = 0.
 __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ llr, float *__restrict__ lamT,
                                                     int32_t n, int32_t F, int32_t Fp) {
+    pdl_wait_then_release();
     // tile of 32 frames x 128 variables: frame rows read as float4 when the
     // rows are 4-aligned, variable rows written 32 frames (128 bytes) at once
     __shared__ float tile[128][33];
@@ -72,6 +73,7 @@ __global__ void k_init_done(uint32_t *done, uint32_t *status, int32_t F, int32_t
 template <int W>
 __global__ void k_syndrome_words(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, int32_t m,
                                  const uint32_t *__restrict__ dec, int32_t G, uint32_t *__restrict__ row) {
+    pdl_wait_then_release();
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t w0 = blockIdx.y * W;
     uint32_t z[W];
@@ -109,6 +111,7 @@ constexpr int kFinStride = kFinVars + 4;  // float4-aligned rows
 
 __global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ app, uint8_t *__restrict__ bits,
                                                   float *__restrict__ post, int32_t n, int32_t F, int32_t Fp) {
+    pdl_wait_then_release();
     __shared__ __align__(16) float tile[32][kFinStride];
     const int32_t j0 = blockIdx.x * kFinVars;
     const int32_t f0 = blockIdx.y * 32;
@@ -153,6 +156,7 @@ __global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ app,
 // 256 frames. A CTA covers 128 variables of one 32-frame word.
 __global__ void __launch_bounds__(256) k_finalize_words(const uint32_t *__restrict__ dec, uint8_t *__restrict__ bits,
                                                         int32_t n, int32_t F, int32_t G) {
+    pdl_wait_then_release();
     __shared__ __align__(16) uint32_t wt[kFinVars];
     const int32_t j0 = blockIdx.x * kFinVars;
     const int32_t g = blockIdx.y;
@@ -181,6 +185,7 @@ __global__ void __launch_bounds__(256) k_finalize_words(const uint32_t *__restri
 // Per-frame iteration count and syndrome status.
 __global__ void k_frame_results(const uint32_t *done, const uint32_t *status, const int32_t *stop_iter,
                                 const uint32_t *final_unsat, int32_t F, int32_t max_iter, int32_t *iters, uint8_t *ok) {
+    pdl_wait_then_release();
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= F) return;
     if (*status != 0u) {  // a device wait of the call gave up: no result
@@ -358,7 +363,10 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     a.ms_beta = o.rule_beta;
     a.ms_table = o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE ? c->d.ms_table : nullptr;
 
-    Launcher L{c, s, o.profile != 0};
+    // profile 2 times only the pass region, so that consecutive kernels keep
+    // their programmatic launch; other nonzero values time every launch too
+    const bool per_kernel = o.profile != 0 && o.profile != 2;
+    Launcher L{c, s, per_kernel};
     cudaError_t e;
     const int words = Fp / 32;
     e = L(LDPC_K_OTHER, 1, [&] {
@@ -371,8 +379,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     if (c->n > 0) {
         e = L(LDPC_K_INTERLEAVE, 1, [&] {
             dim3 grid((unsigned)((c->n + 127) / 128), (unsigned)(Fp / 32), 1);
-            k_interleave<<<grid, 256, 0, s>>>(llr, w.lamT, c->n, F, Fp);
-            return cudaGetLastError();
+            return launch_pdl(k_interleave, grid, dim3(256), 0, s, llr, w.lamT, c->n, F, Fp);
         });
         if (e != cudaSuccess) return e;
     }
@@ -410,7 +417,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
         PassArgs at = a;
         at.f_begin = ti * tile;
         at.f_count = tile;
-        Launcher Lh{c, hs[h], o.profile != 0};
+        Launcher Lh{c, hs[h], per_kernel};
         for (int32_t t = 0; t <= max_iter; ++t) {
             at.pass = t;
             at.syndrome = (t > 0 && at.early_exit) ? 1 : 0;
@@ -449,26 +456,23 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     if (c->m > 0 && c->E > 0) {
         e = L(LDPC_K_SYNDROME, 1, [&] {
             if (words % 4 == 0)
-                k_syndrome_words<4><<<dim3((unsigned)((c->m + 255) / 256), (unsigned)(words / 4)), 256, 0, s>>>(
-                    c->d.row_ptr, c->d.col_idx, c->m, w.dec, words, final_row);
-            else
-                k_syndrome_words<1><<<dim3((unsigned)((c->m + 255) / 256), (unsigned)words), 256, 0, s>>>(
-                    c->d.row_ptr, c->d.col_idx, c->m, w.dec, words, final_row);
-            return cudaGetLastError();
+                return launch_pdl(k_syndrome_words<4>, dim3((unsigned)((c->m + 255) / 256), (unsigned)(words / 4)),
+                                  dim3(256), 0, s, c->d.row_ptr, c->d.col_idx, c->m, w.dec, words, final_row);
+            return launch_pdl(k_syndrome_words<1>, dim3((unsigned)((c->m + 255) / 256), (unsigned)words), dim3(256),
+                              0, s, c->d.row_ptr, c->d.col_idx, c->m, w.dec, words, final_row);
         });
         if (e != cudaSuccess) return e;
     }
     e = L(LDPC_K_FINALIZE, c->n > 0 ? 2 : 1, [&] {
         if (c->n > 0) {
             dim3 grid((unsigned)((c->n + kFinVars - 1) / kFinVars), (unsigned)((F + 31) / 32), 1);
-            if (!a.early_exit && !post)
-                k_finalize_words<<<grid, 256, 0, s>>>(w.dec, bits, c->n, F, Fp / 32);
-            else
-                k_finalize<<<grid, 256, 0, s>>>(w.app, bits, post, c->n, F, Fp);
+            const cudaError_t ef = !a.early_exit && !post
+                                       ? launch_pdl(k_finalize_words, grid, dim3(256), 0, s, w.dec, bits, c->n, F, Fp / 32)
+                                       : launch_pdl(k_finalize, grid, dim3(256), 0, s, w.app, bits, post, c->n, F, Fp);
+            if (ef != cudaSuccess) return ef;
         }
-        k_frame_results<<<(F + 255) / 256, 256, 0, s>>>(w.done, a.status, w.stop_iter, final_row, F, max_iter, iters,
-                                                        ok);
-        return cudaGetLastError();
+        return launch_pdl(k_frame_results, dim3((unsigned)((F + 255) / 256)), dim3(256), 0, s, w.done, a.status,
+                          w.stop_iter, final_row, F, max_iter, iters, ok);
     });
     if (e != cudaSuccess) return e;
     if (r_out) {

@@ -32,6 +32,7 @@
 
 #include <atomic>
 
+#include "ldpc_launch.cuh"
 #include "ldpc_pass.h"
 
 namespace ldpc {
@@ -907,6 +908,7 @@ __device__ __forceinline__ void load_pairs(const M *p, float2 (&x)[V / 2]) {
 template <int D, int V, typename M, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_t *__restrict__ checks,
                                                         int32_t count) {
+    pdl_wait_then_release();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
@@ -1018,6 +1020,7 @@ struct BulkShape {
 
 template <int D, int V, typename M, int S, int MODE, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 *__restrict__ desc, int32_t count) {
+    pdl_wait_then_release();
     using P = PipeShape<D, V, M>;
     using B = BulkShape<D, V, M, S>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1154,6 +1157,7 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 
 template <int V, typename M, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_t *__restrict__ checks,
                                                         int32_t count) {
+    pdl_wait_then_release();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
@@ -1297,6 +1301,7 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
 
 template <int V, typename M>
 __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
+    pdl_wait_then_release();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
@@ -1407,19 +1412,19 @@ static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t 
                                       cudaStream_t s) {
     dim3 grid = pass_grid(a, count, V);
     if (bin == 0) {
-        k_check_reg<4, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+        return launch_pdl(k_check_reg<4, V, M, RULE>, grid, dim3(kThreads), 0, s, a, checks, count);
     } else if (bin == 1) {
-        k_check_reg<6, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+        return launch_pdl(k_check_reg<6, V, M, RULE>, grid, dim3(kThreads), 0, s, a, checks, count);
     } else if (bin == 2) {
-        k_check_reg<8, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+        return launch_pdl(k_check_reg<8, V, M, RULE>, grid, dim3(kThreads), 0, s, a, checks, count);
     } else if constexpr (V <= 2) {
         if (bin == 3) {
-            k_check_reg<16, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+            return launch_pdl(k_check_reg<16, V, M, RULE>, grid, dim3(kThreads), 0, s, a, checks, count);
         } else if (bin == 4) {
-            if constexpr (V == 1) k_check_reg<32, V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+            if constexpr (V == 1) return launch_pdl(k_check_reg<32, V, M, RULE>, grid, dim3(kThreads), 0, s, a, checks, count);
             else return cudaErrorInvalidValue;
         } else {
-            k_check_any<V, M, RULE><<<grid, kThreads, 0, s>>>(a, checks, count);
+            return launch_pdl(k_check_any<V, M, RULE>, grid, dim3(kThreads), 0, s, a, checks, count);
         }
     } else {
         return cudaErrorInvalidValue;
@@ -1452,7 +1457,7 @@ static cudaError_t launch_bulk_mode(const PassArgs &a, const int2 *desc, int32_t
     PassArgs b = a;
     b.grid_ctas = a.sm_count * nres;
     dim3 grid = pass_grid(b, count, V);
-    k_check_bulk<D, V, M, S, MODE, RULE><<<grid, kThreads, smem, s>>>(a, desc, count);
+    return launch_pdl(k_check_bulk<D, V, M, S, MODE, RULE>, grid, dim3(kThreads), smem, s, a, desc, count);
     return cudaGetLastError();
 }
 
@@ -1519,13 +1524,13 @@ cudaError_t launch_bit(const PassArgs &a, cudaStream_t s) {
     b.grid_ctas = a.sm_count * 8;
     dim3 grid = pass_grid(b, a.n, a.V);
     if (a.V == 8)
-        k_bit<8, M><<<grid, kThreads, 0, s>>>(a);
+        return launch_pdl(k_bit<8, M>, grid, dim3(kThreads), 0, s, a);
     else if (a.V == 4)
-        k_bit<4, M><<<grid, kThreads, 0, s>>>(a);
+        return launch_pdl(k_bit<4, M>, grid, dim3(kThreads), 0, s, a);
     else if (a.V == 2)
-        k_bit<2, M><<<grid, kThreads, 0, s>>>(a);
+        return launch_pdl(k_bit<2, M>, grid, dim3(kThreads), 0, s, a);
     else
-        k_bit<1, M><<<grid, kThreads, 0, s>>>(a);
+        return launch_pdl(k_bit<1, M>, grid, dim3(kThreads), 0, s, a);
     return cudaGetLastError();
 }
 

@@ -252,7 +252,7 @@ def _opts(early_exit, l_max, msg_dtype, profile, r_out_ptr, frames_per_lane=0, c
     if rule not in LDPC_RULE:
         raise ValueError(f"rule must be one of {sorted(LDPC_RULE)}")
     return ldpc_decode_opts_t(early_exit=1 if early_exit else 0, l_max=float(l_max), msg_dtype=LDPC_MSG[msg_dtype],
-                              profile=1 if profile else 0, r_out=r_out_ptr, frames_per_lane=int(frames_per_lane),
+                              profile=int(profile), r_out=r_out_ptr, frames_per_lane=int(frames_per_lane),
                               check_schedule=int(check_schedule), streams=int(streams), tile_frames=int(tile_frames),
                               check_rule=LDPC_RULE[rule], rule_alpha=float(rule_alpha), rule_beta=float(rule_beta))
 
