@@ -20,7 +20,7 @@ constexpr int32_t kMaxChunkFrames = 8192;
 // frames get lambda = 0.
 __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ llr, float *__restrict__ lamT,
                                                     int32_t n, int32_t F, int32_t Fp) {
-    pdl_wait_then_release();
+    pdl_wait();
     // tile of 32 frames x 128 variables: frame rows read as float4 when the
     // rows are 4-aligned, variable rows written 32 frames (128 bytes) at once
     __shared__ float tile[128][33];
@@ -73,7 +73,7 @@ __global__ void k_init_done(uint32_t *done, uint32_t *status, int32_t F, int32_t
 template <int W>
 __global__ void k_syndrome_words(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, int32_t m,
                                  const uint32_t *__restrict__ dec, int32_t G, uint32_t *__restrict__ row) {
-    pdl_wait_then_release();
+    pdl_wait();
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t w0 = blockIdx.y * W;
     uint32_t z[W];
@@ -111,7 +111,7 @@ constexpr int kFinStride = kFinVars + 4;  // float4-aligned rows
 
 __global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ app, uint8_t *__restrict__ bits,
                                                   float *__restrict__ post, int32_t n, int32_t F, int32_t Fp) {
-    pdl_wait_then_release();
+    pdl_wait();
     __shared__ __align__(16) float tile[32][kFinStride];
     const int32_t j0 = blockIdx.x * kFinVars;
     const int32_t f0 = blockIdx.y * 32;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ app,
 // 256 frames. A CTA covers 128 variables of one 32-frame word.
 __global__ void __launch_bounds__(256) k_finalize_words(const uint32_t *__restrict__ dec, uint8_t *__restrict__ bits,
                                                         int32_t n, int32_t F, int32_t G) {
-    pdl_wait_then_release();
+    pdl_wait();
     __shared__ __align__(16) uint32_t wt[kFinVars];
     const int32_t j0 = blockIdx.x * kFinVars;
     const int32_t g = blockIdx.y;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_finalize_words(const uint32_t *__restri
 // Per-frame iteration count and syndrome status.
 __global__ void k_frame_results(const uint32_t *done, const uint32_t *status, const int32_t *stop_iter,
                                 const uint32_t *final_unsat, int32_t F, int32_t max_iter, int32_t *iters, uint8_t *ok) {
-    pdl_wait_then_release();
+    pdl_wait();
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= F) return;
     if (*status != 0u) {  // a device wait of the call gave up: no result

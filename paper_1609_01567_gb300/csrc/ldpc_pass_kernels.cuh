@@ -908,7 +908,7 @@ __device__ __forceinline__ void load_pairs(const M *p, float2 (&x)[V / 2]) {
 template <int D, int V, typename M, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_t *__restrict__ checks,
                                                         int32_t count) {
-    pdl_wait_then_release();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
@@ -1020,7 +1020,7 @@ struct BulkShape {
 
 template <int D, int V, typename M, int S, int MODE, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 *__restrict__ desc, int32_t count) {
-    pdl_wait_then_release();
+    pdl_wait();
     using P = PipeShape<D, V, M>;
     using B = BulkShape<D, V, M, S>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1157,7 +1157,7 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 
 template <int V, typename M, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_t *__restrict__ checks,
                                                         int32_t count) {
-    pdl_wait_then_release();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
@@ -1301,7 +1301,7 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
 
 template <int V, typename M>
 __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
-    pdl_wait_then_release();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
