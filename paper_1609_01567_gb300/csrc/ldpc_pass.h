@@ -32,6 +32,8 @@ constexpr int kBinMaxDegree[kNumCheckBins] = {4, 6, 8, 16, 32, INT32_MAX};
 constexpr int kMaxRegisterDegree = 32;
 
 constexpr int kThreads = 256;  // threads per CTA of the pass kernels (8 warps)
+// checks of degree 17-32 in one code from which the any-degree kernel serves them
+constexpr int32_t kWideBinAnyKernel = 2048;
 
 // int8 messages: uniform step 20/127, saturating at +-127 steps (= 20).
 constexpr float kI8Step = 20.0f / 127.0f;

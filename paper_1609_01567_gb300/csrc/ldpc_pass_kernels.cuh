@@ -1486,6 +1486,23 @@ static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *
         default: return launch_bulk<16, 2, M, 2, RULE>(a, desc, count, s);
         }
     }
+    // Degrees 17-32 in a code with many such checks: the any-degree kernel
+    // (phi sums, constant state per frame, inputs read twice) at four frames
+    // per lane; the register kernel pads every check to 32 slots at one frame
+    // per lane (n = 64800 rate 5/6, 256 frames, 10 iterations: 5.28 -> 2.75
+    // ms). A few such checks (a short high-rate code) keep the register
+    // kernel, whose loads of one check are all in flight at once. The choice
+    // depends on the code only, never on the batch, so a frame's result does
+    // not depend on the frames decoded with it.
+    if (bin == 4 && count >= kWideBinAnyKernel) {
+        if (a.V >= 4 && a.f_count % 128 == 0 && a.f_begin % 128 == 0)
+            return launch_pdl(k_check_any<4, M, RULE>, pass_grid(a, count, 4), dim3(kThreads), 0, s, a, checks,
+                              count);
+        if (a.V >= 2)
+            return launch_pdl(k_check_any<2, M, RULE>, pass_grid(a, count, 2), dim3(kThreads), 0, s, a, checks,
+                              count);
+        return launch_pdl(k_check_any<1, M, RULE>, pass_grid(a, count, 1), dim3(kThreads), 0, s, a, checks, count);
+    }
     // Wider bins keep more messages per frame in registers: fewer frames per
     // lane there, to stay clear of spills (bins 3-5 run two frames per lane
     // at most, bin 4 and the unbounded bin one when V is odd).

@@ -289,6 +289,47 @@ def test_offsets_past_two_to_the_32(ldpc, oracle_mod):
     assert bad.size == 0, (bad, exempt)
 
 
+@pytest.fixture(scope="module")
+def n64800_r56():
+    code = I.mixed_code(7)  # n = 64800, rate 5/6, 10,800 checks of degree 17-18
+    llr = I.gaussian_llr(np.zeros((256, code.n), np.uint8), I.sigma2_from_ebn0(2.9, code.rate), seed=5656)
+    return code, llr
+
+
+def test_high_rate_checks_lock_step(ldpc, oracle_mod, n64800_r56):
+    """Checks of degree 17-18 in a code with many of them run in the
+    any-degree kernel: three passes at 256 frames, sampled frames against the
+    oracle from the GPU's own messages."""
+    code, llr = n64800_r56
+    h = ldpc.code_from_inputs(code)
+    info = ldpc.ldpc_code_info(h)
+    assert info["check_bin_count"][4] == code.m and code.m >= 2048
+    sample = np.array([0, 5, 128, 255])
+    prev_r = None
+    for t in range(3):
+        got = gpu_decode(ldpc, h, llr, t, early_exit=False, want_r=True)
+        ref = oracle_mod.sp_pass(code, llr[sample].astype(np.float64), prev_r, n_threads=8)
+        assert close(got["post"][sample], ref["post"]).all(), (t, np.abs(got["post"][sample] - ref["post"]).max())
+        assert close(got["r"][sample], ref["r"], atol=1e-4).all(), (t, np.abs(got["r"][sample] - ref["r"]).max())
+        prev_r = got["r"][sample].astype(np.float64)
+
+
+def test_high_rate_results_do_not_depend_on_layout_or_batch(ldpc, n64800_r56):
+    """The any-degree kernel's results are the same at four, two and one
+    frames per lane, on one or two streams, and for a frame decoded alone or
+    in a batch of 256."""
+    code, llr = n64800_r56
+    h = ldpc.code_from_inputs(code)
+    base = gpu_decode(ldpc, h, llr, 8, early_exit=False)
+    for kw in (dict(frames_per_lane=2), dict(frames_per_lane=1, streams=1), dict(streams=1)):
+        other = gpu_decode(ldpc, h, llr, 8, early_exit=False, **kw)
+        for k in ("bits", "iters", "ok", "post"):
+            np.testing.assert_array_equal(other[k], base[k], err_msg=f"{kw} {k}")
+    part = gpu_decode(ldpc, h, llr[:37], 8, early_exit=False)
+    for k in ("bits", "iters", "ok", "post"):
+        np.testing.assert_array_equal(part[k], base[k][:37], err_msg=f"37 frames {k}")
+
+
 def test_n64800_lock_step_two_passes(ldpc, oracle_mod, n64800):
     code, cw, llr = n64800
     h = ldpc.code_from_inputs(code)
