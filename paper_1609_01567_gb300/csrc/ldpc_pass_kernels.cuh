@@ -1295,6 +1295,183 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
     }
 }
 
+// Checks of degree above 32: one CTA per (check, group of 32 V frames), its
+// eight warps splitting the check's inputs (warp w takes inputs w, w + 8,
+// ...). Each warp forms partial results over its inputs -- the sum of
+// phi(|q|) as an error-free pair (sum-product) or the two smallest |q| and
+// the position of the smallest (min-sum), the parity of the inputs' signs and
+// the previous decision's syndrome -- the CTA merges the eight partials in
+// warp order through shared memory (every warp the same merge, so the same
+// totals), and each warp writes the outputs of its inputs. A lone check of
+// degree 96 then has eight warps per frame group working on it instead of
+// one walking its 96 inputs twice.
+template <int V, typename M, int RULE>
+__global__ void __launch_bounds__(kThreads) k_check_wide(PassArgs a, const int32_t *__restrict__ checks,
+                                                         int32_t count) {
+    pdl_wait();
+    constexpr int W = kThreads / 32;
+    __shared__ float s_hi[W][32 * V], s_lo[W][32 * V];
+    __shared__ int s_idx[W][32 * V];
+    __shared__ uint32_t s_par[W][32 * V], s_z[W][32 * V];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
+    const int f0 = g * 32 * V + lane * V;
+    const size_t Fp = (size_t)a.Fp;
+    M *r = reinterpret_cast<M *>(a.r);
+    const bool first = a.pass == 0;
+    const float *qsrc = first ? a.lamT : a.app;
+
+    bool live[V];
+    bool any_live = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        live[v] = !frame_bit(a.done, f0 + v);
+        any_live |= live[v];
+    }
+    if (!__syncthreads_or(any_live)) return;  // the whole CTA leaves together
+    bool unsat[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) unsat[v] = false;
+
+    for (int w = blockIdx.x; w < count; w += gridDim.x) {
+        const int i = checks[w];
+        const int b = a.row_ptr[i];
+        const int d = a.row_ptr[i + 1] - b;
+        float alpha = a.ms_alpha, beta = a.ms_beta;
+        if (RULE == 1 && a.ms_table) {
+            const float2 t = __ldg(a.ms_table + d);
+            alpha = t.x;
+            beta = t.y;
+        }
+        float hi[V], lo[V];  // sum-product: compensated partial sum; min-sum: two smallest |q|
+        int idx[V];
+        uint32_t par[V], z[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            hi[v] = lo[v] = RULE == 1 ? a.l_max : 0.0f;
+            idx[v] = -1;
+            par[v] = z[v] = 0u;
+        }
+        for (int k = warp; k < d; k += W) {
+            const int slot = b + k;
+            float av[V], qv[V];
+            load_v<V, float>(qsrc + (size_t)a.col_idx[slot] * Fp + f0, av);
+            if (first) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) qv[v] = av[v];
+            } else {
+                float rv[V];
+                load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    qv[v] = av[v] - rv[v];
+                    z[v] ^= av[v] > 0.0f ? 1u : 0u;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if constexpr (RULE == 1) {
+                    const float x = fminf(fabsf(qv[v]), a.l_max);
+                    if (x < hi[v]) {
+                        lo[v] = hi[v];
+                        hi[v] = x;
+                        idx[v] = k;
+                    } else if (x < lo[v]) {
+                        lo[v] = x;
+                    }
+                } else {
+                    float err;
+                    hi[v] = two_sum(hi[v], phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax), err);
+                    lo[v] += err;
+                }
+                par[v] ^= qv[v] > 0.0f ? 1u : 0u;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            s_hi[warp][lane * V + v] = hi[v];
+            s_lo[warp][lane * V + v] = lo[v];
+            s_idx[warp][lane * V + v] = idx[v];
+            s_par[warp][lane * V + v] = par[v];
+            s_z[warp][lane * V + v] = z[v];
+        }
+        __syncthreads();
+        // merge the partials in warp order
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int c = lane * V + v;
+            float H = s_hi[0][c], L = s_lo[0][c];
+            int I = s_idx[0][c];
+            uint32_t P = s_par[0][c], Z = s_z[0][c];
+            for (int u = 1; u < W; ++u) {
+                const float h2 = s_hi[u][c], l2 = s_lo[u][c];
+                if constexpr (RULE == 1) {
+                    // two smallest of both pairs; the position of the smallest
+                    // matters only when it is unique, where this choice is exact
+                    if (h2 < H) {
+                        L = fminf(H, l2);
+                        H = h2;
+                        I = s_idx[u][c];
+                    } else {
+                        L = fminf(L, h2);
+                    }
+                } else {
+                    float err;
+                    const float s2 = two_sum(H, h2, err);
+                    L = (L + l2) + err;
+                    H = s2;
+                }
+                P ^= s_par[u][c];
+                Z ^= s_z[u][c];
+            }
+            hi[v] = H;
+            lo[v] = L;
+            idx[v] = I;
+            par[v] = P;
+            unsat[v] |= Z != 0u;
+        }
+        __syncthreads();  // the partials are read before the next check overwrites them
+        for (int k = warp; k < d; k += W) {
+            const int slot = b + k;
+            float av[V], qv[V];
+            load_v<V, float>(qsrc + (size_t)a.col_idx[slot] * Fp + f0, av);
+            if (first) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) qv[v] = av[v];
+            } else {
+                float rv[V];
+                load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
+#pragma unroll
+                for (int v = 0; v < V; ++v) qv[v] = av[v] - rv[v];
+            }
+            float out[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                float mm;
+                if constexpr (RULE == 1) {
+                    const float m = idx[v] == k ? lo[v] : hi[v];
+                    mm = fminf(fmaxf(fmaf(alpha, m, -beta), 0.0f), a.l_max);
+                } else {
+                    const float own = phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax);
+                    float err;
+                    const float s2 = two_sum(hi[v], -own, err);
+                    mm = phi_hat(s2 + (err + lo[v]), a.l_max, a.phi_lmax);
+                }
+                const uint32_t others = par[v] ^ (qv[v] > 0.0f ? 1u : 0u);
+                out[v] = others ? mm : -mm;
+            }
+            store_v<V, M>(r + (size_t)slot * Fp + f0, out);
+        }
+    }
+    if (a.syndrome && warp == 0) {
+        bool bits[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) bits[v] = unsat[v] && live[v];
+        or_frame_bits<V>(a.unsat + (size_t)(a.pass - 1) * (a.Fp / 32), g, lane, bits);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Bit-node kernel: APP_j = lambda_j + sum_{i in M_j} r_ij
 // ---------------------------------------------------------------------------
@@ -1468,6 +1645,17 @@ static cudaError_t launch_bulk(const PassArgs &a, const int2 *desc, int32_t coun
     return launch_bulk_mode<D, V, M, S, 1, RULE>(a, desc, count, s);
 }
 
+// One CTA per check and group of 32 V frames, as many checks at once as the
+// CTA budget of a pass allows.
+template <int V, typename M, int RULE>
+static cudaError_t launch_wide(const PassArgs &a, const int32_t *checks, int32_t count, cudaStream_t s) {
+    const int groups = a.f_count / (32 * V);
+    int64_t cap = a.grid_ctas / groups;
+    if (cap < 1) cap = 1;
+    const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(count, cap)), (unsigned)groups, 1);
+    return launch_pdl(k_check_wide<V, M, RULE>, grid, dim3(kThreads), 0, s, a, checks, count);
+}
+
 template <typename M, int RULE>
 static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *checks, const int2 *desc,
                                      int32_t count, cudaStream_t s) {
@@ -1502,6 +1690,12 @@ static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *
             return launch_pdl(k_check_any<2, M, RULE>, pass_grid(a, count, 2), dim3(kThreads), 0, s, a, checks,
                               count);
         return launch_pdl(k_check_any<1, M, RULE>, pass_grid(a, count, 1), dim3(kThreads), 0, s, a, checks, count);
+    }
+    // Degrees above 32: a CTA per check and frame group (k_check_wide).
+    if (bin == kNumCheckBins - 1) {
+        if (a.V >= 4 && a.f_count % 128 == 0 && a.f_begin % 128 == 0) return launch_wide<4, M, RULE>(a, checks, count, s);
+        if (a.V >= 2) return launch_wide<2, M, RULE>(a, checks, count, s);
+        return launch_wide<1, M, RULE>(a, checks, count, s);
     }
     // Wider bins keep more messages per frame in registers: fewer frames per
     // lane there, to stay clear of spills (bins 3-5 run two frames per lane

@@ -330,6 +330,33 @@ def test_high_rate_results_do_not_depend_on_layout_or_batch(ldpc, n64800_r56):
         np.testing.assert_array_equal(part[k], base[k][:37], err_msg=f"37 frames {k}")
 
 
+@pytest.mark.parametrize("rule", ["sum_product", "min_sum"])
+def test_wide_check_lock_step_and_layouts(ldpc, oracle_mod, rule):
+    """A code with one check of degree 96 (and a variable of degree 64): the
+    wide check runs a CTA per frame group, its warps splitting the inputs.
+    Four passes at 256 frames on sampled frames against the oracle, and the
+    same results at every frames-per-lane width and on one or two streams."""
+    code = I.mixed_code(4)
+    h = ldpc.code_from_inputs(code)
+    assert ldpc.ldpc_code_info(h)["check_bin_count"][5] == 1
+    llr = I.gaussian_llr(np.zeros((256, code.n), np.uint8), I.sigma2_from_ebn0(2.4, code.rate), seed=9696)
+    kw = dict(rule=rule, rule_alpha=0.8, rule_beta=0.1) if rule == "min_sum" else {}
+    okw = dict(rule="min_sum", alpha=0.8, beta=0.1) if rule == "min_sum" else {}
+    sample = np.array([0, 63, 64, 200, 255])
+    prev_r = None
+    for t in range(4):
+        got = gpu_decode(ldpc, h, llr, t, early_exit=False, want_r=True, **kw)
+        ref = oracle_mod.sp_pass(code, llr[sample].astype(np.float64), prev_r, n_threads=8, **okw)
+        assert close(got["post"][sample], ref["post"]).all(), (t, np.abs(got["post"][sample] - ref["post"]).max())
+        assert close(got["r"][sample], ref["r"], atol=1e-4).all(), (t, np.abs(got["r"][sample] - ref["r"]).max())
+        prev_r = got["r"][sample].astype(np.float64)
+    base = gpu_decode(ldpc, h, llr, 12, **kw)
+    for lay in (dict(frames_per_lane=2), dict(frames_per_lane=1), dict(streams=1), dict(frames_per_lane=8)):
+        other = gpu_decode(ldpc, h, llr, 12, **kw, **lay)
+        for k in ("bits", "iters", "ok", "post"):
+            np.testing.assert_array_equal(other[k], base[k], err_msg=f"{lay} {k}")
+
+
 def test_n64800_lock_step_two_passes(ldpc, oracle_mod, n64800):
     code, cw, llr = n64800
     h = ldpc.code_from_inputs(code)
