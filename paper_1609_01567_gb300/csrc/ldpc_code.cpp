@@ -186,7 +186,10 @@ extern "C" int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t
             int hi = kBinMaxDegree[b];
             for (int32_t i = 0; i < m; ++i) {
                 int d = c->row_ptr[i + 1] - c->row_ptr[i];
-                if (d >= lo && d <= hi) c->bin_checks.push_back(i);
+                if (d >= lo && d <= hi) {
+                    c->bin_checks.push_back(i);
+                    c->bin_max_degree[b] = std::max(c->bin_max_degree[b], d);
+                }
             }
         }
         c->bin_off[kNumCheckBins] = (int32_t)c->bin_checks.size();

@@ -425,6 +425,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
             for (int b = 0; b < kNumCheckBins; ++b) {
                 int32_t count = c->bin_off[b + 1] - c->bin_off[b];
                 if (count == 0) continue;
+                at.bin_degree = c->bin_max_degree[b];
                 e = Lh(LDPC_K_CHECK, 1, [&] {
                     return launch_check_bin<M>(at, b, c->d.bin_checks + c->bin_off[b], c->d.bin_desc + c->bin_off[b],
                                                count, hs[h]);

@@ -98,6 +98,7 @@ struct ldpc_code {
     std::vector<int32_t> bin_checks;
     std::vector<int2> bin_desc;
     int32_t bin_off[ldpc::kNumCheckBins + 1] = {0};
+    int32_t bin_max_degree[ldpc::kNumCheckBins] = {0};  // largest check degree present in each bin
     // device side
     int device = -1;
     int sm_count = 0;

@@ -107,6 +107,7 @@ struct PassArgs {
     int32_t check_schedule;  // 0 auto, 1 direct loads, 2 shared-memory pipeline
     int32_t f_begin;     // first frame of the range this launch covers (a multiple of 32 V)
     int32_t f_count;     // frames in that range (a multiple of 32 V)
+    int32_t bin_degree;  // largest check degree present in the bin being launched
     int32_t check_rule;  // 0 sum-product, 1 min-sum family, 2 sum-product with tabulated phi,
                          // 3 min-sum with (alpha, beta) per check degree from ms_table
     const float2 *phi_table;  // device chords of the tabulated phi (rule 2)

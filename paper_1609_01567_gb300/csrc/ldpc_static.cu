@@ -207,6 +207,7 @@ cudaError_t run_static(ldpc_code *c, unsigned char *scratch, const float *llr, i
         for (int b = 0; b < kNumCheckBins; ++b) {
             int32_t count = c->bin_off[b + 1] - c->bin_off[b];
             if (count == 0) continue;
+            a.bin_degree = c->bin_max_degree[b];
             e = launch_check_bin<M>(a, b, c->d.bin_checks + c->bin_off[b], c->d.bin_desc + c->bin_off[b], count, s);
             if (e != cudaSuccess) return e;
         }

@@ -357,6 +357,24 @@ def test_wide_check_lock_step_and_layouts(ldpc, oracle_mod, rule):
             np.testing.assert_array_equal(other[k], base[k], err_msg=f"{lay} {k}")
 
 
+def test_checks_of_degree_9_to_12_in_twelve_slots(ldpc, oracle_mod):
+    """A bin of checks of degree 9-16 whose largest degree is 12 runs in 12
+    slots instead of 16; padding slots are exact no-ops, so the results equal
+    the 16-slot kernel's (check_schedule 1) bit for bit, and the oracle's."""
+    code = I.mixed_code(1)  # n = 1152, rate 3/4, checks of degree 11-12
+    h = ldpc.code_from_inputs(code)
+    assert ldpc.ldpc_code_info(h)["check_bin_count"][3] == code.m
+    llr = I.gaussian_llr(np.zeros((256, code.n), np.uint8), I.sigma2_from_ebn0(3.3, code.rate), seed=1212)
+    base = gpu_decode(ldpc, h, llr, 20)
+    slots16 = gpu_decode(ldpc, h, llr, 20, check_schedule=1)
+    for k in ("bits", "iters", "ok", "post"):
+        np.testing.assert_array_equal(slots16[k], base[k], err_msg=k)
+    ref = oracle_mod.decode(code, llr.astype(np.float64), 20, n_threads=8)
+    bad, exempt = compare_decodes(base, ref)
+    short = ref["iters"] <= 12
+    assert not np.isin(bad, np.flatnonzero(short)).any(), bad
+
+
 def test_n64800_lock_step_two_passes(ldpc, oracle_mod, n64800):
     code, cw, llr = n64800
     h = ldpc.code_from_inputs(code)
