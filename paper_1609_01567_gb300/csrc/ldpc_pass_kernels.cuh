@@ -1582,8 +1582,8 @@ inline dim3 pass_grid(const PassArgs &a, int64_t nodes, int V) {
 }
 
 // Only the (bin, frames-per-lane) pairs launch_check_rule selects are
-// instantiated: V = 4 for bins 0-2 (degree <= 8), V = 2 for bins 0-3 and the
-// unbounded bin, V = 1 for every bin.
+// instantiated: V = 4 for bins 0-2 (degree <= 8), V = 2 for bins 0-3, V = 1
+// for bins 0-4 (the unbounded bin has its own kernel, k_check_wide).
 template <int V, typename M, int RULE>
 static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t *checks, int32_t count,
                                       cudaStream_t s) {
@@ -1601,7 +1601,7 @@ static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t 
             if constexpr (V == 1) return launch_pdl(k_check_reg<32, V, M, RULE>, grid, dim3(kThreads), 0, s, a, checks, count);
             else return cudaErrorInvalidValue;
         } else {
-            return launch_pdl(k_check_any<V, M, RULE>, grid, dim3(kThreads), 0, s, a, checks, count);
+            return cudaErrorInvalidValue;
         }
     } else {
         return cudaErrorInvalidValue;
@@ -1701,9 +1701,10 @@ static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *
         if (a.V >= 2) return launch_wide<2, M, RULE>(a, checks, count, s);
         return launch_wide<1, M, RULE>(a, checks, count, s);
     }
-    // Wider bins keep more messages per frame in registers: fewer frames per
-    // lane there, to stay clear of spills (bins 3-5 run two frames per lane
-    // at most, bin 4 and the unbounded bin one when V is odd).
+    // The register kernel for the other layouts. Wider bins keep more
+    // messages per frame in registers: fewer frames per lane there, to stay
+    // clear of spills (bin 3 runs two frames per lane at most, the 17-32 bin
+    // of a code with few such checks one).
     if (a.V == 4 && bin < 3) return launch_check_bin_v<4, M, RULE>(a, bin, checks, count, s);
     if (a.V >= 2 && bin != 4) return launch_check_bin_v<2, M, RULE>(a, bin, checks, count, s);
     return launch_check_bin_v<1, M, RULE>(a, bin, checks, count, s);
