@@ -56,9 +56,11 @@ __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ ll
 }
 
 // done bits: padding frames (f >= F) start as stopped.
-__global__ void k_init_done(uint32_t *done, uint32_t *status, int32_t F, int32_t Fp) {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_init_done(uint32_t *done, uint32_t *status, uint32_t *unsat, int64_t n_unsat, int32_t F,
+                            int32_t Fp) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w == 0) *status = 0u;
+    for (int64_t i = w; i < n_unsat; i += (int64_t)gridDim.x * blockDim.x) unsat[i] = 0u;  // syndrome rows
     if (w >= Fp / 32) return;
     uint32_t bits = 0;
     for (int b = 0; b < 32; ++b)
@@ -102,6 +104,31 @@ __global__ void k_syndrome_words(const int32_t *__restrict__ row_ptr, const int3
     }
 }
 
+// Per-frame iteration count and syndrome status, written by the finalize
+// kernels' first CTA column (or by k_frame_results for a code without
+// variables).
+struct FrameResults {
+    const uint32_t *done;
+    const uint32_t *status;
+    const int32_t *stop_iter;
+    const uint32_t *final_unsat;
+    int32_t F, max_iter;
+    int32_t *iters;
+    uint8_t *ok;
+};
+
+__device__ __forceinline__ void write_frame_result(const FrameResults &fr, int32_t f) {
+    if (f >= fr.F) return;
+    if (*fr.status != 0u) {  // a device wait of the call gave up: no result
+        fr.iters[f] = -1;
+        fr.ok[f] = 0;
+        return;
+    }
+    const bool stopped = frame_bit(fr.done, f);
+    fr.iters[f] = stopped ? fr.stop_iter[f] : fr.max_iter;
+    fr.ok[f] = stopped ? 1 : (frame_bit(fr.final_unsat, f) ? 0 : 1);
+}
+
 // APP [n][Fp] -> bits [F][n] (1 iff APP > 0, Algorithm 5) and optional post
 // [F][n]. A CTA transposes a tile of 128 variables x 32 frames through shared
 // memory and writes each frame's 128 decisions as 32 four-byte words (128
@@ -110,8 +137,10 @@ constexpr int kFinVars = 128;
 constexpr int kFinStride = kFinVars + 4;  // float4-aligned rows
 
 __global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ app, uint8_t *__restrict__ bits,
-                                                  float *__restrict__ post, int32_t n, int32_t F, int32_t Fp) {
+                                                  float *__restrict__ post, int32_t n, int32_t F, int32_t Fp,
+                                                  FrameResults fr) {
     pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x < 32) write_frame_result(fr, (int32_t)blockIdx.y * 32 + threadIdx.x);
     __shared__ __align__(16) float tile[32][kFinStride];
     const int32_t j0 = blockIdx.x * kFinVars;
     const int32_t f0 = blockIdx.y * 32;
@@ -155,8 +184,9 @@ __global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ app,
 // early): 2 MB of words read instead of the 66 MB APP array at n = 64800 and
 // 256 frames. A CTA covers 128 variables of one 32-frame word.
 __global__ void __launch_bounds__(256) k_finalize_words(const uint32_t *__restrict__ dec, uint8_t *__restrict__ bits,
-                                                        int32_t n, int32_t F, int32_t G) {
+                                                        int32_t n, int32_t F, int32_t G, FrameResults fr) {
     pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x < 32) write_frame_result(fr, (int32_t)blockIdx.y * 32 + threadIdx.x);
     __shared__ __align__(16) uint32_t wt[kFinVars];
     const int32_t j0 = blockIdx.x * kFinVars;
     const int32_t g = blockIdx.y;
@@ -182,20 +212,9 @@ __global__ void __launch_bounds__(256) k_finalize_words(const uint32_t *__restri
     }
 }
 
-// Per-frame iteration count and syndrome status.
-__global__ void k_frame_results(const uint32_t *done, const uint32_t *status, const int32_t *stop_iter,
-                                const uint32_t *final_unsat, int32_t F, int32_t max_iter, int32_t *iters, uint8_t *ok) {
+__global__ void k_frame_results(FrameResults fr) {
     pdl_wait();
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= F) return;
-    if (*status != 0u) {  // a device wait of the call gave up: no result
-        iters[f] = -1;
-        ok[f] = 0;
-        return;
-    }
-    bool stopped = frame_bit(done, f);
-    iters[f] = stopped ? stop_iter[f] : max_iter;
-    ok[f] = stopped ? 1 : (frame_bit(final_unsat, f) ? 0 : 1);
+    write_frame_result(fr, (int32_t)(blockIdx.x * blockDim.x + threadIdx.x));
 }
 
 // ---------------------------------------------------------------------------
@@ -370,9 +389,9 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     cudaError_t e;
     const int words = Fp / 32;
     e = L(LDPC_K_OTHER, 1, [&] {
-        cudaError_t ee = cudaMemsetAsync(w.unsat, 0, sizeof(uint32_t) * (size_t)(max_iter + 1) * words, s);
-        if (ee != cudaSuccess) return ee;
-        k_init_done<<<(words + 127) / 128, 128, 0, s>>>(w.done, a.status, F, Fp);
+        const int64_t n_unsat = (int64_t)(max_iter + 1) * words;
+        const int64_t blocks = std::min<int64_t>(std::max<int64_t>(words, n_unsat) / 128 + 1, 1024);
+        k_init_done<<<(unsigned)blocks, 128, 0, s>>>(w.done, a.status, w.unsat, n_unsat, F, Fp);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -464,16 +483,15 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
         });
         if (e != cudaSuccess) return e;
     }
-    e = L(LDPC_K_FINALIZE, c->n > 0 ? 2 : 1, [&] {
+    e = L(LDPC_K_FINALIZE, 1, [&] {
+        const FrameResults fr{w.done, a.status, w.stop_iter, final_row, F, max_iter, iters, ok};
         if (c->n > 0) {
             dim3 grid((unsigned)((c->n + kFinVars - 1) / kFinVars), (unsigned)((F + 31) / 32), 1);
-            const cudaError_t ef = !a.early_exit && !post
-                                       ? launch_pdl(k_finalize_words, grid, dim3(256), 0, s, w.dec, bits, c->n, F, Fp / 32)
-                                       : launch_pdl(k_finalize, grid, dim3(256), 0, s, w.app, bits, post, c->n, F, Fp);
-            if (ef != cudaSuccess) return ef;
+            return !a.early_exit && !post
+                       ? launch_pdl(k_finalize_words, grid, dim3(256), 0, s, w.dec, bits, c->n, F, Fp / 32, fr)
+                       : launch_pdl(k_finalize, grid, dim3(256), 0, s, w.app, bits, post, c->n, F, Fp, fr);
         }
-        return launch_pdl(k_frame_results, dim3((unsigned)((F + 255) / 256)), dim3(256), 0, s, w.done, a.status,
-                          w.stop_iter, final_row, F, max_iter, iters, ok);
+        return launch_pdl(k_frame_results, dim3((unsigned)((F + 255) / 256)), dim3(256), 0, s, fr);
     });
     if (e != cudaSuccess) return e;
     if (r_out) {
