@@ -296,19 +296,23 @@ def n64800_r56():
     return code, llr
 
 
-def test_high_rate_checks_lock_step(ldpc, oracle_mod, n64800_r56):
+@pytest.mark.parametrize("rule", ["sum_product", "min_sum"])
+def test_high_rate_checks_lock_step(ldpc, oracle_mod, n64800_r56, rule):
     """Checks of degree 17-18 in a code with many of them run in the
     any-degree kernel: three passes at 256 frames, sampled frames against the
-    oracle from the GPU's own messages."""
+    oracle from the GPU's own messages (sum-product and offset/normalised
+    min-sum)."""
     code, llr = n64800_r56
     h = ldpc.code_from_inputs(code)
     info = ldpc.ldpc_code_info(h)
     assert info["check_bin_count"][4] == code.m and code.m >= 2048
+    kw = dict(rule=rule, rule_alpha=0.85, rule_beta=0.1) if rule == "min_sum" else {}
+    okw = dict(rule="min_sum", alpha=0.85, beta=0.1) if rule == "min_sum" else {}
     sample = np.array([0, 5, 128, 255])
     prev_r = None
     for t in range(3):
-        got = gpu_decode(ldpc, h, llr, t, early_exit=False, want_r=True)
-        ref = oracle_mod.sp_pass(code, llr[sample].astype(np.float64), prev_r, n_threads=8)
+        got = gpu_decode(ldpc, h, llr, t, early_exit=False, want_r=True, **kw)
+        ref = oracle_mod.sp_pass(code, llr[sample].astype(np.float64), prev_r, n_threads=8, **okw)
         assert close(got["post"][sample], ref["post"]).all(), (t, np.abs(got["post"][sample] - ref["post"]).max())
         assert close(got["r"][sample], ref["r"], atol=1e-4).all(), (t, np.abs(got["r"][sample] - ref["r"]).max())
         prev_r = got["r"][sample].astype(np.float64)
