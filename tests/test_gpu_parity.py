@@ -379,6 +379,26 @@ def test_checks_of_degree_9_to_12_in_twelve_slots(ldpc, oracle_mod):
     assert not np.isin(bad, np.flatnonzero(short)).any(), bad
 
 
+@pytest.mark.parametrize("msg", ["f16", "bf16", "i8"])
+def test_new_check_paths_in_every_message_format(ldpc, msg):
+    """The 12-slot, high-rate (any-degree) and wide-check paths with 16-bit
+    and int8 messages: the same results at one frame per lane with direct
+    loads on one stream as in the default layout, and the same codeword as
+    the FP32 decode on nearly every frame that FP32 corrects."""
+    for idx, ebn0 in ((1, 3.6), (4, 2.8), (7, 3.1)):  # n = 1152 r 3/4, n = 8192 with a degree-96 check, n = 64800 r 5/6
+        code = I.mixed_code(idx)
+        h = ldpc.code_from_inputs(code)
+        llr = I.gaussian_llr(np.zeros((256, code.n), np.uint8), I.sigma2_from_ebn0(ebn0, code.rate), seed=77 + idx)
+        base = gpu_decode(ldpc, h, llr, 15, msg_dtype=msg)
+        other = gpu_decode(ldpc, h, llr, 15, msg_dtype=msg, frames_per_lane=1, check_schedule=1, streams=1)
+        for k in ("bits", "iters", "ok", "post"):
+            np.testing.assert_array_equal(other[k], base[k], err_msg=f"{code.name} {msg} {k}")
+        f32 = gpu_decode(ldpc, h, llr, 15)
+        conv = f32["ok"] == 1  # frames the FP32 decode corrects; the others part ways chaotically
+        agree = ((base["bits"] == f32["bits"]).all(axis=1) & (base["ok"] == 1))[conv].mean()
+        assert conv.mean() > 0.3 and agree >= 0.9, (code.name, msg, conv.mean(), agree)
+
+
 def test_n64800_lock_step_two_passes(ldpc, oracle_mod, n64800):
     code, cw, llr = n64800
     h = ldpc.code_from_inputs(code)
