@@ -165,11 +165,15 @@ typedef struct {
     int32_t frames_per_lane; /* tuning: frames each GPU lane carries in the
                            bit-node kernel (1, 2, 4 or 8); 0 picks by batch
                            size                                              */
-    int32_t check_schedule;  /* tuning: check-node kernel schedule; 0 = auto,
-                           1 = inputs loaded straight from global memory,
-                           2 = rows staged through a shared-memory ring by
-                           bulk copies (when the batch allows: degree <= 16,
-                           frame groups of 64 or 128)                        */
+    int32_t check_schedule;  /* tuning: check-node kernel schedule for checks
+                           of degree <= 16; 0 = auto, 1 = inputs loaded
+                           straight from global memory, 2 = rows staged
+                           through a shared-memory ring by bulk copies (when
+                           the batch allows: frame groups of 64 or 128).
+                           Wider checks have kernels chosen by the code: the
+                           register kernel, the any-degree kernel (a code
+                           with >= 2048 checks of degree 17-32) or one CTA
+                           per check (degree > 32)                           */
     int32_t streams;    /* tuning: 1 = all passes on `stream`; 2 = the two
                            halves of the batch on two library streams, half a
                            pass apart, so that the check pass of one half
