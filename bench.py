@@ -50,6 +50,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=50)
     p.add_argument("--early-exit-steps", type=int, default=10)
+    p.add_argument("--by-msg-steps", type=int, default=200, help="steps per message format in by_msg (0 = skip)")
     p.add_argument("--streams", type=int, default=0, help="decode tuning: 1 or 2 streams (0 = library choice)")
     p.add_argument("--frames-per-lane", type=int, default=0, help="decode tuning (0 = library choice)")
     return p.parse_args()
@@ -251,71 +252,111 @@ def run_ours(args):
     sigma2 = inputs.sigma2_from_ebn0(args.ebn0, code.rate)
     n_buf = 4
     llrs = [ldpc.ldpc_gen_awgn(17 + b, rank * F, F, code.n, sigma2, cw, device=local) for b in range(n_buf)]
-    out = None
     kw = dict(early_exit=False, msg_dtype=args.msg, streams=args.streams, frames_per_lane=args.frames_per_lane)
-    for i in range(args.warmup):
-        out = ldpc.ldpc_decode(h, llrs[i % n_buf], args.max_iter, out=out, want_post=False, **kw)
+    stream = torch.cuda.current_stream()
+    n = code.n
+    E = code.n_edges
+    passes = args.max_iter + 1
+    peak, peak_src = measured_hbm_peak()
+
+    def timed_steps(msg, steps, warmup, clocks=None):
+        """K decode steps of the workload in message format msg, device-timed on
+        the launching stream; the library times the pass region (profile=2)."""
+        kwm = dict(kw, msg_dtype=msg)
+        out = None
+        for i in range(warmup):
+            out = ldpc.ldpc_decode(h, llrs[i % n_buf], args.max_iter, out=out, want_post=False, **kwm)
+        torch.cuda.synchronize()
+        ldpc.ldpc_prof_read(h, reset=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        events = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        events[0].record(stream)
+        # profile=2: CUDA events on the launching stream around the region of
+        # the flooding passes only; per-kernel events would break the
+        # programmatic launches between consecutive kernels
+        for i in range(steps):
+            out = ldpc.ldpc_decode(h, llrs[i % n_buf], args.max_iter, out=out, want_post=False, profile=2, **kwm)
+            events[i + 1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        total_ms = events[0].elapsed_time(events[-1])
+        step_ms = [events[i].elapsed_time(events[i + 1]) for i in range(steps)]
+        prof = ldpc.ldpc_prof_read(h, reset=True)
+        if dist:
+            t = torch.tensor([total_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return total_ms / steps, step_ms, prof, clk, out
+
+    def pass_roofline(msg, region_ms_step):
+        """HBM roofline of the flooding pass (check-node + bit-node kernels;
+        with two streams they overlap, so the unit timed is the pass region)."""
+        s = {"f32": 4, "f16": 2, "bf16": 2, "i8": 1}[msg]
+        pass_ms = region_ms_step / passes
+        # the scope table's model: 3 s E + 12.125 n bytes per frame and pass
+        model = (3 * s * E + 12.125 * n) * F
+        # per kernel: check 2 s E + 4 n (first pass s E + 4 n: no old messages),
+        # bit s E + 8 n; decision bits not counted
+        check_step = ((passes - 1) * (2 * s * E + 4 * n) + (s * E + 4 * n)) * F
+        bit_step = passes * (s * E + 8 * n) * F
+        refined = (check_step + bit_step) / passes
+        traffic, traffic_src = recorded_traffic(msg)
+        achieved = model / (pass_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": "flooding pass (check-node + bit-node kernels)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": peak_src, "traffic_source": traffic_src,
+                "algorithmic_bytes_per_launch": model,
+                "model": "3 s E + 12.125 n bytes per frame and pass (s = bytes per stored message)",
+                "refined": {"algorithmic_bytes_per_launch": refined,
+                            "achieved": refined / (pass_ms * 1e-3) / 1e9,
+                            "frac": refined / (pass_ms * 1e-3) / 1e9 / peak,
+                            "model": "check 2 s E + 4 n (first pass s E + 4 n), bit s E + 8 n per frame"},
+                "avg_launch_ms": pass_ms,
+                "launch": "one pass over the batch (check + bit kernels, one or two streams)"}, check_step, bit_step
+
+    clocks = ClockSampler(local)
+    ms_per_step, step_ms, prof, clk, out = timed_steps(args.msg, args.steps, args.warmup, clocks)
+    value = world * F * K_BITS / (ms_per_step * 1e-3) / 1e9
+    region_ms_step = prof["passes"]["total_ms"] / args.steps
+    roofline, check_bytes_step, bit_bytes_step = pass_roofline(args.msg, region_ms_step)
+    roofline["share_of_step"] = region_ms_step / ms_per_step
+
+    # per-kernel durations: further steps on ONE stream with every launch timed
+    # (outside the timed region), so the kernels run one after another and
+    # their durations add up to that one-stream step
+    kernel_steps = min(args.steps, 50)
+    kw1 = dict(kw, streams=1)
+    o1 = None
+    for i in range(3):
+        o1 = ldpc.ldpc_decode(h, llrs[i % n_buf], args.max_iter, out=o1, want_post=False, **kw1)
     torch.cuda.synchronize()
     ldpc.ldpc_prof_read(h, reset=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    stream = torch.cuda.current_stream()
-    events[0].record(stream)
-    # profile=2: the library times the region of the flooding passes with CUDA
-    # events on the launching stream; per-kernel events would break the
-    # programmatic launches between consecutive kernels, so they are taken in
-    # a separate profiled loop below
-    for i in range(args.steps):
-        out = ldpc.ldpc_decode(h, llrs[i % n_buf], args.max_iter, out=out, want_post=False, profile=2, **kw)
-        events[i + 1].record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    total_ms = events[0].elapsed_time(events[-1])
-    step_ms = [events[i].elapsed_time(events[i + 1]) for i in range(args.steps)]
-    prof = ldpc.ldpc_prof_read(h, reset=True)
-    # per-kernel durations (every launch timed), outside the timed region
-    kernel_steps = min(args.steps, 50)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
     for i in range(kernel_steps):
-        out = ldpc.ldpc_decode(h, llrs[i % n_buf], args.max_iter, out=out, want_post=False, profile=1, **kw)
+        o1 = ldpc.ldpc_decode(h, llrs[i % n_buf], args.max_iter, out=o1, want_post=False, profile=1, **kw1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    one_stream_ms = ev0.elapsed_time(ev1) / kernel_steps
     kprof = ldpc.ldpc_prof_read(h, reset=True)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    passes = args.max_iter + 1
-    E = code.n_edges
-    value = world * F * K_BITS / (ms_per_step * 1e-3) / 1e9
+    kern = {k: v for k, v in kprof.items() if isinstance(v, dict) and v["launches"] and k != "passes"}
+    step_kernel_ms = sum(v["total_ms"] for v in kern.values()) / kernel_steps
+
     # decode quality of the last step (same noise realisation as buffer (steps-1) % 4)
     last = (args.steps - 1) % n_buf
     ref_bits = ldpc.ldpc_decode(h, llrs[last], args.max_iter, **kw)
     bit_err = int((ref_bits["bits"] != cw).sum().item())
     frame_err = int((ref_bits["bits"] != cw).any(dim=1).sum().item())
 
-    # Roofline of the dominant work, the flooding passes (check-node and
-    # bit-node kernels; with two streams they overlap, so the unit timed is the
-    # pass region on the launching stream): algorithmic bytes / time.
-    s = {"f32": 4, "f16": 2, "bf16": 2, "i8": 1}[args.msg]
-    n = code.n
-    check_bytes_step = ((passes - 1) * (2 * s * E + 4 * n) + (s * E + 4 * n)) * F
-    bit_bytes_step = passes * (s * E + 8 * n) * F
-    kern = {k: v for k, v in kprof.items() if isinstance(v, dict) and v["launches"] and k != "passes"}
-    region_ms_step = prof["passes"]["total_ms"] / args.steps
-    peak, peak_src = measured_hbm_peak()
-    pass_bytes = (check_bytes_step + bit_bytes_step) / passes
-    achieved = pass_bytes / (region_ms_step / passes * 1e-3) / 1e9
-    traffic, traffic_src = recorded_traffic(args.msg)
-    step_kernel_ms = sum(v["total_ms"] for v in kern.values()) / kernel_steps
-    shares = {k: v["total_ms"] / kernel_steps / step_kernel_ms for k, v in kern.items()}
-    model_bytes_step = passes * (3 * s * E + 12.125 * n) * F
+    model_bytes_step = passes * (3 * {"f32": 4, "f16": 2, "bf16": 2, "i8": 1}[args.msg] * E + 12.125 * n) * F
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -326,25 +367,32 @@ def run_ours(args):
                                                                            int(math.ceil(0.99 * len(step_ms))) - 1)],
         "model_bytes_per_step": model_bytes_step,
         "model_hbm_frac": model_bytes_step / (ms_per_step * 1e-3) / 1e9 / peak,
-        "roofline": {"bound": "hbm", "kernel": "flooding pass (check-node + bit-node kernels)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": peak_src, "traffic_source": traffic_src,
-                     "algorithmic_bytes_per_launch": pass_bytes, "avg_launch_ms": region_ms_step / passes,
-                     "launch": "one pass over the batch (check + bit kernels, one or two streams)",
-                     "share_of_step": region_ms_step / ms_per_step},
+        "roofline": roofline,
         "kernel_ms": {k: v["total_ms"] / v["launches"] for k, v in kern.items()},
-        "kernel_share": shares,
-        "check_kernel": {"achieved_gbs": check_bytes_step / (kern["check"]["total_ms"] / kernel_steps * 1e-3) / 1e9,
-                         "note": "durations overlap the other stream's bit kernel when streams = 2"},
+        "kernel_share": {k: v["total_ms"] / kernel_steps / step_kernel_ms for k, v in kern.items()},
+        "check_kernel": {"achieved_gbs": check_bytes_step / (kern["check"]["total_ms"] / kernel_steps * 1e-3) / 1e9},
         "bit_kernel": {"achieved_gbs": bit_bytes_step / (kern["bit"]["total_ms"] / kernel_steps * 1e-3) / 1e9},
         "launches_per_step": {k: v["launches"] / kernel_steps for k, v in kern.items()},
-        "kernel_timing": f"kernel_ms, kernel_share, check_kernel, bit_kernel and launches_per_step from "
-                         f"{kernel_steps} further steps with every launch timed (outside the timed region); the "
-                         f"timed steps time only the pass region, which keeps the kernels' programmatic launches",
+        "kernel_timing": {"one_stream_ms_per_step": one_stream_ms, "kernel_ms_per_step": step_kernel_ms,
+                          "note": f"kernel_ms, kernel_share, check_kernel and bit_kernel from {kernel_steps} further "
+                                  f"steps on one stream with every launch timed (outside the timed region): the "
+                                  f"kernels run one after another, so their per-step sum is at most the one-stream "
+                                  f"step; the timed steps run the two-stream schedule"},
         "gpu_launches": prof["kernels"],
         "clocks": clk,
         "quality": {"frames": F, "frame_errors": frame_err, "bit_errors": bit_err, "ebn0_db": args.ebn0},
     }
+
+    # the same workload in every message format (FP32 node arithmetic; only
+    # the stored check-to-bit messages change type)
+    if args.by_msg_steps > 0:
+        by_msg = {}
+        for msg in ("f32", "f16", "bf16", "i8"):
+            ms, _, pm, _, _ = timed_steps(msg, args.by_msg_steps, max(3, args.warmup))
+            rl, _, _ = pass_roofline(msg, pm["passes"]["total_ms"] / args.by_msg_steps)
+            by_msg[msg] = {"value": world * F * K_BITS / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                           "steps": args.by_msg_steps, "roofline": rl}
+        line["by_msg"] = by_msg
 
     # end to end through the host entry point (pinned buffers, copies inside)
     llr_host = [llrs[b].cpu().pin_memory() for b in range(n_buf)]

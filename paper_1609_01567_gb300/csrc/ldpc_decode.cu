@@ -239,7 +239,7 @@ static int msg_size(int dtype) { return msg_bytes(dtype); }
 // Frames per lane V and padded frame count Fp (a multiple of 32 V).
 // `want` = 0 picks by batch size: four frames per lane (the widest rows,
 // best for the bandwidth-bound bit kernel) once the padding stays small.
-static void frames_layout(int32_t F, int32_t want, int32_t *V, int32_t *Fp) {
+void frames_layout(int32_t F, int32_t want, int32_t *V, int32_t *Fp) {
     int32_t v = want;
     if (v != 1 && v != 2 && v != 4 && v != 8) v = F > 64 ? 4 : (F > 32 ? 2 : 1);
     *V = v;
@@ -341,21 +341,18 @@ struct Launcher {
     }
 };
 
-template <typename M>
-static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32_t F, int32_t max_iter,
-                             const ldpc_decode_opts_t &o, float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok,
-                             float *post, float *r_out, cudaStream_t s) {
-    int32_t V, Fp;
-    frames_layout(F, o.frames_per_lane, &V, &Fp);
+PassArgs make_pass_args(const ldpc_code *c, const ldpc_decode_opts_t &o, float l_max, int32_t F, int32_t V,
+                        int32_t Fp, float *lamT, float *app, void *r, uint32_t *done, uint32_t *status,
+                        uint32_t *unsat, int32_t *stop_iter) {
     PassArgs a{};
     a.row_ptr = c->d.row_ptr;
     a.col_idx = c->d.col_idx;
     a.col_ptr = c->d.col_ptr;
     a.edge_slot = c->d.edge_slot;
     a.phi_table = c->d.phi_table;
-    a.lamT = w.lamT;
-    a.app = w.app;
-    a.r = w.r;
+    a.lamT = lamT;
+    a.app = app;
+    a.r = r;
     a.m = c->m;
     a.n = c->n;
     a.E = c->E;
@@ -368,10 +365,10 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     a.c_min = (float)(2.0 / (std::exp((double)l_max) + 1.0));
     a.c_max = (float)(-std::expm1(-(double)l_max));
     a.t_min = (float)std::exp(-(double)l_max);
-    a.done = w.done;
-    a.status = w.done + w.fp_cap / 32;  // the word after the frame bits
-    a.unsat = w.unsat;
-    a.stop_iter = w.stop_iter;
+    a.done = done;
+    a.status = status;
+    a.unsat = unsat;
+    a.stop_iter = stop_iter;
     a.grid_ctas = std::max(1, c->sm_count) * 4;
     a.sm_count = std::max(1, c->sm_count);
     a.check_schedule = o.check_schedule;
@@ -381,6 +378,18 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     a.ms_alpha = o.rule_alpha > 0.0f ? o.rule_alpha : 1.0f;
     a.ms_beta = o.rule_beta;
     a.ms_table = o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE ? c->d.ms_table : nullptr;
+    return a;
+}
+
+template <typename M>
+static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32_t F, int32_t max_iter,
+                             const ldpc_decode_opts_t &o, float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok,
+                             float *post, float *r_out, cudaStream_t s) {
+    int32_t V, Fp;
+    frames_layout(F, o.frames_per_lane, &V, &Fp);
+    // the status word follows the frame bits
+    PassArgs a = make_pass_args(c, o, l_max, F, V, Fp, w.lamT, w.app, w.r, w.done, w.done + w.fp_cap / 32, w.unsat,
+                                w.stop_iter);
 
     // profile 2 times only the pass region, so that consecutive kernels keep
     // their programmatic launch; other nonzero values time every launch too

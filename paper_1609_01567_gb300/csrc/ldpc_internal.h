@@ -116,3 +116,18 @@ struct ldpc_code {
     uint64_t graph_tick = 0;
     cudaStream_t capture_stream = nullptr;
 };
+
+namespace ldpc {
+
+// Frames per lane V (1, 2, 4 or 8) and padded frame count Fp (a multiple of
+// 32 V) of a decode of F frames; `want` = 0 picks by batch size.
+void frames_layout(int32_t F, int32_t want, int32_t *V, int32_t *Fp);
+
+// The argument block of every pass of one decode (code tables, options,
+// layout and the decode's buffers), shared by all decode entry points so that
+// none of them leaves a field unset. status is the call's device-wait word.
+PassArgs make_pass_args(const ldpc_code *c, const ldpc_decode_opts_t &o, float l_max, int32_t F, int32_t V,
+                        int32_t Fp, float *lamT, float *app, void *r, uint32_t *done, uint32_t *status,
+                        uint32_t *unsat, int32_t *stop_iter);
+
+}  // namespace ldpc

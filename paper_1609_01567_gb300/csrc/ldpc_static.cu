@@ -155,40 +155,7 @@ cudaError_t run_static(ldpc_code *c, unsigned char *scratch, const float *llr, i
     uint32_t *unsat = reinterpret_cast<uint32_t *>(carve(sizeof(uint32_t) * words * (max_iter + 1)));
     int32_t *stop_iter = reinterpret_cast<int32_t *>(carve(sizeof(int32_t) * (size_t)Fp));
 
-    PassArgs a{};
-    a.row_ptr = c->d.row_ptr;
-    a.col_idx = c->d.col_idx;
-    a.col_ptr = c->d.col_ptr;
-    a.edge_slot = c->d.edge_slot;
-    a.phi_table = c->d.phi_table;
-    a.lamT = lamT;
-    a.app = app;
-    a.r = r;
-    a.m = c->m;
-    a.n = c->n;
-    a.E = c->E;
-    a.Fp = Fp;
-    a.V = V;
-    a.n_frames = F;
-    a.early_exit = o.early_exit ? 1 : 0;
-    a.l_max = l_max;
-    a.phi_lmax = (float)std::log1p(2.0 / std::expm1((double)l_max));
-    a.c_min = (float)(2.0 / (std::exp((double)l_max) + 1.0));
-    a.c_max = (float)(-std::expm1(-(double)l_max));
-    a.t_min = (float)std::exp(-(double)l_max);
-    a.done = done;
-    a.status = done + words;
-    a.unsat = unsat;
-    a.stop_iter = stop_iter;
-    a.grid_ctas = std::max(1, c->sm_count) * 4;
-    a.sm_count = std::max(1, c->sm_count);
-    a.check_schedule = o.check_schedule;
-    a.f_begin = 0;
-    a.f_count = Fp;
-    a.check_rule = o.check_rule;
-    a.ms_alpha = o.rule_alpha > 0.0f ? o.rule_alpha : 1.0f;
-    a.ms_beta = o.rule_beta;
-    a.ms_table = o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE ? c->d.ms_table : nullptr;
+    PassArgs a = make_pass_args(c, o, l_max, F, V, Fp, lamT, app, r, done, done + words, unsat, stop_iter);
 
     // what must start at zero: the syndrome flag rows, and posteriors (the
     // padding frames' columns are read but never written)
@@ -260,36 +227,18 @@ extern "C" int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int
         o.early_exit = 1;
         o.l_max = 20.0f;
     }
-    if (!c) return set_error(LDPC_EINVAL, "ldpc_decode_static: code is NULL");
-    if (c->device < 0) return set_error(LDPC_ENODEV, "ldpc_decode_static: the code was created without device tables");
-    if (n_frames < 0) return set_error(LDPC_EINVAL, "ldpc_decode_static: n_frames=%d < 0", n_frames);
-    if (max_iter < 0 || max_iter > 100000)
-        return set_error(LDPC_EINVAL, "ldpc_decode_static: max_iter=%d outside [0, 100000]", max_iter);
-    float l_max = o.l_max > 0.0f ? o.l_max : 20.0f;
-    if (!(l_max <= 80.0f)) return set_error(LDPC_EINVAL, "ldpc_decode_static: l_max=%g outside (0, 80]", (double)o.l_max);
-    if (!msg_dtype_valid(o.msg_dtype)) return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown msg_dtype %d", o.msg_dtype);
+    // the argument rules of ldpc_decode, plus the one exception of this entry point
+    float l_max = 20.0f;
+    int st = check_opts(c, n_frames, max_iter, o, &l_max, "ldpc_decode_static");
+    if (st != LDPC_OK) return st;
     if (o.profile) return set_error(LDPC_EINVAL, "ldpc_decode_static: profiling is not available on this entry point");
-    if (o.check_rule != LDPC_RULE_SUM_PRODUCT && o.check_rule != LDPC_RULE_MIN_SUM &&
-        o.check_rule != LDPC_RULE_SP_TABLE && o.check_rule != LDPC_RULE_MIN_SUM_ADAPTIVE)
-        return set_error(LDPC_EINVAL, "ldpc_decode_static: unknown check_rule %d", o.check_rule);
-    if (o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE && !c->ms_table_set)
-        return set_error(LDPC_EINVAL, "ldpc_decode_static: the adaptive min-sum rule needs ldpc_code_set_rule_table first");
-    if (o.check_rule == LDPC_RULE_SP_TABLE && !(l_max <= kPhiTableMaxLmax))
-        return set_error(LDPC_EINVAL, "ldpc_decode_static: the tabulated rule needs l_max <= 22");
-    if (!(o.rule_beta >= 0.0f) || !std::isfinite(o.rule_alpha))
-        return set_error(LDPC_EINVAL, "ldpc_decode_static: rule_beta must be >= 0 and rule_alpha finite");
-    if (o.check_schedule < 0 || o.check_schedule > 2)
-        return set_error(LDPC_EINVAL, "ldpc_decode_static: check_schedule=%d not in {0, 1, 2}", o.check_schedule);
-    if (o.frames_per_lane != 0 && o.frames_per_lane != 1 && o.frames_per_lane != 2 && o.frames_per_lane != 4)
-        return set_error(LDPC_EINVAL, "ldpc_decode_static: frames_per_lane=%d not in {0, 1, 2, 4}", o.frames_per_lane);
     if (n_frames == 0) return LDPC_OK;
     if ((c->n > 0 && (!llr || !bits)) || !iters || !syndrome_ok)
         return set_error(LDPC_EINVAL, "ldpc_decode_static: NULL llr, bits, iters or syndrome_ok");
 
-    // same frame layout rule as ldpc_decode
-    int32_t V = o.frames_per_lane;
-    if (V != 1 && V != 2 && V != 4) V = n_frames > 64 ? 4 : (n_frames > 32 ? 2 : 1);
-    const int32_t Fp = (n_frames + 32 * V - 1) / (32 * V) * (32 * V);
+    // the frame layout of ldpc_decode
+    int32_t V = 0, Fp = 0;
+    frames_layout(n_frames, o.frames_per_lane, &V, &Fp);
     const size_t msg = (size_t)msg_bytes(o.msg_dtype);
     const size_t words = (size_t)Fp / 32;
     const size_t need = align256(4 * (size_t)c->n * Fp) * 2 + align256(msg * (size_t)c->E * Fp) +
@@ -303,7 +252,7 @@ extern "C" int ldpc_decode_static(const ldpc_code_t *code, const float *llr, int
 
     DeviceSwitch guard(c->device);
     void *scratch = nullptr;
-    int st = scratch_address(c->device, &scratch);
+    st = scratch_address(c->device, &scratch);
     if (st != LDPC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *base = static_cast<unsigned char *>(scratch);

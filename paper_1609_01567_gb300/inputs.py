@@ -25,12 +25,9 @@ from __future__ import annotations
 import collections
 import dataclasses
 import math
-from pathlib import Path
 
 import numpy as np
 import scipy.sparse
-
-GOLDEN_DIR = Path(__file__).resolve().parent.parent / "tests" / "golden"
 
 
 @dataclasses.dataclass(frozen=True)
@@ -228,31 +225,22 @@ def gaussian_llr(codewords: np.ndarray, sigma2: float, seed: int) -> np.ndarray:
 
 # --- the paper's worked example -------------------------------------------------
 
-def _read_golden_table(path: Path) -> dict[str, np.ndarray]:
-    out = {}
-    for line in path.read_text().splitlines():
-        line = line.strip()
-        if not line or line.startswith("#"):
-            continue
-        name, vals = line.split(":", 1)
-        out[name.strip()] = np.array([int(x) for x in vals.split()], dtype=np.int64)
-    return out
-
-
-def table(number: int) -> dict[str, np.ndarray]:
-    """Arrays of Table 1 (variable-sorted) or Table 2 (check-sorted), (14,7) code."""
-    return _read_golden_table(GOLDEN_DIR / f"table{number}_code_14_7.txt")
+# Table 1 (Section III-B), rows v and c: edge e joins variable V_14_7[e] and
+# check C_14_7[e] of the (14,7) example code. The parity-check matrix itself is
+# printed only as a figure; these two rows of the table define it.
+V_14_7 = (0, 0, 0, 0, 1, 1, 2, 2, 3, 3, 3, 4, 4, 5, 5, 6, 6, 7, 7, 8, 8, 9, 9, 10, 10, 11, 11, 12, 12, 13, 13)
+C_14_7 = (5, 3, 2, 0, 4, 0, 5, 1, 6, 4, 1, 4, 3, 1, 0, 4, 2, 6, 5, 5, 4, 2, 1, 6, 0, 3, 1, 6, 3, 5, 0)
 
 
 def code_14_7() -> Code:
     """The (14,7) code of the paper's example, COO in Table 1's edge order.
 
-    Table 1 lists for each edge e its variable v_e and check c_e; H has a one
-    at (c_e, v_e). The COO keeps Table 1's order, so the edge ids the library
-    assigns must reproduce e = 0..30.
+    H has a one at (C_14_7[e], V_14_7[e]) for every edge e of Table 1. The
+    COO keeps the table's order, so the edge ids the library assigns must
+    reproduce e = 0..30.
     """
-    t1 = table(1)
-    return Code(m=7, n=14, rows=t1["c"].astype(np.int32), cols=t1["v"].astype(np.int32), name="paper_14_7", k=7)
+    return Code(m=7, n=14, rows=np.array(C_14_7, dtype=np.int32), cols=np.array(V_14_7, dtype=np.int32),
+                name="paper_14_7", k=7)
 
 
 # --- workloads ----------------------------------------------------------------------

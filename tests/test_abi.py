@@ -13,6 +13,7 @@ import pytest
 
 from paper_1609_01567_gb300 import build as lib_build
 from paper_1609_01567_gb300 import inputs as I
+from tests.paper_tables import table
 
 ROOT = Path(__file__).resolve().parent.parent
 
@@ -54,7 +55,7 @@ def test_host_tables_reproduce_tables_1_and_2(ldpc):
     h = ldpc.ldpc_code_create(code.m, code.n, code.rows, code.cols, device=-1)
     got = ldpc.ldpc_code_tables(h)
     for number in (1, 2):
-        for name, want in I.table(number).items():
+        for name, want in table(number).items():
             if name == "e":
                 continue
             np.testing.assert_array_equal(got[name], want, err_msg=f"Table {number} array {name}")

@@ -12,6 +12,7 @@ import pytest
 from scipy import stats
 
 from paper_1609_01567_gb300 import inputs as I
+from tests.paper_tables import table
 
 
 # --- Tables 1-2 (Section III-B) --------------------------------------------------
@@ -19,8 +20,34 @@ from paper_1609_01567_gb300 import inputs as I
 def test_address_iterators_match_tables_1_and_2(oracle_mod):
     it = oracle_mod.address_iterators(I.code_14_7())
     for number in (1, 2):
-        for name, want in I.table(number).items():
+        for name, want in table(number).items():
             np.testing.assert_array_equal(it[name], want, err_msg=f"Table {number} array {name}")
+
+
+def test_example_code_edges_are_table_1():
+    """The input module's copy of the (14,7) code is Table 1's v and c rows."""
+    code = I.code_14_7()
+    t1 = table(1)
+    np.testing.assert_array_equal(code.cols, t1["v"])
+    np.testing.assert_array_equal(code.rows, t1["c"])
+
+
+# --- sigma^2 of the BER simulator (Section IV) -----------------------------------
+
+@pytest.mark.parametrize("ebn0_db,rate,want", [
+    (0.0, 0.5, 1.0),                                 # 1 / (2 * 1/2 * 1)
+    (10.0, 0.5, 0.1),                                # 1 / (2 * 1/2 * 10)
+    (0.0, 0.25, 2.0),                                # 1 / (2 * 1/4 * 1)
+    (10.0, 1.0 / 3.0, 0.15),                         # 1 / (2 * 1/3 * 10)
+    (3.0, 5.0 / 6.0, 0.3007123401763634),            # 1 / (5/3 * 1.99526231497) = 1 / 3.32543719161
+    (20.0, 0.5, 0.01),
+])
+def test_sigma2_from_ebn0_hand_values(ebn0_db, rate, want):
+    """Unit-energy BPSK: Es = 1, Eb = 1/R, sigma^2 = N0/2 = 1 / (2 R Eb/N0).
+    The expected values are worked out by hand, so a wrong factor of 2, R or
+    a dB conversion by 20 instead of 10 fails here (both sides of every
+    parity test read this one function)."""
+    assert I.sigma2_from_ebn0(ebn0_db, rate) == pytest.approx(want, rel=1e-12)
 
 
 def test_code_14_7_rank_and_text_example(oracle_mod):
