@@ -255,7 +255,9 @@ int ldpc_decode(ldpc_code_t *code, const float *llr, int32_t n_frames, int32_t m
  * ldpc_decode on HOST buffers (same shapes, host memory; pinned memory makes
  * the copies asynchronous). Copies llr to the device, decodes, copies bits,
  * iters, syndrome_ok (and post_llr when non-NULL) back, and synchronizes
- * `stream` before returning. opts->r_out must be NULL.
+ * `stream` before returning. opts->r_out must be NULL. Returns LDPC_ETIMEOUT
+ * (results copied back, iters = -1) when a bounded device wait of the decode
+ * gave up.
  */
 int ldpc_decode_host(ldpc_code_t *code, const float *llr_host, int32_t n_frames, int32_t max_iter,
                      const ldpc_decode_opts_t *opts, uint8_t *bits_host, int32_t *iters_host,
@@ -272,7 +274,8 @@ int ldpc_decode_host(ldpc_code_t *code, const float *llr_host, int32_t n_frames,
  * is needed for the overlap (pageable memory works, serialised). Returns when
  * every result is in host memory. opts->r_out and opts->profile must be
  * unset. Output pointers may repeat across batches (the copies out run in
- * batch order). The paper decodes one frame set per call; this is the
+ * batch order). Returns LDPC_ETIMEOUT when a bounded device wait of any
+ * batch's decode gave up (that batch reports iters = -1). The paper decodes one frame set per call; this is the
  * receive-chain form of the same decode.
  */
 int ldpc_decode_host_stream(ldpc_code_t *code, int32_t n_batches, const float *const *llr_host, int32_t n_frames,
@@ -466,6 +469,25 @@ int ldpc_count_errors(const uint8_t *bits, const uint8_t *ref, int32_t n_frames,
  * [count][4] uint64. */
 int ldpc_philox4x64_10(uint64_t key0, uint64_t key1, uint64_t ctr0, uint64_t ctr1, int64_t count,
                        uint64_t *out, void *stream);
+
+/*
+ * Test hook for the bounded device waits (no counterpart in the paper: it
+ * exercises this library's failure reporting). The pipelined check kernel
+ * waits for its row copies with a bounded number of polls; a warp whose wait
+ * runs out flags the call, waits (again bounded) for its own copies still in
+ * flight, and leaves, and the call then reports iters = -1 and
+ * syndrome_ok = 0 for every frame (LDPC_ETIMEOUT from the host-buffer entry
+ * points). ldpc_debug_giveup arms the next decode of `code` (ldpc_decode,
+ * ldpc_decode_host, ldpc_decode_host_stream; run directly, never from a
+ * captured graph) so that warp 0 of CTA `cta` (blockIdx.y * gridDim.x +
+ * blockIdx.x) of its first later check pass takes that path after the rows
+ * of its first check have landed: the give-up path runs without any wait
+ * running out and without a fault. It only has an effect where that pass
+ * runs the pipelined check kernel (frame groups of 64 or 128, checks of
+ * degree <= 16). cta = -1 disarms it; the hook clears itself after one
+ * decode. Returns LDPC_EINVAL for a NULL code or cta < -1.
+ */
+int ldpc_debug_giveup(ldpc_code_t *code, int32_t cta);
 
 /* Kernel classes reported by ldpc_prof_read. */
 enum {

@@ -269,6 +269,7 @@ static int ensure_workspace_dims(Workspace &w, int32_t n, int64_t E, int32_t Fp,
             (e = grow(reinterpret_cast<char **>(&w.r), (size_t)E * cap * mb)) != cudaSuccess ||
             (e = grow(&w.done, (size_t)cap / 32 + 1)) != cudaSuccess ||
             (e = grow(&w.stop_iter, (size_t)cap)) != cudaSuccess ||
+
             (e = grow(&w.dec, (size_t)n * cap / 32)) != cudaSuccess) {
             w.fp_cap = 0;
             w.iter_cap = -1;
@@ -362,9 +363,7 @@ PassArgs make_pass_args(const ldpc_code *c, const ldpc_decode_opts_t &o, float l
     a.early_exit = o.early_exit ? 1 : 0;
     a.l_max = l_max;
     a.phi_lmax = (float)std::log1p(2.0 / std::expm1((double)l_max));
-    a.c_min = (float)(2.0 / (std::exp((double)l_max) + 1.0));
-    a.c_max = (float)(-std::expm1(-(double)l_max));
-    a.t_min = (float)std::exp(-(double)l_max);
+    a.r_max = (float)std::exp((double)l_max);
     a.done = done;
     a.status = status;
     a.unsat = unsat;
@@ -378,6 +377,7 @@ PassArgs make_pass_args(const ldpc_code *c, const ldpc_decode_opts_t &o, float l
     a.ms_alpha = o.rule_alpha > 0.0f ? o.rule_alpha : 1.0f;
     a.ms_beta = o.rule_beta;
     a.ms_table = o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE ? c->d.ms_table : nullptr;
+    a.giveup_cta = -1;
     return a;
 }
 
@@ -440,6 +440,9 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
         if ((e = cudaStreamWaitEvent(hs[0], w.fork, 0)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(hs[1], w.fork, 0)) != cudaSuccess) return e;
     }
+    // test hook: one CTA of the first later check pass gives up its wait
+    const int32_t giveup = c->debug_giveup_cta;
+    c->debug_giveup_cta = -1;
     for (int32_t ti = 0; ti < ntiles; ++ti) {
         const int h = ti % nstreams;
         PassArgs at = a;
@@ -450,6 +453,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
             at.pass = t;
             at.syndrome = (t > 0 && at.early_exit) ? 1 : 0;
             at.dec = t == max_iter ? w.dec : nullptr;
+            at.giveup_cta = (t == 1 && ti == 0) ? giveup : -1;
             for (int b = 0; b < kNumCheckBins; ++b) {
                 int32_t count = c->bin_off[b + 1] - c->bin_off[b];
                 if (count == 0) continue;
@@ -648,7 +652,7 @@ static int decode_locked(ldpc_code *c, const float *llr, int32_t F, int32_t max_
     cudaError_t e = cudaStreamWaitEvent(s, c->ws.last_use, 0);
     if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: cudaStreamWaitEvent");
     bool done = false;
-    if (!o.profile) {
+    if (!o.profile && c->debug_giveup_cta < 0) {
         GraphKey key;
         key.llr = llr;
         key.bits = bits;
@@ -732,6 +736,23 @@ extern "C" int ldpc_decode_host(ldpc_code_t *c, const float *llr_host, int32_t F
         return cuda_error(e, "ldpc_decode_host: copy out");
     if ((e = cudaEventRecord(w.last_use, s)) != cudaSuccess) return cuda_error(e, "ldpc_decode_host: record");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_error(e, "ldpc_decode_host: synchronize");
+    return report_gave_up(iters_host, F, "ldpc_decode_host");
+}
+
+namespace ldpc {
+int report_gave_up(const int32_t *iters_host, int32_t F, const char *fn) {
+    for (int32_t f = 0; f < F; ++f)
+        if (iters_host[f] < 0)
+            return set_error(LDPC_ETIMEOUT, "%s: a bounded device wait of the decode ran out; no results", fn);
+    return LDPC_OK;
+}
+}  // namespace ldpc
+
+extern "C" int ldpc_debug_giveup(ldpc_code_t *c, int32_t cta) {
+    if (!c) return set_error(LDPC_EINVAL, "ldpc_debug_giveup: code is NULL");
+    if (cta < -1) return set_error(LDPC_EINVAL, "ldpc_debug_giveup: cta=%d < -1", cta);
+    std::lock_guard<std::mutex> lock(c->mu);
+    c->debug_giveup_cta = cta;
     return LDPC_OK;
 }
 

@@ -145,5 +145,7 @@ extern "C" int ldpc_decode_host_stream(ldpc_code_t *c, int32_t n_batches, const 
     if (st != LDPC_OK) return st;
     if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
     if (e != cudaSuccess) return cuda_error(e, "ldpc_decode_host_stream");
+    for (int32_t i = 0; i < n_batches; ++i)
+        if ((st = report_gave_up(iters_host[i], n_frames, "ldpc_decode_host_stream")) != LDPC_OK) return st;
     return LDPC_OK;
 }

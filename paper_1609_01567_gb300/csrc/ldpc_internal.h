@@ -115,6 +115,7 @@ struct ldpc_code {
     int n_seen = 0, next_seen = 0;
     uint64_t graph_tick = 0;
     cudaStream_t capture_stream = nullptr;
+    int32_t debug_giveup_cta = -1;  // ldpc_debug_giveup: armed for the next decode, then cleared
 };
 
 namespace ldpc {
@@ -126,6 +127,10 @@ void frames_layout(int32_t F, int32_t want, int32_t *V, int32_t *Fp);
 // The argument block of every pass of one decode (code tables, options,
 // layout and the decode's buffers), shared by all decode entry points so that
 // none of them leaves a field unset. status is the call's device-wait word.
+// LDPC_ETIMEOUT (with its message) when a frame of a finished host-side
+// decode reports iters = -1 (a bounded device wait gave up), else LDPC_OK.
+int report_gave_up(const int32_t *iters_host, int32_t F, const char *fn);
+
 PassArgs make_pass_args(const ldpc_code *c, const ldpc_decode_opts_t &o, float l_max, int32_t F, int32_t V,
                         int32_t Fp, float *lamT, float *app, void *r, uint32_t *done, uint32_t *status,
                         uint32_t *unsat, int32_t *stop_iter);

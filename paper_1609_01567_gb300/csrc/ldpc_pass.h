@@ -13,6 +13,7 @@
 // (V = 4 frames per lane).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -94,9 +95,7 @@ struct PassArgs {
     int32_t early_exit;
     float l_max;
     float phi_lmax;      // phi(l_max)
-    float c_min;         // 1 - tanh(l_max / 2): complement of the largest |r|
-    float c_max;         // 1 - e^-l_max: complement of the smallest |r|
-    float t_min;         // e^-l_max: the smallest t = e^-|q| of the product form
+    float r_max;         // e^l_max: the largest (A + B) / D of the product form, |r| = l_max
     uint32_t *done;      // [Fp/32]
     uint32_t *dec;       // [n][Fp/32] hard-decision words, written by the last bit pass (else null)
     uint32_t *status;    // one word, nonzero once a device wait of the call gave up
@@ -114,7 +113,21 @@ struct PassArgs {
     float ms_alpha;      // min-sum scale
     float ms_beta;       // min-sum offset
     const float2 *ms_table;   // degree-adaptive min-sum: (alpha, beta) indexed by check degree, else null
+    int32_t giveup_cta;  // test hook (ldpc_debug_giveup): this CTA of the launch treats its first
+                         // completed bounded wait as run out; -1 = off
+    // Tensor maps of the pipelined check kernel, filled by its launcher: the
+    // rows the check inputs are read from (lamT on the first pass, else app;
+    // float, box {32 V frames, 1 row}, gathered four rows at a time) and the
+    // message rows (r, box {32 V frames, D rows}: one check's rows).
+    CUtensorMap tm_q;
+    CUtensorMap tm_r;
 };
+
+// A 2-D tensor map (TMA descriptor) over a row-major buffer of `rows` rows
+// of `cols` elements (CUtensorMapDataType dtype), rows `row_bytes` apart,
+// with a box of {box_cols, box_rows}; encoded on the host, cached per thread.
+cudaError_t tensor_map_2d(CUtensorMap *out, int dtype, const void *base, uint64_t cols, uint64_t rows,
+                          uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows);
 
 template <typename M>
 cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, const int2 *desc, int32_t count,

@@ -31,6 +31,7 @@
 #include <cuda_fp16.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "ldpc_launch.cuh"
 #include "ldpc_pass.h"
@@ -120,53 +121,74 @@ struct MsgIO<__nv_bfloat16> {
     static __device__ __forceinline__ void store1(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
 };
 
-// int8 levels are converted with FP32 arithmetic instead of the int<->float
-// conversion instructions, which share the transcendental unit with the
-// check rule's ex2/lg2/rcp: adding 1.5 * 2^23 to a float of magnitude below
-// 2^22 leaves round(value) (ties to even) in the low mantissa bits, whose low
-// byte is the two's-complement level, and subtracting it back from a float
-// with such a pattern recovers the level exactly.
-constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
-constexpr uint32_t kRoundMagicBits = 0x4B400000u;
+// int8 messages are stored as biased levels u = k + 128 (k = round(r / step),
+// |k| <= 127, so 1 <= u <= 255) and converted with FP32 arithmetic instead of
+// the int<->float conversion instructions, which share the transcendental
+// unit with the check rule's ex2/lg2/rcp:
+//  * load: one byte permute assembles the float with bit pattern
+//    0x4B000000 + u, which is exactly 2^23 + u; subtracting 2^23 + 128 leaves
+//    k exactly, and k * step is the message (the same product as k * step
+//    from any other route, so the stored format does not change any value);
+//  * store: adding 1.5 * 2^23 + 128 to r / step (|r / step| < 2^22) leaves
+//    round(r / step) + 128 (ties to even) in the low mantissa bits, whose low
+//    byte is u.
+constexpr float kI8StoreMagic = 12583040.0f;   // 1.5 * 2^23 + 128
+constexpr float kI8LoadBias = 8388736.0f;      // 2^23 + 128
 
 template <>
 struct MsgIO<int8_t> {
-    // the level of x (clamped to +-127 steps) in the low byte of the result
+    // 2^23 + (byte B of w) as a float
+    template <int B>
+    static __device__ __forceinline__ float biased(uint32_t w) {
+        uint32_t f;
+        // bytes 1-3 of the result from 0x4B000000 (selectors 5, 6, 7), byte 0 from w
+        asm("prmt.b32 %0, %1, 0x4B000000, %2;" : "=r"(f) : "r"(w), "n"(0x7650 | B));
+        return __uint_as_float(f);
+    }
+    static __device__ __forceinline__ float2 values2(float a, float b) {
+        return __fmul2_rn(__fadd2_rn(make_float2(a, b), make_float2(-kI8LoadBias, -kI8LoadBias)),
+                          make_float2(kI8Step, kI8Step));
+    }
+    // the biased level of x (x clamped to +-127 steps) in the low byte
     static __device__ __forceinline__ uint32_t level_bits(float x) {
         x = fminf(fmaxf(x, -127.0f * kI8Step), 127.0f * kI8Step);
-        return __float_as_uint(fmaf(x, kI8Inv, kRoundMagic));
+        return __float_as_uint(fmaf(x, kI8Inv, kI8StoreMagic));
     }
-    // byte b of w, sign-extended, as level * step
-    template <int B>
-    static __device__ __forceinline__ float value(uint32_t w) {
-        // prmt with the sign-replicate bit set in the upper three selectors
-        constexpr uint32_t sel = (0x8u | B) << 12 | (0x8u | B) << 8 | (0x8u | B) << 4 | B;
-        int k;
-        asm("prmt.b32 %0, %1, 0, %2;" : "=r"(k) : "r"(w), "n"(sel));
-        return (__int_as_float((int)kRoundMagicBits + k) - kRoundMagic) * kI8Step;
+    // the same for two values already within +-127.5 steps (no clamp)
+    static __device__ __forceinline__ float2 level_bits2(float a, float b) {
+        return __ffma2_rn(make_float2(a, b), make_float2(kI8Inv, kI8Inv), make_float2(kI8StoreMagic, kI8StoreMagic));
     }
     static __device__ __forceinline__ void load4(const int8_t *p, float (&x)[4]) {
         const uint32_t w = *reinterpret_cast<const uint32_t *>(p);
-        x[0] = value<0>(w);
-        x[1] = value<1>(w);
-        x[2] = value<2>(w);
-        x[3] = value<3>(w);
+        const float2 lo = values2(biased<0>(w), biased<1>(w));
+        const float2 hi = values2(biased<2>(w), biased<3>(w));
+        x[0] = lo.x; x[1] = lo.y; x[2] = hi.x; x[3] = hi.y;
+    }
+    static __device__ __forceinline__ uint32_t pack4(uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) {
+        return __byte_perm(__byte_perm(b0, b1, 0x0040u), __byte_perm(b2, b3, 0x0040u), 0x5410u);
     }
     static __device__ __forceinline__ void store4(int8_t *p, const float (&x)[4]) {
-        const uint32_t lo = __byte_perm(level_bits(x[0]), level_bits(x[1]), 0x0040u);
-        const uint32_t hi = __byte_perm(level_bits(x[2]), level_bits(x[3]), 0x0040u);
-        *reinterpret_cast<uint32_t *>(p) = __byte_perm(lo, hi, 0x5410u);
+        *reinterpret_cast<uint32_t *>(p) = pack4(level_bits(x[0]), level_bits(x[1]), level_bits(x[2]), level_bits(x[3]));
+    }
+    // for |x| <= 127.5 steps (messages of a rule saturating at L_MAX <= 20)
+    static __device__ __forceinline__ void store4_unclamped(int8_t *p, const float (&x)[4]) {
+        const float2 lo = level_bits2(x[0], x[1]), hi = level_bits2(x[2], x[3]);
+        *reinterpret_cast<uint32_t *>(p) =
+            pack4(__float_as_uint(lo.x), __float_as_uint(lo.y), __float_as_uint(hi.x), __float_as_uint(hi.y));
     }
     static __device__ __forceinline__ void load2(const int8_t *p, float (&x)[2]) {
         const uint32_t w = *reinterpret_cast<const uint16_t *>(p);
-        x[0] = value<0>(w);
-        x[1] = value<1>(w);
+        const float2 v = values2(biased<0>(w), biased<1>(w));
+        x[0] = v.x;
+        x[1] = v.y;
     }
     static __device__ __forceinline__ void store2(int8_t *p, const float (&x)[2]) {
         *reinterpret_cast<uint16_t *>(p) = (uint16_t)__byte_perm(level_bits(x[0]), level_bits(x[1]), 0x0040u);
     }
+    // explicit roundings: a product left to the compiler could be fused into
+    // the caller's next add, which the packed forms never do
     static __device__ __forceinline__ float load1(const int8_t *p) {
-        return value<0>((uint32_t)(uint8_t)*p);
+        return __fmul_rn(__fadd_rn(biased<0>((uint32_t)(uint8_t)*p), -kI8LoadBias), kI8Step);
     }
     static __device__ __forceinline__ void store1(int8_t *p, float x) { *p = (int8_t)(level_bits(x) & 0xFFu); }
 };
@@ -376,118 +398,119 @@ __device__ __forceinline__ float two_sum(float a, float b, float &err) {
 // ---------------------------------------------------------------------------
 // The check rule in product form. Algorithm 1 ("Values to Variable Nodes")
 // computes r0 - r1 = prod_{j' != j} (1 - 2 q1_j'); in magnitudes this is
-//   tanh(|r_ij| / 2) = prod_{j' != j} T_j',   T = tanh(|q| / 2),
-// the same rule as phi(sum phi) above. The kernels carry it in complement
-// form so that nothing cancels: every input gives D = 1 - T = 2t / (1 + t),
-// t = e^-|q| (accurate for strong inputs, where T rounds to 1), partial
-// products are kept as C = 1 - prod T, merged by C(A u {k}) = C(A) + P(A) D_k
-// and P(A u {k}) = P(A) (1 - D_k) (sums of non-negative terms), and the
-// output magnitude is |r| = ln((1 + P) / (1 - P)) = ln((2 - C) / C).
-// Saturation: |q| > L acts as L (t is kept >= e^-L; the lower clamp of phi^,
-// |q| >= phi(L), leaves t = 1 in float and needs no instruction), and C is
-// kept >= 1 - tanh(L / 2) so that |r| <= L; C <= 1 holds up to rounding, so
-// the smallest magnitudes come out as 0 (or a rounding-sized value) instead
-// of phi(L). Scalar and packed forms run the same operations in the same
-// order.
+//   tanh(|r_ij| / 2) = prod_{j' != j} T_j',   T = tanh(x / 2),
+// x = min(|q|, L) (the saturation: |q| > L acts as L), the same rule as
+// phi(sum phi) above. With t = e^-x, T = (1 - t) / (1 + t), so for a set S of
+// inputs
+//   A(S) = prod (1 + t),  B(S) = prod (1 - t),  D(S) = A(S) - B(S),
+//   prod_S T = B / A,     |r| = ln((1 + B/A) / (1 - B/A)) = ln((A + B) / D)
+// for S the other inputs of an output. The kernels carry (A2, D) = (2A, D),
+// which needs no division per input and nothing that cancels:
+//   merging an input t:  D <- D + t (A2 - D)   (A2 - D = A + B),
+//                        A2 <- A2 (1 + t);
+//   an output joins the inputs before it (prefix p) and after it (suffix s):
+//     K = 2 D(p u s) = D_p A2_s + D_s (A2_p - 2 D_p)   (A2_p - 2 D_p = 2 B_p),
+//     (A + B) / D of p u s = A2_p A2_s / K - 1,
+// sums and products of non-negative terms (A2_p - 2 D_p loses relative
+// precision only where B_p << A_p, and then the term it scales is a few ulp
+// of K). One exponential per input, a reciprocal and a logarithm per output.
+// t = 2^(x * -log2(e)) with the product rounded once: its relative error is
+// below 2e-6 at x = 20, an absolute error of ~2e-6 in the strong outputs it
+// decides; the final "- 1" applies to a quotient >= 2, so weak outputs (A + B
+// close to D) carry an absolute error of a few ulp of 1 (the smallest
+// magnitudes come out as 0 or a rounding-sized value instead of phi(L)).
+// Saturation of the output, |r| <= L: only an empty set of other inputs (a
+// degree-1 check, K = 0) exceeds it; its quotient is clamped at e^L. Any
+// other set gives |r| <= min x <= L, and for two or more other inputs a
+// margin of ln 2 below L, so checks of a bin's full degree D >= 4 skip the
+// clamp with the same results. Padding inputs (t = 0) are exact no-ops of
+// the merge. Scalar and packed forms run the same operations in the same
+// order, so every frame layout gives the same results.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ float tanh_complement(float x, float t_min) {
-    float pn = x * -kL2E;
-    float e = fmaf(x, kL2E, pn);
-    e = fmaf(x, kL2ELo, e);
-    float t = ex2_approx(pn);
-    t = fmaxf(fmaf(t, e * -kLn2, t), t_min);
-    float rr = rcp_approx(t + 1.0f);
-    return (t + t) * rr;
+__device__ __forceinline__ float exp_neg(float x) { return ex2_approx(__fmul_rn(x, -kL2E)); }
+
+__device__ __forceinline__ float2 exp_neg2(float2 x) {
+    const float2 pn = mul2(x, f2(-kL2E));
+    return make_float2(ex2_approx(pn.x), ex2_approx(pn.y));
 }
 
-__device__ __forceinline__ float2 tanh_complement2(float2 x, float t_min) {
-    float2 pn = mul2(x, f2(-kL2E));
-    float2 e = fma2(x, f2(kL2E), pn);
-    e = fma2(x, f2(kL2ELo), e);
-    float2 t = make_float2(ex2_approx(pn.x), ex2_approx(pn.y));
-    t = fma2(t, mul2(e, f2(-kLn2)), t);
-    t = make_float2(fmaxf(t.x, t_min), fmaxf(t.y, t_min));
-    float2 tp = add2(t, f2(1.0f));
-    float2 rr = make_float2(rcp_approx(tp.x), rcp_approx(tp.y));
-    return mul2(add2(t, t), rr);
+// x = min(|q|, L) of two frames
+__device__ __forceinline__ float2 sat_abs2(float2 q, float l_max) {
+    return make_float2(fminf(fabsf(q.x), l_max), fminf(fabsf(q.y), l_max));
 }
 
-__device__ __forceinline__ float mag_of_complement(float c, float c_min) {
-    c = fmaxf(c, c_min);
-    float ratio = fmaf(c, -1.0f, 2.0f) * rcp_approx(c);
-    return lg2_approx(ratio) * kLn2;
+// The extrinsic input q = APP - r with a zero q given the sign of APP:
+// fma(APP, 2^-60, q) equals q exactly whenever q != 0 (|q| > 2^-36 |APP|
+// for any nonzero float difference, so the added term is below half an ulp
+// of q), and is 2^-60 APP when q = 0. A zero input then flips with its
+// posterior, as every other input does, so the outputs it has made (almost)
+// zero keep the exact sign symmetry of the rule under a codeword flip of the
+// inputs; their magnitudes are unchanged (t = e^-|q| rounds to 1 either way).
+constexpr float kZeroSign = 0x1.0p-60f;
+
+__device__ __forceinline__ float extrinsic(float app, float r) { return fmaf(app, kZeroSign, app - r); }
+
+__device__ __forceinline__ float2 extrinsic2(float2 app, float2 r) {
+    return fma2(app, f2(kZeroSign), fma2(r, f2(-1.0f), app));
 }
 
-__device__ __forceinline__ float2 mag_of_complement2(float2 c, float c_min) {
-    c.x = fmaxf(c.x, c_min);
-    c.y = fmaxf(c.y, c_min);
-    float2 ratio = mul2(fma2(c, f2(-1.0f), f2(2.0f)), make_float2(rcp_approx(c.x), rcp_approx(c.y)));
+// |mag| with the sign bit of `sign` (bit 31): one bit select. A weak output
+// can round to a magnitude of -1e-7 (a quotient just below 1); taking its
+// absolute value keeps the sign rule exact, and the rule symmetric under a
+// codeword flip of the inputs.
+__device__ __forceinline__ float with_sign(float mag, uint32_t sign) {
+    return __uint_as_float((__float_as_uint(mag) & 0x7FFFFFFFu) | (sign & 0x80000000u));
+}
+
+__device__ __forceinline__ void pf_merge(float &a2, float &dl, float t) {
+    const float s = fmaf(dl, -1.0f, a2);
+    dl = fmaf(t, s, dl);
+    a2 = fmaf(t, a2, a2);
+}
+
+__device__ __forceinline__ void pf_merge2(float2 &a2, float2 &dl, float2 t) {
+    const float2 s = fma2(dl, f2(-1.0f), a2);
+    dl = fma2(t, s, dl);
+    a2 = fma2(t, a2, a2);
+}
+
+template <bool kClamp>
+__device__ __forceinline__ float pf_log(float ratio, float r_max) {
+    if constexpr (kClamp) ratio = fminf(ratio, r_max);
+    return __fmul_rn(lg2_approx(ratio), kLn2);
+}
+
+template <bool kClamp>
+__device__ __forceinline__ float2 pf_log2(float2 ratio, float r_max) {
+    if constexpr (kClamp) {
+        ratio.x = fminf(ratio.x, r_max);
+        ratio.y = fminf(ratio.y, r_max);
+    }
     return mul2(make_float2(lg2_approx(ratio.x), lg2_approx(ratio.y)), f2(kLn2));
 }
 
-// Element-wise helpers over V frames (packed when V is even).
-template <int V>
-__device__ __forceinline__ void vtanh_complement(float (&x)[V], float t_min) {
-    if constexpr (V % 2 == 0) {
-#pragma unroll
-        for (int v = 0; v < V; v += 2) {
-            float2 y = tanh_complement2(make_float2(x[v], x[v + 1]), t_min);
-            x[v] = y.x;
-            x[v + 1] = y.y;
-        }
-    } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) x[v] = tanh_complement(x[v], t_min);
-    }
+// |r| for the union of a prefix (pa, pd) and a suffix (sa, sd)
+template <bool kClamp>
+__device__ __forceinline__ float pf_out(float pa, float pd, float sa, float sd, float r_max) {
+    const float k2 = fmaf(pd, sa, __fmul_rn(sd, fmaf(pd, -2.0f, pa)));
+    return pf_log<kClamp>(fmaf(__fmul_rn(pa, sa), rcp_approx(k2), -1.0f), r_max);
 }
 
-template <int V>
-__device__ __forceinline__ void vmag_of_complement(float (&c)[V], float c_min) {
-    if constexpr (V % 2 == 0) {
-#pragma unroll
-        for (int v = 0; v < V; v += 2) {
-            float2 y = mag_of_complement2(make_float2(c[v], c[v + 1]), c_min);
-            c[v] = y.x;
-            c[v + 1] = y.y;
-        }
-    } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) c[v] = mag_of_complement(c[v], c_min);
-    }
+template <bool kClamp>
+__device__ __forceinline__ float2 pf_out2(float2 pa, float2 pd, float2 sa, float2 sd, float r_max) {
+    const float2 k2 = fma2(pd, sa, mul2(sd, fma2(pd, f2(-2.0f), pa)));
+    const float2 rk = make_float2(rcp_approx(k2.x), rcp_approx(k2.y));
+    return pf_log2<kClamp>(fma2(mul2(pa, sa), rk, f2(-1.0f)), r_max);
 }
 
-// o = a * b + c
-template <int V>
-__device__ __forceinline__ void vfma(float (&o)[V], const float (&a)[V], const float (&b)[V], const float (&c)[V]) {
-    if constexpr (V % 2 == 0) {
-#pragma unroll
-        for (int v = 0; v < V; v += 2) {
-            float2 y = fma2(make_float2(a[v], a[v + 1]), make_float2(b[v], b[v + 1]), make_float2(c[v], c[v + 1]));
-            o[v] = y.x;
-            o[v + 1] = y.y;
-        }
-    } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) o[v] = fmaf(a[v], b[v], c[v]);
-    }
-}
-
-// p = p * (1 - dk)
-template <int V>
-__device__ __forceinline__ void vscale_by_tanh(float (&p)[V], const float (&dk)[V]) {
-    if constexpr (V % 2 == 0) {
-#pragma unroll
-        for (int v = 0; v < V; v += 2) {
-            float2 tk = fma2(make_float2(dk[v], dk[v + 1]), f2(-1.0f), f2(1.0f));
-            float2 y = mul2(make_float2(p[v], p[v + 1]), tk);
-            p[v] = y.x;
-            p[v + 1] = y.y;
-        }
-    } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) p[v] = p[v] * fmaf(dk[v], -1.0f, 1.0f);
-    }
+// The same where one side is empty, (A2, D) = (2, 0): K = 2 d and the product
+// 2 a of the other side, exactly the values pf_out2 forms from (2, 0).
+template <bool kClamp>
+__device__ __forceinline__ float2 pf_out_one2(float2 a2, float2 dl, float r_max) {
+    const float2 k2 = add2(dl, dl);
+    const float2 rk = make_float2(rcp_approx(k2.x), rcp_approx(k2.y));
+    return pf_log2<kClamp>(fma2(add2(a2, a2), rk, f2(-1.0f)), r_max);
 }
 
 // ---------------------------------------------------------------------------
@@ -627,7 +650,7 @@ __device__ __forceinline__ void check_node(int d, bool first, bool syn, Load &&l
     if constexpr (RULE == 1) {
         min_sum_node<D, V, M>(d, first, syn, load, out, Fp, a, unsat);
     } else {
-        float dc[D][V];    // D_k = 1 - tanh(|q_k| / 2)
+        float tt[D][V];    // t_k = e^-min(|q_k|, L); 0 (a no-op) for slots k >= d
         uint32_t ones[V];  // bit k: input k says "bit 1" (q > 0)
         uint32_t z[V];
     #pragma unroll
@@ -643,60 +666,60 @@ __device__ __forceinline__ void check_node(int d, bool first, bool syn, Load &&l
                 }
                 if (!first) {
     #pragma unroll
-                    for (int v = 0; v < V; ++v) av[v] = av[v] - rv[v];
+                    for (int v = 0; v < V; ++v) av[v] = extrinsic(av[v], rv[v]);
                 }
     #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     ones[v] |= (av[v] > 0.0f ? 1u : 0u) << k;
-                    dc[k][v] = fabsf(av[v]);
+                    tt[k][v] = exp_neg(fminf(fabsf(av[v]), a.l_max));
                 }
-                vtanh_complement<V>(dc[k], a.t_min);
             } else {
     #pragma unroll
-                for (int v = 0; v < V; ++v) dc[k][v] = 0.0f;  // T = 1: neutral
+                for (int v = 0; v < V; ++v) tt[k][v] = 0.0f;
             }
         }
     #pragma unroll
         for (int v = 0; v < V; ++v) unsat[v] |= z[v] != 0u;
-        // complements of the suffix products, then a running prefix
-        float csuf[D][V];
+        // (A2, D) of the inputs after k, then a running prefix
+        float sa[D][V], sd[D][V];
         {
-            float cr[V], pr[V];
+            float ca[V], cd[V];
     #pragma unroll
             for (int v = 0; v < V; ++v) {
-                cr[v] = 0.0f;
-                pr[v] = 1.0f;
+                ca[v] = 2.0f;
+                cd[v] = 0.0f;
             }
     #pragma unroll
             for (int k = D - 1; k >= 0; --k) {
     #pragma unroll
-                for (int v = 0; v < V; ++v) csuf[k][v] = cr[v];
-                vfma<V>(cr, pr, dc[k], cr);
-                vscale_by_tanh<V>(pr, dc[k]);
+                for (int v = 0; v < V; ++v) {
+                    sa[k][v] = ca[v];
+                    sd[k][v] = cd[v];
+                    if (k > 0) pf_merge(ca[v], cd[v], tt[k][v]);
+                }
             }
         }
         // output k is negative (bit-0 message) iff the other inputs hold an even
         // number of ones, i.e. iff input k's bit equals the total parity
-        float cp[V], pp[V];
+        float pa[V], pd[V];
         uint32_t neg[V];
     #pragma unroll
         for (int v = 0; v < V; ++v) {
-            cp[v] = 0.0f;
-            pp[v] = 1.0f;
+            pa[v] = 2.0f;
+            pd[v] = 0.0f;
             neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
         }
     #pragma unroll
         for (int k = 0; k < D; ++k) {
             if (k < d) {
                 float o[V];
-                vfma<V>(o, pp, csuf[k], cp);  // C of all inputs but k
-                vmag_of_complement<V>(o, a.c_min);
     #pragma unroll
-                for (int v = 0; v < V; ++v)
-                    o[v] = __int_as_float(__float_as_int(o[v]) | (int)((neg[v] << (31 - k)) & 0x80000000u));
+                for (int v = 0; v < V; ++v) {
+                    o[v] = pf_out<true>(pa[v], pd[v], sa[k][v], sd[k][v], a.r_max);
+                    o[v] = with_sign(o[v], neg[v] << (31 - k));
+                    pf_merge(pa[v], pd[v], tt[k][v]);
+                }
                 store_v<V, M>(out + (size_t)k * Fp, o);
-                vfma<V>(cp, pp, dc[k], cp);
-                vscale_by_tanh<V>(pp, dc[k]);
             }
         }
     }
@@ -734,7 +757,7 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
         };
         min_sum_node<D, 2 * P, M>(d, first, syn, load_flat, out, Fp, a, unsat);
     } else {
-        float2 dc[D][P];       // D_k = 1 - tanh(|q_k| / 2), two frames per entry
+        float2 tt[D][P];       // t_k, two frames per entry; 0 for slots k >= d
         uint32_t ones[2 * P];  // bit k: input k says "bit 1" (q > 0)
         uint32_t z[2 * P];
     #pragma unroll
@@ -750,42 +773,42 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
                         z[2 * q] ^= av[q].x > 0.0f ? 1u : 0u;
                         z[2 * q + 1] ^= av[q].y > 0.0f ? 1u : 0u;
                     }
-                    if (!first) av[q] = fma2(rv[q], f2(-1.0f), av[q]);
+                    if (!first) av[q] = extrinsic2(av[q], rv[q]);
                     ones[2 * q] |= (av[q].x > 0.0f ? 1u : 0u) << k;
                     ones[2 * q + 1] |= (av[q].y > 0.0f ? 1u : 0u) << k;
-                    dc[k][q] = tanh_complement2(make_float2(fabsf(av[q].x), fabsf(av[q].y)), a.t_min);
+                    tt[k][q] = exp_neg2(sat_abs2(av[q], a.l_max));
                 }
             } else {
     #pragma unroll
-                for (int q = 0; q < P; ++q) dc[k][q] = f2(0.0f);  // T = 1: neutral
+                for (int q = 0; q < P; ++q) tt[k][q] = f2(0.0f);
             }
         }
     #pragma unroll
         for (int v = 0; v < 2 * P; ++v) unsat[v] |= z[v] != 0u;
-        float2 csuf[D][P];
+        float2 sa[D][P], sd[D][P];
         {
-            float2 cr[P], pr[P];
+            float2 ca[P], cd[P];
     #pragma unroll
             for (int q = 0; q < P; ++q) {
-                cr[q] = f2(0.0f);
-                pr[q] = f2(1.0f);
+                ca[q] = f2(2.0f);
+                cd[q] = f2(0.0f);
             }
     #pragma unroll
             for (int k = D - 1; k >= 0; --k) {
     #pragma unroll
                 for (int q = 0; q < P; ++q) {
-                    csuf[k][q] = cr[q];
-                    cr[q] = fma2(pr[q], dc[k][q], cr[q]);
-                    pr[q] = mul2(pr[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
+                    sa[k][q] = ca[q];
+                    sd[k][q] = cd[q];
+                    if (k > 0) pf_merge2(ca[q], cd[q], tt[k][q]);
                 }
             }
         }
-        float2 cp[P], pp[P];
+        float2 pa[P], pd[P];
         uint32_t neg[2 * P];
     #pragma unroll
         for (int q = 0; q < P; ++q) {
-            cp[q] = f2(0.0f);
-            pp[q] = f2(1.0f);
+            pa[q] = f2(2.0f);
+            pd[q] = f2(0.0f);
         }
     #pragma unroll
         for (int v = 0; v < 2 * P; ++v) neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
@@ -795,11 +818,10 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
                 float2 o[P];
     #pragma unroll
                 for (int q = 0; q < P; ++q) {
-                    o[q] = mag_of_complement2(fma2(pp[q], csuf[k][q], cp[q]), a.c_min);
-                    o[q].x = __int_as_float(__float_as_int(o[q].x) | (int)((neg[2 * q] << (31 - k)) & 0x80000000u));
-                    o[q].y = __int_as_float(__float_as_int(o[q].y) | (int)((neg[2 * q + 1] << (31 - k)) & 0x80000000u));
-                    cp[q] = fma2(pp[q], dc[k][q], cp[q]);
-                    pp[q] = mul2(pp[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
+                    o[q] = pf_out2<true>(pa[q], pd[q], sa[k][q], sd[k][q], a.r_max);
+                    o[q].x = with_sign(o[q].x, neg[2 * q] << (31 - k));
+                    o[q].y = with_sign(o[q].y, neg[2 * q + 1] << (31 - k));
+                    pf_merge2(pa[q], pd[q], tt[k][q]);
                 }
                 store_pairs<M, P>(out + (size_t)k * Fp, o);
             }
@@ -817,8 +839,8 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
 template <int D, int P, typename M, bool kFirst, bool kSyn, bool kFull, typename Load>
 __device__ __forceinline__ void check_node_pairs_masked(int d, Load &&load, M *out, size_t Fp, const PassArgs &a,
                                                         bool (&unsat)[2 * P]) {
-    const float t_min = a.t_min, c_min = a.c_min;
-    float2 dc[D][P];
+    const float l_max = a.l_max, r_max = a.r_max;
+    float2 tt[D][P];
     // sign bits of the inputs, input k at bit D - 1 - k (shifted in by one
     // funnel shift per input; padding slots shift in 0)
     uint32_t sb[2 * P];
@@ -836,40 +858,41 @@ __device__ __forceinline__ void check_node_pairs_masked(int d, Load &&load, M *o
                 z[2 * q] ^= (real && av[q].x > 0.0f) ? 1u : 0u;
                 z[2 * q + 1] ^= (real && av[q].y > 0.0f) ? 1u : 0u;
             }
-            if constexpr (!kFirst) av[q] = fma2(rv[q], f2(-1.0f), av[q]);
+            if constexpr (!kFirst) av[q] = extrinsic2(av[q], rv[q]);
             const uint32_t bx = real ? __float_as_uint(av[q].x) : 0u, by = real ? __float_as_uint(av[q].y) : 0u;
             sb[2 * q] = __funnelshift_l(bx, sb[2 * q], 1);
             sb[2 * q + 1] = __funnelshift_l(by, sb[2 * q + 1], 1);
-            const float2 t = tanh_complement2(make_float2(fabsf(av[q].x), fabsf(av[q].y)), t_min);
-            dc[k][q] = make_float2(real ? t.x : 0.0f, real ? t.y : 0.0f);
+            const float2 t = exp_neg2(sat_abs2(av[q], l_max));
+            tt[k][q] = make_float2(real ? t.x : 0.0f, real ? t.y : 0.0f);
         }
     }
 #pragma unroll
     for (int v = 0; v < 2 * P; ++v) unsat[v] |= z[v] != 0u;
-    float2 csuf[D][P];
+    // (A2, D) of the inputs after k (the last one's is empty: (2, 0))
+    float2 sa[D][P], sd[D][P];
     {
-        float2 cr[P], pr[P];
+        float2 ca[P], cd[P];
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            cr[q] = f2(0.0f);
-            pr[q] = f2(1.0f);
+            ca[q] = f2(2.0f);
+            cd[q] = f2(0.0f);
         }
 #pragma unroll
         for (int k = D - 1; k >= 0; --k) {
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                csuf[k][q] = cr[q];
-                cr[q] = fma2(pr[q], dc[k][q], cr[q]);
-                pr[q] = mul2(pr[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
+                sa[k][q] = ca[q];
+                sd[k][q] = cd[q];
+                if (k > 0) pf_merge2(ca[q], cd[q], tt[k][q]);
             }
         }
     }
-    float2 cp[P], pp[P];
+    float2 pa[P], pd[P];
     uint32_t neg[2 * P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
-        cp[q] = f2(0.0f);
-        pp[q] = f2(1.0f);
+        pa[q] = f2(2.0f);
+        pd[q] = f2(0.0f);
     }
     // r_k > 0 iff an odd number of the other real inputs are > 0. With s_j
     // the sign bit of q_j, that count is (d - 1) - sum_{j != k} s_j, so r_k
@@ -884,15 +907,25 @@ __device__ __forceinline__ void check_node_pairs_masked(int d, Load &&load, M *o
         float2 o[P];
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            o[q] = mag_of_complement2(fma2(pp[q], csuf[k][q], cp[q]), c_min);
-            o[q].x = __int_as_float(__float_as_int(o[q].x) | (int)((neg[2 * q] << (32 - D + k)) & 0x80000000u));
-            o[q].y = __int_as_float(__float_as_int(o[q].y) | (int)((neg[2 * q + 1] << (32 - D + k)) & 0x80000000u));
-            if (k + 1 < D) {
-                cp[q] = fma2(pp[q], dc[k][q], cp[q]);
-                pp[q] = mul2(pp[q], fma2(dc[k][q], f2(-1.0f), f2(1.0f)));
-            }
+            // checks of the bin's full degree D >= 4 never need the clamp
+            if (k == 0)
+                o[q] = pf_out_one2<!kFull>(sa[0][q], sd[0][q], r_max);
+            else if (k == D - 1)
+                o[q] = pf_out_one2<!kFull>(pa[q], pd[q], r_max);
+            else
+                o[q] = pf_out2<!kFull>(pa[q], pd[q], sa[k][q], sd[k][q], r_max);
+            o[q].x = with_sign(o[q].x, neg[2 * q] << (32 - D + k));
+            o[q].y = with_sign(o[q].y, neg[2 * q + 1] << (32 - D + k));
+            if (k + 1 < D) pf_merge2(pa[q], pd[q], tt[k][q]);
         }
-        if (kFull || k < d) store_pairs<M, P>(out + (size_t)k * Fp, o);
+        if constexpr (kFull && std::is_same_v<M, int8_t> && P == 2) {
+            // |r| <= L <= 20 here (the caller takes this path for int8 only
+            // then), so the levels need no clamp
+            const float x[4] = {o[0].x, o[0].y, o[1].x, o[1].y};
+            MsgIO<int8_t>::store4_unclamped(out + (size_t)k * Fp, x);
+        } else if (kFull || k < d) {
+            store_pairs<M, P>(out + (size_t)k * Fp, o);
+        }
     }
 }
 
@@ -977,7 +1010,9 @@ template <int D, int V, typename M>
 struct PipeShape {
     static constexpr int kRowA = 32 * V * 4;                  // bytes of one APP row segment
     static constexpr int kRowR = 32 * V * (int)sizeof(M);     // bytes of one message row segment
-    static constexpr int kStage = D * (kRowA + kRowR);        // bytes of one check's rows
+    static constexpr int kOffR = D * kRowA;                   // message rows after the APP rows
+    static constexpr int kStage = kOffR + D * kRowR;          // bytes of one check's rows
+    static_assert(kRowA % 128 == 0 && kStage % 128 == 0, "copy destinations stay 128-byte aligned");
 };
 
 constexpr uint32_t kSpinLimit = 1u << 22;
@@ -1004,6 +1039,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+// One box {32 V frames, h rows} of a 2-D tensor map at (frame x, row y).
+__device__ __forceinline__ void tma_tile_2d(uint32_t dst, const CUtensorMap *tm, int x, int y, uint32_t bar,
+                                            uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(bar), "l"(pol)
+        : "memory");
+}
+// Four one-row boxes at (frame x, rows y0..y3), landing as four consecutive rows.
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *tm, int x, int y0, int y1, int y2, int y3,
+                                            uint32_t bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(bar), "l"(pol)
+        : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar, uint64_t pol) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::
@@ -1019,11 +1072,12 @@ struct BulkShape {
 };
 
 template <int D, int V, typename M, int S, int MODE, int RULE>
-__global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 *__restrict__ desc, int32_t count) {
+__global__ void __launch_bounds__(kThreads) k_check_bulk(const __grid_constant__ PassArgs a,
+                                                         const int2 *__restrict__ desc, int32_t count) {
     pdl_wait();
     using P = PipeShape<D, V, M>;
     using B = BulkShape<D, V, M, S>;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char *ring = smem + B::kBarBytes + (size_t)warp * S * P::kStage;
@@ -1035,7 +1089,6 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 
     M *r = reinterpret_cast<M *>(a.r);
     constexpr bool first = MODE == 0;
     constexpr bool syn = MODE == 2;
-    const float *qsrc = first ? a.lamT : a.app;
 
     bool live[V];
     bool any_live = false;
@@ -1055,23 +1108,37 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 
 
     const int stride = gridDim.x * (kThreads / 32);
     const int w0 = blockIdx.x * (kThreads / 32) + warp;
-    constexpr uint32_t kTx = (uint32_t)P::kRowA + (first ? 0u : (uint32_t)P::kRowR);  // bytes per input
     const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
+    // int8 messages of a rule saturating above 20 keep the clamped stores
+    const bool full_ok = !std::is_same_v<M, int8_t> || a.l_max <= 20.0f;
 
     // Copy the rows of one check (first slot b, degree d, lane k holding the
-    // column of input k) into stage st.
+    // column of input k) into stage st: lane 0 issues one tensor copy of the
+    // check's d message rows (a box of D rows from slot b; rows past the
+    // check are read but never used), a four-row gather per four APP rows and
+    // a one-row copy for each of the last d mod 4.
     auto issue = [&](int st, int b, int d, int jl) {
         if (d <= 0) return;
-        const uint32_t bar = bar0 + 8 * st;
-        if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)d * kTx);
+        // every lane's reads of this stage come before the copies that refill it
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncwarp();
-        if (lane < d) {
-            const uint32_t base = smem_u32(ring + st * P::kStage);
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            bulk_g2s(base + lane * P::kRowA, qsrc + (size_t)jl * Fp + fbase, P::kRowA, bar, pol_keep);
-            if (!first)
-                bulk_g2s(base + D * P::kRowA + lane * P::kRowR, r + (size_t)(b + lane) * Fp + fbase, P::kRowR, bar,
-                         pol_stream);
+        const uint32_t bar = bar0 + 8 * st;
+        const uint32_t base = smem_u32(ring + st * P::kStage);
+        const int d4 = d & ~3;
+        int cj[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) cj[k] = __shfl_sync(kFull, jl, k);
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar, (uint32_t)(d * P::kRowA) + (first ? 0u : (uint32_t)(D * P::kRowR)));
+#pragma unroll
+            for (int k = 0; k + 3 < D; k += 4)
+                if (k < d4)
+                    tma_gather4(base + k * P::kRowA, &a.tm_q, fbase, cj[k], cj[k + 1], cj[k + 2], cj[k + 3], bar,
+                                pol_keep);
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                if (k >= d4 && k < d) tma_tile_2d(base + k * P::kRowA, &a.tm_q, fbase, cj[k], bar, pol_keep);
+            if (!first) tma_tile_2d(base + P::kOffR, &a.tm_r, fbase, b, bar, pol_stream);
         }
     };
     auto get_desc = [&](int w) { return w < count ? desc[w] : make_int2(0, 0); };
@@ -1101,7 +1168,12 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 
         const int st = n % S;
         // every lane waits (the wait makes the copied rows visible to it);
         // the warp gives up together if any lane did
-        if (!__all_sync(kFull, mbar_wait(bar0 + 8 * st, (uint32_t)((n / S) & 1)))) {
+        bool landed = __all_sync(kFull, mbar_wait(bar0 + 8 * st, (uint32_t)((n / S) & 1)));
+        // test hook: warp 0 of the chosen CTA takes the give-up path with its
+        // first check's rows already landed (no wait runs out, nothing faults)
+        if (a.giveup_cta >= 0 && n == 0 && warp == 0 && (int)(blockIdx.y * gridDim.x + blockIdx.x) == a.giveup_cta)
+            landed = false;
+        if (!landed) {
             timed_out = true;
             break;
         }
@@ -1112,12 +1184,12 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(PassArgs a, const int2 
 #pragma unroll
             for (int q = 0; q < V / 2; ++q) av[q] = pa[q];
             if (!first)
-                load_pairs<V, M>(reinterpret_cast<const M *>(base + D * P::kRowA + k * P::kRowR) + lane * V, rv);
+                load_pairs<V, M>(reinterpret_cast<const M *>(base + P::kOffR + k * P::kRowR) + lane * V, rv);
         };
         if constexpr (RULE == 0) {
             // checks of the bin's full degree (most of them) skip the masking;
             // the widest bin keeps one path (registers)
-            if (D <= 8 && qd[0] == D)
+            if (D <= 8 && qd[0] == D && full_ok)
                 check_node_pairs_masked<D, V / 2, M, first, syn, true>(D, load, r + (size_t)qb[0] * Fp + f0, Fp, a,
                                                                       unsat);
             else
@@ -1171,7 +1243,7 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
     // whole CTA before any warp may leave
     const float2 *tab = nullptr;
     if constexpr (RULE == 2) {
-        extern __shared__ __align__(16) unsigned char smem[];
+        extern __shared__ __align__(128) unsigned char smem[];
         float2 *t = reinterpret_cast<float2 *>(smem);
         for (int i = threadIdx.x; i < kPhiTableSize; i += blockDim.x) t[i] = a.phi_table[i];
         __syncthreads();
@@ -1228,7 +1300,10 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
                 load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    qv[v] = av[v] - rv[v];
+                    // sum-product outputs next to a zero input are tiny, not
+                    // zero, so that input takes the sign of APP (min-sum
+                    // makes them exactly zero)
+                    qv[v] = RULE == 1 ? av[v] - rv[v] : extrinsic(av[v], rv[v]);
                     z[v] ^= av[v] > 0.0f ? 1u : 0u;
                 }
             }
@@ -1265,7 +1340,7 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
                 float rv[V];
                 load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
 #pragma unroll
-                for (int v = 0; v < V; ++v) qv[v] = av[v] - rv[v];
+                for (int v = 0; v < V; ++v) qv[v] = RULE == 1 ? av[v] - rv[v] : extrinsic(av[v], rv[v]);
             }
             float out[V];
 #pragma unroll
@@ -1365,7 +1440,10 @@ __global__ void __launch_bounds__(kThreads) k_check_wide(PassArgs a, const int32
                 load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    qv[v] = av[v] - rv[v];
+                    // sum-product outputs next to a zero input are tiny, not
+                    // zero, so that input takes the sign of APP (min-sum
+                    // makes them exactly zero)
+                    qv[v] = RULE == 1 ? av[v] - rv[v] : extrinsic(av[v], rv[v]);
                     z[v] ^= av[v] > 0.0f ? 1u : 0u;
                 }
             }
@@ -1443,7 +1521,7 @@ __global__ void __launch_bounds__(kThreads) k_check_wide(PassArgs a, const int32
                 float rv[V];
                 load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
 #pragma unroll
-                for (int v = 0; v < V; ++v) qv[v] = av[v] - rv[v];
+                for (int v = 0; v < V; ++v) qv[v] = RULE == 1 ? av[v] - rv[v] : extrinsic(av[v], rv[v]);
             }
             float out[V];
 #pragma unroll
@@ -1609,6 +1687,26 @@ static cudaError_t launch_check_bin_v(const PassArgs &a, int bin, const int32_t 
     return cudaGetLastError();
 }
 
+// Element type of a message buffer for its tensor map.
+template <typename M>
+struct TensorType;
+template <>
+struct TensorType<float> {
+    static constexpr int value = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+};
+template <>
+struct TensorType<__half> {
+    static constexpr int value = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+};
+template <>
+struct TensorType<__nv_bfloat16> {
+    static constexpr int value = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+};
+template <>
+struct TensorType<int8_t> {
+    static constexpr int value = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+};
+
 // Pipelined kernel: dynamic shared memory above 48 KB needs an opt-in, and
 // the grid is sized to the CTAs that fit on the GPU at once.
 template <int D, int V, typename M, int S, int MODE, int RULE>
@@ -1634,8 +1732,16 @@ static cudaError_t launch_bulk_mode(const PassArgs &a, const int2 *desc, int32_t
     PassArgs b = a;
     b.grid_ctas = a.sm_count * nres;
     dim3 grid = pass_grid(b, count, V);
-    return launch_pdl(k_check_bulk<D, V, M, S, MODE, RULE>, grid, dim3(kThreads), smem, s, a, desc, count);
-    return cudaGetLastError();
+    // the tensor maps of this launch: input rows (float, one-row boxes) and
+    // message rows (boxes of D rows), both 32 V frames wide
+    const float *qsrc = MODE == 0 ? a.lamT : a.app;
+    cudaError_t e = tensor_map_2d(&b.tm_q, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, qsrc, (uint64_t)a.Fp, (uint64_t)a.n,
+                                  (uint64_t)a.Fp * sizeof(float), 32 * V, 1);
+    if (e == cudaSuccess && MODE != 0)
+        e = tensor_map_2d(&b.tm_r, TensorType<M>::value, a.r, (uint64_t)a.Fp, (uint64_t)a.E,
+                          (uint64_t)a.Fp * sizeof(M), 32 * V, D);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_check_bulk<D, V, M, S, MODE, RULE>, grid, dim3(kThreads), smem, s, b, desc, count);
 }
 
 template <int D, int V, typename M, int S, int RULE>

@@ -66,7 +66,7 @@ EXPORTS = ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_enc
            "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_count_errors", "ldpc_batch_create",
            "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info", "ldpc_batch_destroy", "ldpc_server_create",
            "ldpc_server_submit", "ldpc_server_wait", "ldpc_server_stats", "ldpc_server_destroy", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_last_error",
-           "ldpc_version")
+           "ldpc_version", "ldpc_debug_giveup")
 
 _LIB = None
 _LOCK = threading.Lock()
@@ -114,6 +114,7 @@ def library():
             lib.ldpc_server_destroy.argtypes = [vp]
             lib.ldpc_server_destroy.restype = None
             lib.ldpc_prof_read.argtypes = [vp, ctypes.POINTER(ldpc_prof_t), i32]
+            lib.ldpc_debug_giveup.argtypes = [vp, i32]
             lib.ldpc_last_error.restype = ctypes.c_char_p
             lib.ldpc_version.restype = ctypes.c_char_p
             for name in ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira",
@@ -122,7 +123,8 @@ def library():
                          "ldpc_decode_static",
                          "ldpc_gen_awgn", "ldpc_philox4x64_10", "ldpc_prof_read", "ldpc_count_errors",
                          "ldpc_batch_create", "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info",
-                         "ldpc_server_create", "ldpc_server_submit", "ldpc_server_wait", "ldpc_server_stats"):
+                         "ldpc_server_create", "ldpc_server_submit", "ldpc_server_wait", "ldpc_server_stats",
+                         "ldpc_debug_giveup"):
                 getattr(lib, name).restype = ctypes.c_int
             _LIB = lib
         return _LIB
@@ -456,6 +458,13 @@ def ldpc_philox4x64_10(key0: int, key1: int, ctr0: int, ctr1: int, count: int, d
     _check(library().ldpc_philox4x64_10(key0, key1, ctr0, ctr1, count, ctypes.c_void_p(out.data_ptr()),
                                         _stream_handle(stream)))
     return out
+
+
+def ldpc_debug_giveup(code: Code, cta: int) -> None:
+    """Arm the bounded-wait test hook for the next decode of ``code``: warp 0
+    of CTA ``cta`` of its first later check pass takes the give-up path after
+    its rows have landed (-1 disarms)."""
+    _check(library().ldpc_debug_giveup(code.handle, int(cta)))
 
 
 def ldpc_prof_read(code: Code, reset: bool = True) -> dict:

@@ -181,3 +181,13 @@ def test_rule_table_validation(ldpc):
     assert "host-only" in str(e.value)
     with pytest.raises(ValueError):
         ldpc.ldpc_code_set_rule_table(h, [0.8, 0.7], [0.1])
+
+
+def test_debug_giveup_hook_validation(ldpc):
+    code = I.code_14_7()
+    h = ldpc.ldpc_code_create(code.m, code.n, code.rows, code.cols, device=-1)
+    ldpc.ldpc_debug_giveup(h, 0)
+    ldpc.ldpc_debug_giveup(h, -1)
+    with pytest.raises(ldpc.LdpcError) as e:
+        ldpc.ldpc_debug_giveup(h, -2)
+    assert e.value.status == -1
