@@ -320,24 +320,33 @@ int ldpc_batch_info(const ldpc_batch_t *batch, int32_t item, int32_t *frames_per
 void ldpc_batch_destroy(ldpc_batch_t *batch);
 
 /*
- * Decode server: continuous request batching over device-resident codes.
- * Requests (a code index, n_frames frames, caller-owned device buffers laid
- * out as in ldpc_decode) queue per code; a dispatcher thread hands the
- * oldest queued requests of one code, up to max_batch_frames frames, to a
- * free slot (a decode workspace with its own stream), gathers their LLRs,
- * decodes, scatters the results back and completes the requests from a host
- * callback. Several slots run at once, so requests that arrive while others
- * are on the GPU are admitted as slots free up and their work overlaps. The
- * slot count follows memory_budget (device bytes; admission by free memory)
- * and max_slots; submits beyond max_pending_frames queued frames return
- * LDPC_EBUSY. A request's results do not depend on the requests it was
- * batched with. Buffers must stay valid until ldpc_server_wait returns for
- * the request. All entry points are thread-safe.
+ * Decode server: continuous batching, at the frame level, over
+ * device-resident codes (the parallel decoders of the paper's Results
+ * section, serving requests as they arrive). Requests (a code index, n_frames
+ * frames, caller-owned device buffers laid out as in ldpc_decode) queue per
+ * code. A slot -- a frame set of up to max_batch_frames frames with its own
+ * workspace and stream -- serves one code at a time and decodes in chunks of
+ * a few flooding passes; between two chunks, every frame that has stopped
+ * (zero syndrome, with early exit) or used up its max_iter iterations has its
+ * results written to its request's buffers, the live frames are packed to
+ * the front, and queued requests of that code are admitted into the free
+ * frame groups, running their first pass and then sharing every later pass
+ * with the frames already running, each frame counting its own iterations. A
+ * request completes when its last frame is written out. Several slots run at
+ * once, so requests arriving while others are on the GPU are admitted as
+ * frames and slots free up and their work overlaps; a slot with no live frame
+ * takes the code with the oldest waiting request. The slot count follows
+ * memory_budget (admission by free memory) and max_slots; submits beyond
+ * max_pending_frames queued frames return LDPC_EBUSY. A request's results do
+ * not depend on the requests decoded beside it or on when it was admitted
+ * (they equal ldpc_decode's for the same options). Buffers must stay valid
+ * until ldpc_server_wait returns for the request. All entry points are
+ * thread-safe.
  */
 typedef struct ldpc_server ldpc_server_t;
 
 typedef struct {
-    int32_t max_batch_frames;   /* frames per batch, 1..8192 (0 = 1024); also the
+    int32_t max_batch_frames;   /* frames of a slot, 1..8192 (0 = 1024); also the
                                    largest request                              */
     int32_t max_slots;          /* batches in flight at once (0 = 4)              */
     int64_t memory_budget;      /* device bytes for the slots (0 = a quarter of
@@ -357,9 +366,9 @@ typedef struct {
     int32_t slots;         /* slots allocated                                    */
     int64_t completed;     /* requests completed                                 */
     int64_t frames;        /* frames completed                                   */
-    int64_t batches;       /* batches dispatched                                 */
+    int64_t batches;       /* admissions: groups of requests added to a slot     */
     int64_t queued_frames; /* frames waiting for a slot                          */
-    int64_t info_bits;     /* information bits of the dispatched frames          */
+    int64_t info_bits;     /* information bits of the admitted frames            */
 } ldpc_server_stats_t;
 
 /* Start a server over n_codes code handles (one device; the server borrows

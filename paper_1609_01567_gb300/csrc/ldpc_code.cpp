@@ -50,6 +50,7 @@ static void free_device_tables(ldpc_code *c) {
     cudaFree(c->d.bin_desc);
     cudaFree(c->d.phi_table);
     cudaFree(c->d.ms_table);
+    cudaFree(c->d.wide_vars);
     free_host_stream(c);
     free_decode_graphs(c);
     free_workspace(c->ws);
@@ -162,7 +163,10 @@ extern "C" int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t
             }
         }
         for (int32_t i = 0; i < m; ++i) c->max_cdeg = std::max(c->max_cdeg, c->row_ptr[i + 1] - c->row_ptr[i]);
-        for (int32_t j = 0; j < n; ++j) c->max_vdeg = std::max(c->max_vdeg, c->col_ptr[j + 1] - c->col_ptr[j]);
+        for (int32_t j = 0; j < n; ++j) {
+            c->max_vdeg = std::max(c->max_vdeg, c->col_ptr[j + 1] - c->col_ptr[j]);
+            if (c->col_ptr[j + 1] - c->col_ptr[j] > kWideVarDegree) c->wide_vars.push_back(j);
+        }
         // IRA form: column k + i joins checks i and i + 1 (the last one only
         // check m - 1), k = n - m
         if (n >= m) {
@@ -220,6 +224,7 @@ extern "C" int ldpc_code_create(int32_t m, int32_t n, int64_t nnz, const int32_t
             (e = upload(&c->d.bin_checks, c->bin_checks)) != cudaSuccess ||
             (e = upload(&c->d.bin_desc, c->bin_desc)) != cudaSuccess ||
             (e = upload(&c->d.phi_table, phi_chords())) != cudaSuccess ||
+            (e = upload(&c->d.wide_vars, c->wide_vars)) != cudaSuccess ||
             (e = upload(&c->d.ms_table, std::vector<float2>((size_t)c->max_cdeg + 1, make_float2(1.0f, 0.0f)))) !=
                 cudaSuccess ||
             (e = cudaEventCreateWithFlags(&c->ws.last_use, cudaEventDisableTiming)) != cudaSuccess) {

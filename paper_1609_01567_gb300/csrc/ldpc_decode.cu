@@ -55,12 +55,14 @@ __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ ll
     }
 }
 
-// done bits: padding frames (f >= F) start as stopped.
+// done bits: padding frames (f >= F) start as stopped; slot f holds frame f.
 __global__ void k_init_done(uint32_t *done, uint32_t *status, uint32_t *unsat, int64_t n_unsat, int32_t F,
-                            int32_t Fp) {
+                            int32_t Fp, int32_t *slot_frame) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w == 0) *status = 0u;
     for (int64_t i = w; i < n_unsat; i += (int64_t)gridDim.x * blockDim.x) unsat[i] = 0u;  // syndrome rows
+    if (slot_frame)
+        for (int32_t f = w; f < Fp; f += gridDim.x * blockDim.x) slot_frame[f] = f < F ? f : -1;
     if (w >= Fp / 32) return;
     uint32_t bits = 0;
     for (int b = 0; b < 32; ++b)
@@ -115,18 +117,26 @@ struct FrameResults {
     int32_t F, max_iter;
     int32_t *iters;
     uint8_t *ok;
+    const int32_t *slot_frame;  // frame held by each slot (-1: none); null: slot f holds frame f
 };
 
-__device__ __forceinline__ void write_frame_result(const FrameResults &fr, int32_t f) {
-    if (f >= fr.F) return;
+__device__ __forceinline__ int32_t frame_of_slot(const int32_t *slot_frame, int32_t s) {
+    return slot_frame ? slot_frame[s] : s;
+}
+
+// results of the frame in slot s (per-slot state, written at its frame index)
+__device__ __forceinline__ void write_frame_result(const FrameResults &fr, int32_t s) {
+    if (s >= fr.F) return;
+    const int32_t f = frame_of_slot(fr.slot_frame, s);
+    if (f < 0) return;
     if (*fr.status != 0u) {  // a device wait of the call gave up: no result
         fr.iters[f] = -1;
         fr.ok[f] = 0;
         return;
     }
-    const bool stopped = frame_bit(fr.done, f);
-    fr.iters[f] = stopped ? fr.stop_iter[f] : fr.max_iter;
-    fr.ok[f] = stopped ? 1 : (frame_bit(fr.final_unsat, f) ? 0 : 1);
+    const bool stopped = frame_bit(fr.done, s);
+    fr.iters[f] = stopped ? fr.stop_iter[s] : fr.max_iter;
+    fr.ok[f] = stopped ? 1 : (frame_bit(fr.final_unsat, s) ? 0 : 1);
 }
 
 // APP [n][Fp] -> bits [F][n] (1 iff APP > 0, Algorithm 5) and optional post
@@ -159,8 +169,10 @@ __global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ app,
                      (reinterpret_cast<uintptr_t>(post) & 15) == 0;
     for (int wi = threadIdx.x; wi < 32 * (kFinVars / 4); wi += blockDim.x) {
         const int fi = wi / (kFinVars / 4), q = wi % (kFinVars / 4);
-        const int32_t f = f0 + fi, j = j0 + 4 * q;
-        if (f >= F || j >= n) continue;
+        const int32_t s = f0 + fi, j = j0 + 4 * q;
+        if (s >= F || j >= n) continue;
+        const int32_t f = frame_of_slot(fr.slot_frame, s);
+        if (f < 0) continue;
         const float4 x = *reinterpret_cast<const float4 *>(&tile[fi][4 * q]);
         const size_t o = (size_t)f * n + j;
         if (vec) {
@@ -218,6 +230,176 @@ __global__ void k_frame_results(FrameResults fr) {
 }
 
 // ---------------------------------------------------------------------------
+// Early-exit compaction. A warp works on 32 V consecutive frame slots and
+// returns at once only when all of them have stopped, so a batch whose
+// frames stop at scattered iterations keeps most groups alive. Between two
+// passes, the live frames still held in slots [L, Fp) (L = live frames) are
+// moved into the slots [0, L) that hold stopped frames, after those stopped
+// frames' results have been written out; the trailing groups then hold no
+// live frame. Every step is a kernel on the decode's stream (no host
+// decision), and a compaction that would not free a group moves nothing.
+// ---------------------------------------------------------------------------
+
+constexpr int kPlanThreads = 1024;  // one thread per 32-slot word: Fp <= 32768
+
+// moves[0] = (M, L); moves[1 + i] = (source, destination) slot of move i.
+// `always`: pack the live frames to the front even when no group is freed.
+// `release` (continuous decoding): stopped slots, whose results have been
+// written out, give up their frame (slot_frame = -1).
+__global__ void __launch_bounds__(kPlanThreads) k_compact_plan(const uint32_t *__restrict__ done, int32_t Fp,
+                                                               int32_t group, int2 *__restrict__ moves, int32_t always,
+                                                               int32_t *__restrict__ release) {
+    pdl_wait();
+    __shared__ int32_t s_a[kPlanThreads], s_b[kPlanThreads];
+    const int t = threadIdx.x;
+    const int W = Fp / 32;
+    const uint32_t live = t < W ? ~done[t] : 0u;
+    if (release && t < W)
+        for (uint32_t x = ~live; x; x &= x - 1) release[t * 32 + __ffs(x) - 1] = -1;
+    // inclusive scan of the live counts
+    s_a[t] = __popc(live);
+    __syncthreads();
+    for (int o = 1; o < kPlanThreads; o <<= 1) {
+        const int v = t >= o ? s_a[t - o] : 0;
+        __syncthreads();
+        s_a[t] += v;
+        __syncthreads();
+    }
+    const int32_t L = s_a[kPlanThreads - 1];
+    // groups with a live frame now, and after packing
+    const int wpg = group / 32;
+    s_b[t] = (t < W && t % wpg == 0) ? 0 : 0;
+    __syncthreads();
+    if (t < W && live) atomicOr(&s_b[t / wpg], 1);
+    __syncthreads();
+    int32_t busy = 0;
+    for (int g = 0; g < (W + wpg - 1) / wpg; ++g) busy += s_b[g];
+    const int32_t after = (L + group - 1) / group;
+    __syncthreads();
+    if (after >= busy && !always) {
+        if (t == 0) moves[0] = make_int2(0, L);
+        return;
+    }
+    // holes: stopped slots below L; movers: live slots at or above L
+    const int32_t base = t * 32;
+    uint32_t below = 0u;  // bit b set when slot base + b < L
+    if (t < W) below = L >= base + 32 ? 0xFFFFFFFFu : (L <= base ? 0u : ((1u << (L - base)) - 1u));
+    const uint32_t holes = t < W ? ~live & below : 0u;
+    const uint32_t movers = t < W ? live & ~below : 0u;
+    s_a[t] = __popc(holes);
+    s_b[t] = __popc(movers);
+    __syncthreads();
+    for (int o = 1; o < kPlanThreads; o <<= 1) {
+        const int va = t >= o ? s_a[t - o] : 0, vb = t >= o ? s_b[t - o] : 0;
+        __syncthreads();
+        s_a[t] += va;
+        s_b[t] += vb;
+        __syncthreads();
+    }
+    int32_t h = s_a[t] - __popc(holes), m = s_b[t] - __popc(movers);  // exclusive offsets
+    for (uint32_t x = holes; x; x &= x - 1) moves[1 + h++].y = base + __ffs(x) - 1;
+    for (uint32_t x = movers; x; x &= x - 1) moves[1 + m++].x = base + __ffs(x) - 1;
+    if (t == kPlanThreads - 1) moves[0] = make_int2(s_a[t], L);
+}
+
+// Results of the stopped frames in the destination slots (about to be
+// reused): 128 variables x 32 moves per CTA, as k_finalize.
+__global__ void __launch_bounds__(256) k_compact_emit(const float *__restrict__ app, const int2 *__restrict__ moves,
+                                                      uint8_t *__restrict__ bits, float *__restrict__ post,
+                                                      int32_t n, int32_t Fp, FrameResults fr) {
+    pdl_wait();
+    const int32_t M = moves[0].x;
+    const int32_t i0 = blockIdx.y * 32;
+    if (i0 >= M) return;
+    __shared__ __align__(16) float tile[32][kFinStride];
+    __shared__ int32_t s_slot[32], s_frame[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 32) {
+        const int32_t s = i0 + lane < M ? moves[1 + i0 + lane].y : -1;
+        s_slot[lane] = s;
+        s_frame[lane] = s >= 0 ? fr.slot_frame[s] : -1;
+        if (blockIdx.x == 0 && s >= 0) write_frame_result(fr, s);
+    }
+    __syncthreads();
+    const int32_t j0 = blockIdx.x * kFinVars;
+    for (int r = warp; r < kFinVars; r += 8) {
+        const int32_t j = j0 + r;
+        const int32_t s = s_slot[lane];
+        tile[lane][r] = (j < n && s >= 0) ? app[(size_t)j * Fp + s] : 0.0f;
+    }
+    __syncthreads();
+    for (int wi = threadIdx.x; wi < 32 * kFinVars; wi += blockDim.x) {
+        const int fi = wi / kFinVars, q = wi % kFinVars;
+        const int32_t f = s_frame[fi], j = j0 + q;
+        if (f < 0 || j >= n) continue;
+        const float x = tile[fi][q];
+        bits[(size_t)f * n + j] = x > 0.0f ? 1 : 0;
+        if (post) post[(size_t)f * n + j] = x;
+    }
+}
+
+// Move the columns (LLRs, posteriors, messages) of every (source, destination)
+// pair: a warp per row; then the slots' frame map and stop bits.
+template <typename M>
+__global__ void __launch_bounds__(256) k_compact_move(float *__restrict__ lamT, float *__restrict__ app, M *r,
+                                                      int32_t n, int64_t E, int32_t Fp, const int2 *__restrict__ moves,
+                                                      int32_t *__restrict__ slot_frame, uint32_t *__restrict__ done,
+                                                      int32_t *__restrict__ base) {
+    pdl_wait();
+    const int32_t Mv = moves[0].x;
+    if (Mv == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = 2 * (int64_t)n + E;
+    for (int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); row < rows; row += (int64_t)gridDim.x * 8) {
+        if (row < 2 * (int64_t)n) {
+            float *p = (row < n ? lamT : app) + (size_t)(row < n ? row : row - n) * Fp;
+            for (int i = lane; i < Mv; i += 32) {
+                const int2 mv = moves[1 + i];
+                p[mv.y] = p[mv.x];
+            }
+        } else {
+            M *p = r + (size_t)(row - 2 * (int64_t)n) * Fp;
+            for (int i = lane; i < Mv; i += 32) {
+                const int2 mv = moves[1 + i];
+                p[mv.y] = p[mv.x];
+            }
+        }
+    }
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < Mv; i += blockDim.x) {
+            const int2 mv = moves[1 + i];
+            slot_frame[mv.y] = slot_frame[mv.x];
+            slot_frame[mv.x] = -1;
+            if (base) base[mv.y] = base[mv.x];
+            atomicAnd(done + (mv.y >> 5), ~(1u << (mv.y & 31)));
+            atomicOr(done + (mv.x >> 5), 1u << (mv.x & 31));
+        }
+    }
+}
+
+// The compaction of a continuous decode's frame set (the decode server's
+// slots): stopped slots release their frame, and the live frames are packed
+// to the front; moves[0] = (moves, live frames) afterwards.
+template <typename M>
+static cudaError_t launch_pack(const PassArgs &a, int32_t group, int32_t *slot_frame, int2 *moves, cudaStream_t s) {
+    cudaError_t e = launch_pdl(k_compact_plan, dim3(1), dim3(kPlanThreads), 0, s, a.done, a.Fp, group, moves, 1,
+                               slot_frame);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_compact_move<M>, dim3((unsigned)std::max(1, a.sm_count) * 8), dim3(256), 0, s,
+                       const_cast<float *>(a.lamT), a.app, reinterpret_cast<M *>(a.r), a.n, a.E, a.Fp,
+                       static_cast<const int2 *>(moves), slot_frame, a.done, const_cast<int32_t *>(a.base));
+    return e;
+}
+
+cudaError_t launch_continuous_pack(const PassArgs &a, int msg_dtype, int32_t group, int32_t *slot_frame, int2 *moves,
+                                   cudaStream_t s) {
+    return with_msg_type(msg_dtype, [&](auto tag) {
+        using M = typename decltype(tag)::type;
+        return launch_pack<M>(a, group, slot_frame, moves, s);
+    });
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 
@@ -269,7 +451,8 @@ static int ensure_workspace_dims(Workspace &w, int32_t n, int64_t E, int32_t Fp,
             (e = grow(reinterpret_cast<char **>(&w.r), (size_t)E * cap * mb)) != cudaSuccess ||
             (e = grow(&w.done, (size_t)cap / 32 + 1)) != cudaSuccess ||
             (e = grow(&w.stop_iter, (size_t)cap)) != cudaSuccess ||
-
+            (e = grow(&w.slot_frame, (size_t)cap)) != cudaSuccess ||
+            (e = grow(&w.moves, (size_t)cap + 1)) != cudaSuccess ||
             (e = grow(&w.dec, (size_t)n * cap / 32)) != cudaSuccess) {
             w.fp_cap = 0;
             w.iter_cap = -1;
@@ -378,6 +561,11 @@ PassArgs make_pass_args(const ldpc_code *c, const ldpc_decode_opts_t &o, float l
     a.ms_beta = o.rule_beta;
     a.ms_table = o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE ? c->d.ms_table : nullptr;
     a.giveup_cta = -1;
+    a.base = nullptr;
+    a.max_iter = 0;
+    a.unsat_ring = 0;
+    a.wide_vars = c->d.wide_vars;
+    a.n_wide_vars = (int32_t)c->wide_vars.size();
     return a;
 }
 
@@ -395,12 +583,18 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     // their programmatic launch; other nonzero values time every launch too
     const bool per_kernel = o.profile != 0 && o.profile != 2;
     Launcher L{c, s, per_kernel};
+    // Early-exit decodes of two or more frame groups compact their live frames
+    // at a few pass boundaries (not with the message export, which reads the
+    // messages by slot).
+    const int32_t group = 32 * V;
+    const bool compact = a.early_exit && max_iter >= 6 && Fp >= 2 * group && !r_out && c->n > 0;
     cudaError_t e;
     const int words = Fp / 32;
     e = L(LDPC_K_OTHER, 1, [&] {
         const int64_t n_unsat = (int64_t)(max_iter + 1) * words;
         const int64_t blocks = std::min<int64_t>(std::max<int64_t>(words, n_unsat) / 128 + 1, 1024);
-        k_init_done<<<(unsigned)blocks, 128, 0, s>>>(w.done, a.status, w.unsat, n_unsat, F, Fp);
+        k_init_done<<<(unsigned)blocks, 128, 0, s>>>(w.done, a.status, w.unsat, n_unsat, F, Fp,
+                                                     compact ? w.slot_frame : nullptr);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -443,41 +637,75 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     // test hook: one CTA of the first later check pass gives up its wait
     const int32_t giveup = c->debug_giveup_cta;
     c->debug_giveup_cta = -1;
-    for (int32_t ti = 0; ti < ntiles; ++ti) {
-        const int h = ti % nstreams;
-        PassArgs at = a;
-        at.f_begin = ti * tile;
-        at.f_count = tile;
-        Launcher Lh{c, hs[h], per_kernel};
-        for (int32_t t = 0; t <= max_iter; ++t) {
-            at.pass = t;
-            at.syndrome = (t > 0 && at.early_exit) ? 1 : 0;
-            at.dec = t == max_iter ? w.dec : nullptr;
-            at.giveup_cta = (t == 1 && ti == 0) ? giveup : -1;
-            for (int b = 0; b < kNumCheckBins; ++b) {
-                int32_t count = c->bin_off[b + 1] - c->bin_off[b];
-                if (count == 0) continue;
-                at.bin_degree = c->bin_max_degree[b];
-                e = Lh(LDPC_K_CHECK, 1, [&] {
-                    return launch_check_bin<M>(at, b, c->d.bin_checks + c->bin_off[b], c->d.bin_desc + c->bin_off[b],
-                                               count, hs[h]);
-                });
-                if (e != cudaSuccess) return e;
-            }
-            if (nstreams == 2 && ti == 0 && t == 0) {
-                if ((e = cudaEventRecord(w.phase, hs[0])) != cudaSuccess) return e;
-                if ((e = cudaStreamWaitEvent(hs[1], w.phase, 0)) != cudaSuccess) return e;
-            }
-            if (c->n > 0) {
-                e = Lh(LDPC_K_BIT, 1, [&] { return launch_bit<M>(at, hs[h]); });
-                if (e != cudaSuccess) return e;
+    // Segments of passes; between two segments the streams join and the
+    // compaction kernels run on `s`.
+    static constexpr int32_t kCuts[] = {6, 10, 15, 21, 28, 36, 46, 60, 80};
+    std::vector<int32_t> bounds{0};
+    if (compact)
+        for (int32_t t : kCuts)
+            if (t <= max_iter) bounds.push_back(t);
+    bounds.push_back(max_iter + 1);
+    for (size_t sg = 0; sg + 1 < bounds.size(); ++sg) {
+        const int32_t t0 = bounds[sg], t1 = bounds[sg + 1];
+        if (sg > 0 && nstreams == 2) {  // fork again after a compaction
+            if ((e = cudaEventRecord(w.fork, s)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(hs[0], w.fork, 0)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(hs[1], w.fork, 0)) != cudaSuccess) return e;
+        }
+        for (int32_t ti = 0; ti < ntiles; ++ti) {
+            const int h = ti % nstreams;
+            PassArgs at = a;
+            at.f_begin = ti * tile;
+            at.f_count = tile;
+            Launcher Lh{c, hs[h], per_kernel};
+            for (int32_t t = t0; t < t1; ++t) {
+                at.pass = t;
+                at.syndrome = (t > 0 && at.early_exit) ? 1 : 0;
+                at.dec = t == max_iter ? w.dec : nullptr;
+                at.giveup_cta = (t == 1 && ti == 0) ? giveup : -1;
+                for (int b = 0; b < kNumCheckBins; ++b) {
+                    int32_t count = c->bin_off[b + 1] - c->bin_off[b];
+                    if (count == 0) continue;
+                    at.bin_degree = c->bin_max_degree[b];
+                    e = Lh(LDPC_K_CHECK, 1, [&] {
+                        return launch_check_bin<M>(at, b, c->d.bin_checks + c->bin_off[b],
+                                                   c->d.bin_desc + c->bin_off[b], count, hs[h]);
+                    });
+                    if (e != cudaSuccess) return e;
+                }
+                if (nstreams == 2 && ti == 0 && t == t0) {
+                    if ((e = cudaEventRecord(w.phase, hs[0])) != cudaSuccess) return e;
+                    if ((e = cudaStreamWaitEvent(hs[1], w.phase, 0)) != cudaSuccess) return e;
+                }
+                if (c->n > 0) {
+                    e = Lh(LDPC_K_BIT, c->wide_vars.empty() ? 1 : 2, [&] { return launch_bit<M>(at, hs[h]); });
+                    if (e != cudaSuccess) return e;
+                }
             }
         }
-    }
-    if (nstreams == 2) {
-        for (int h = 0; h < 2; ++h) {
-            if ((e = cudaEventRecord(w.join[h], hs[h])) != cudaSuccess) return e;
-            if ((e = cudaStreamWaitEvent(s, w.join[h], 0)) != cudaSuccess) return e;
+        if (nstreams == 2) {
+            for (int h = 0; h < 2; ++h) {
+                if ((e = cudaEventRecord(w.join[h], hs[h])) != cudaSuccess) return e;
+                if ((e = cudaStreamWaitEvent(s, w.join[h], 0)) != cudaSuccess) return e;
+            }
+        }
+        if (sg + 2 < bounds.size()) {
+            e = L(LDPC_K_OTHER, 3, [&] {
+                cudaError_t ee = launch_pdl(k_compact_plan, dim3(1), dim3(kPlanThreads), 0, s, w.done, Fp, group,
+                                            w.moves, 0, static_cast<int32_t *>(nullptr));
+                const FrameResults fr{w.done, a.status, w.stop_iter, nullptr, F, max_iter, iters, ok, w.slot_frame};
+                if (ee == cudaSuccess)
+                    ee = launch_pdl(k_compact_emit, dim3((unsigned)((c->n + kFinVars - 1) / kFinVars),
+                                                         (unsigned)((Fp + 63) / 64)),
+                                    dim3(256), 0, s, w.app, w.moves, bits, post, c->n, Fp, fr);
+                if (ee == cudaSuccess)
+                    ee = launch_pdl(k_compact_move<M>, dim3((unsigned)std::max(1, c->sm_count) * 8), dim3(256), 0, s,
+                                    w.lamT, w.app, reinterpret_cast<M *>(w.r), c->n, c->E, Fp,
+                                    static_cast<const int2 *>(w.moves), w.slot_frame, w.done,
+                                    static_cast<int32_t *>(nullptr));
+                return ee;
+            });
+            if (e != cudaSuccess) return e;
         }
     }
     if (o.profile) {
@@ -497,7 +725,8 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
         if (e != cudaSuccess) return e;
     }
     e = L(LDPC_K_FINALIZE, 1, [&] {
-        const FrameResults fr{w.done, a.status, w.stop_iter, final_row, F, max_iter, iters, ok};
+        const FrameResults fr{w.done, a.status, w.stop_iter, final_row, F, max_iter, iters, ok,
+                              compact ? w.slot_frame : nullptr};
         if (c->n > 0) {
             dim3 grid((unsigned)((c->n + kFinVars - 1) / kFinVars), (unsigned)((F + 31) / 32), 1);
             return !a.early_exit && !post
@@ -817,6 +1046,8 @@ void free_workspace(Workspace &w) {
     cudaFree(w.done);
     cudaFree(w.unsat);
     cudaFree(w.stop_iter);
+    cudaFree(w.slot_frame);
+    cudaFree(w.moves);
     cudaFree(w.dec);
     cudaFree(w.h_llr);
     cudaFree(w.h_bits);

@@ -25,6 +25,10 @@ struct Workspace {
     uint32_t *unsat = nullptr;
     uint32_t *dec = nullptr;  // [n][Fp/32] final hard-decision words
     int32_t *stop_iter = nullptr;
+    // early-exit compaction: the frame each slot holds (-1: none), and the
+    // (source, destination) slot pairs of a compaction with their count
+    int32_t *slot_frame = nullptr;
+    int2 *moves = nullptr;
     // staging for ldpc_decode_host
     int32_t host_cap = 0;
     float *h_llr = nullptr;
@@ -96,6 +100,7 @@ struct ldpc_code {
     std::vector<int32_t> col_idx;       // vbar [E]
     std::vector<int32_t> edge_slot;     // [E]
     std::vector<int32_t> bin_checks;
+    std::vector<int32_t> wide_vars;     // variables of degree above kWideVarDegree
     std::vector<int2> bin_desc;
     int32_t bin_off[ldpc::kNumCheckBins + 1] = {0};
     int32_t bin_max_degree[ldpc::kNumCheckBins] = {0};  // largest check degree present in each bin
@@ -127,6 +132,12 @@ void frames_layout(int32_t F, int32_t want, int32_t *V, int32_t *Fp);
 // The argument block of every pass of one decode (code tables, options,
 // layout and the decode's buffers), shared by all decode entry points so that
 // none of them leaves a field unset. status is the call's device-wait word.
+// Compaction of a continuous decode's frame set (see ldpc_decode.cu):
+// stopped slots release their frame (slot_frame = -1), live frames are packed
+// to the front; moves[0] = (moves, live frames) afterwards.
+cudaError_t launch_continuous_pack(const PassArgs &a, int msg_dtype, int32_t group, int32_t *slot_frame, int2 *moves,
+                                   cudaStream_t s);
+
 // LDPC_ETIMEOUT (with its message) when a frame of a finished host-side
 // decode reports iters = -1 (a bounded device wait gave up), else LDPC_OK.
 int report_gave_up(const int32_t *iters_host, int32_t F, const char *fn);

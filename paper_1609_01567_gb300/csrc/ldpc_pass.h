@@ -68,7 +68,19 @@ struct DeviceTables {
     int2 *bin_desc = nullptr;      // [m']  (first slot, degree) of each binned check
     float2 *phi_table = nullptr;   // [kPhiTableSize] chords (a, b) of the tabulated phi
     float2 *ms_table = nullptr;    // [max check degree + 1] (alpha_d, beta_d) of the degree-adaptive min-sum
+    int32_t *wide_vars = nullptr;  // variables of degree above kWideVarDegree (their own bit kernel)
 };
+
+// Per-frame flag bits: frame f is bit (f & 31) of word f >> 5.
+__device__ __forceinline__ bool frame_bit(const uint32_t *words, int f) { return (words[f >> 5] >> (f & 31)) & 1u; }
+
+// stop_iter of a frame of a continuous decode that used up its iterations
+// with a nonzero syndrome (the low bits hold max_iter)
+constexpr int32_t kStopFailed = 0x40000000;
+
+// Variables of higher degree are summed by a CTA (k_bit_wide), its warps
+// splitting the edges; the others by one warp each.
+constexpr int kWideVarDegree = 16;
 
 // Tabulated phi: bucket key = float bits >> 17 (64 buckets per octave) over
 // [2^-32, 2^5); entry key - kPhiKey0 holds the chord a + b x of the bucket.
@@ -113,6 +125,17 @@ struct PassArgs {
     float ms_alpha;      // min-sum scale
     float ms_beta;       // min-sum offset
     const float2 *ms_table;   // degree-adaptive min-sum: (alpha, beta) indexed by check degree, else null
+    // Continuous decoding (the decode server's slots): frames enter and leave a
+    // running frame set. base[f] is the pass before frame f's own first pass,
+    // so its own pass count at pass t is t - base[f]; it stops at its first
+    // zero syndrome (early exit) or after max_iter of its own passes. The
+    // syndrome rows are then a ring of two (unsat_ring != 0). Null base: every
+    // frame starts at pass 0 of the call.
+    const int32_t *base;
+    int32_t max_iter;
+    int32_t unsat_ring;
+    const int32_t *wide_vars;  // variables of degree above kWideVarDegree
+    int32_t n_wide_vars;
     int32_t giveup_cta;  // test hook (ldpc_debug_giveup): this CTA of the launch treats its first
                          // completed bounded wait as run out; -1 = off
     // Tensor maps of the pipelined check kernel, filled by its launcher: the

@@ -517,7 +517,13 @@ __device__ __forceinline__ float2 pf_out_one2(float2 a2, float2 dl, float r_max)
 // Per-frame flag bits: frame f is bit (f & 31) of word f >> 5.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ bool frame_bit(const uint32_t *words, int f) { return (words[f >> 5] >> (f & 31)) & 1u; }
+// The syndrome flag row of the decision after pass p: row p of the call, or
+// one of two alternating rows in continuous decoding.
+__device__ __forceinline__ uint32_t *unsat_row(const PassArgs &a, int p) {
+    return a.unsat + (size_t)(a.unsat_ring ? (p & 1) : p) * (a.Fp / 32);
+}
+
+
 
 // OR the per-lane frame bits (frames f0 .. f0 + V - 1 of every lane) into the
 // flag row `row` with one atomic per 32 frames.
@@ -989,7 +995,7 @@ __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_
         bool bits[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) bits[v] = unsat[v] && live[v];
-        or_frame_bits<V>(a.unsat + (size_t)(a.pass - 1) * (a.Fp / 32), g, lane, bits);
+        or_frame_bits<V>(unsat_row(a, a.pass - 1), g, lane, bits);
     }
 }
 
@@ -1130,14 +1136,23 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(const __grid_constant__
         for (int k = 0; k < D; ++k) cj[k] = __shfl_sync(kFull, jl, k);
         if (lane == 0) {
             mbar_arrive_expect_tx(bar, (uint32_t)(d * P::kRowA) + (first ? 0u : (uint32_t)(D * P::kRowR)));
+            if (d == D) {  // most checks of a bin: straight-line copies
 #pragma unroll
-            for (int k = 0; k + 3 < D; k += 4)
-                if (k < d4)
+                for (int k = 0; k + 3 < D; k += 4)
                     tma_gather4(base + k * P::kRowA, &a.tm_q, fbase, cj[k], cj[k + 1], cj[k + 2], cj[k + 3], bar,
                                 pol_keep);
 #pragma unroll
-            for (int k = 0; k < D; ++k)
-                if (k >= d4 && k < d) tma_tile_2d(base + k * P::kRowA, &a.tm_q, fbase, cj[k], bar, pol_keep);
+                for (int k = D & ~3; k < D; ++k) tma_tile_2d(base + k * P::kRowA, &a.tm_q, fbase, cj[k], bar, pol_keep);
+            } else {
+#pragma unroll
+                for (int k = 0; k + 3 < D; k += 4)
+                    if (k < d4)
+                        tma_gather4(base + k * P::kRowA, &a.tm_q, fbase, cj[k], cj[k + 1], cj[k + 2], cj[k + 3], bar,
+                                    pol_keep);
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+                    if (k >= d4 && k < d) tma_tile_2d(base + k * P::kRowA, &a.tm_q, fbase, cj[k], bar, pol_keep);
+            }
             if (!first) tma_tile_2d(base + P::kOffR, &a.tm_r, fbase, b, bar, pol_stream);
         }
     };
@@ -1217,7 +1232,133 @@ __global__ void __launch_bounds__(kThreads) k_check_bulk(const __grid_constant__
         bool bits[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) bits[v] = unsat[v] && live[v];
-        or_frame_bits<V>(a.unsat + (size_t)(a.pass - 1) * (a.Fp / 32), g, lane, bits);
+        or_frame_bits<V>(unsat_row(a, a.pass - 1), g, lane, bits);
+    }
+}
+
+// Checks of degree 17-32 in codes with many of them (high-rate codes): the
+// product form of the register kernels, with each input's t and each suffix
+// state (A2, D) staged per warp in shared memory instead of registers, so
+// that the per-frame state does not grow with the degree. One pass over the
+// inputs (APP gathered, messages read once), a suffix sweep and an output
+// sweep over shared memory. The same operations in the same order as
+// check_node_pairs, one or two frames per lane (V = 1 or 2), so the results
+// do not depend on the frame layout.
+template <int V, typename M>
+struct ProdShape {
+    static constexpr int kPairs = V == 1 ? 1 : V / 2;  // float (V = 1) or float2 entries per lane
+    static constexpr int kEntry = V == 1 ? 4 : 8;
+    // bytes per warp for `ds` staged inputs: t, A2 and D of every input
+    static __host__ __device__ constexpr size_t warp_bytes(int ds) { return (size_t)3 * ds * 32 * kEntry; }
+};
+
+template <int V, typename M>
+__global__ void __launch_bounds__(kThreads) k_check_prod(PassArgs a, const int32_t *__restrict__ checks,
+                                                         int32_t count) {
+    static_assert(V == 1 || V == 2, "one or two frames per lane");
+    pdl_wait();
+    extern __shared__ __align__(128) unsigned char smem[];
+    using T = typename std::conditional<V == 1, float, float2>::type;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int ds = a.bin_degree;
+    T *tt = reinterpret_cast<T *>(smem + (size_t)warp * ProdShape<V, M>::warp_bytes(ds));
+    T *sa = tt + (size_t)ds * 32;
+    T *sd = sa + (size_t)ds * 32;
+    const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
+    const int f0 = g * 32 * V + lane * V;
+    const size_t Fp = (size_t)a.Fp;
+    M *r = reinterpret_cast<M *>(a.r);
+    const bool first = a.pass == 0;
+    const bool syn = a.syndrome != 0;
+    const float *qsrc = first ? a.lamT : a.app;
+    const float l_max = a.l_max, r_max = a.r_max;
+
+    bool live[V];
+    bool any_live = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        live[v] = !frame_bit(a.done, f0 + v);
+        any_live |= live[v];
+    }
+    if (!__any_sync(kFull, any_live)) return;
+    bool unsat[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) unsat[v] = false;
+    const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
+
+    auto two = [](float x) {
+        if constexpr (V == 1) return x;
+        else return f2(x);
+    };
+    for (int w = blockIdx.x * (kThreads / 32) + warp; w < count; w += gridDim.x * (kThreads / 32)) {
+        const int i = checks[w];
+        const int b = a.row_ptr[i];
+        const int d = a.row_ptr[i + 1] - b;  // 17 <= d <= ds
+        uint32_t sb[V], z[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) sb[v] = z[v] = 0u;
+        // inputs: t and sign bits (input k at bit d - 1 - k)
+#pragma unroll 4
+        for (int k = 0; k < d; ++k) {
+            float av[V], rv[V];
+            load_v_hint<V, float>(qsrc + (size_t)a.col_idx[b + k] * Fp + f0, av, pol_keep);
+            if (!first) load_v_hint<V, M>(r + (size_t)(b + k) * Fp + f0, rv, pol_stream);
+            float x[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (syn) z[v] ^= av[v] > 0.0f ? 1u : 0u;
+                if (!first) av[v] = extrinsic(av[v], rv[v]);
+                sb[v] = __funnelshift_l(__float_as_uint(av[v]), sb[v], 1);
+                x[v] = fminf(fabsf(av[v]), l_max);
+            }
+            if constexpr (V == 1) {
+                tt[k * 32 + lane] = exp_neg(x[0]);
+            } else {
+                tt[k * 32 + lane] = exp_neg2(make_float2(x[0], x[1]));
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) unsat[v] |= z[v] != 0u;
+        // suffix states: (A2, D) of the inputs after k
+        {
+            T ca = two(2.0f), cd = two(0.0f);
+            for (int k = d - 1; k >= 0; --k) {
+                sa[k * 32 + lane] = ca;
+                sd[k * 32 + lane] = cd;
+                if (k > 0) {
+                    if constexpr (V == 1) pf_merge(ca, cd, tt[k * 32 + lane]);
+                    else pf_merge2(ca, cd, tt[k * 32 + lane]);
+                }
+            }
+        }
+        // outputs with a running prefix
+        uint32_t neg[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) neg[v] = (((uint32_t)d ^ __popc(sb[v])) & 1u) ? ~sb[v] : sb[v];
+        T pa = two(2.0f), pd = two(0.0f);
+        M *out = r + (size_t)b * Fp + f0;
+        for (int k = 0; k < d; ++k) {
+            const T t = tt[k * 32 + lane];
+            float o[V];
+            if constexpr (V == 1) {
+                o[0] = with_sign(pf_out<true>(pa, pd, sa[k * 32 + lane], sd[k * 32 + lane], r_max),
+                                 neg[0] << (32 - d + k));
+                pf_merge(pa, pd, t);
+            } else {
+                const float2 y = pf_out2<true>(pa, pd, sa[k * 32 + lane], sd[k * 32 + lane], r_max);
+                o[0] = with_sign(y.x, neg[0] << (32 - d + k));
+                o[1] = with_sign(y.y, neg[1] << (32 - d + k));
+                pf_merge2(pa, pd, t);
+            }
+            store_v<V, M>(out + (size_t)k * Fp, o);
+        }
+    }
+    if (a.syndrome) {
+        bool bits[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) bits[v] = unsat[v] && live[v];
+        or_frame_bits<V>(unsat_row(a, a.pass - 1), g, lane, bits);
     }
 }
 
@@ -1366,7 +1507,7 @@ __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_
         bool bits[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) bits[v] = unsat[v] && live[v];
-        or_frame_bits<V>(a.unsat + (size_t)(a.pass - 1) * (a.Fp / 32), g, lane, bits);
+        or_frame_bits<V>(unsat_row(a, a.pass - 1), g, lane, bits);
     }
 }
 
@@ -1546,7 +1687,7 @@ __global__ void __launch_bounds__(kThreads) k_check_wide(PassArgs a, const int32
         bool bits[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) bits[v] = unsat[v] && live[v];
-        or_frame_bits<V>(a.unsat + (size_t)(a.pass - 1) * (a.Fp / 32), g, lane, bits);
+        or_frame_bits<V>(unsat_row(a, a.pass - 1), g, lane, bits);
     }
 }
 
@@ -1563,21 +1704,32 @@ __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
     const int f0 = g * 32 * V + lane * V;
     const size_t Fp = (size_t)a.Fp;
     const M *r = reinterpret_cast<const M *>(a.r);
-    const uint32_t *unsat_prev = a.pass > 0 ? a.unsat + (size_t)(a.pass - 1) * (a.Fp / 32) : nullptr;
+    const uint32_t *unsat_prev = a.pass > 0 ? unsat_row(a, a.pass - 1) : nullptr;
     const bool exit_test = a.early_exit && a.pass > 0;
+    const bool cont = a.base != nullptr && a.pass > 0;  // continuous decoding, a later pass
 
-    // One CTA records the frames whose previous hard decision was a codeword.
-    // Other CTAs may see the done bit either before or after it is set; both
-    // give the same answer, since it is set exactly when that frame's
-    // previous syndrome was zero, which they test as well.
-    if (exit_test && blockIdx.x == 0 && blockIdx.y == 0) {
+    // One CTA records the frames whose previous hard decision was a codeword
+    // (and, in continuous decoding, those that have used up their
+    // iterations). Other CTAs may see the done bit either before or after it
+    // is set; both give the same answer, since it is set exactly when the
+    // condition they test as well holds.
+    if ((exit_test || cont) && blockIdx.x == 0 && blockIdx.y == 0) {
         const int f_end = min(a.f_begin + a.f_count, a.n_frames);
         for (int f = a.f_begin + threadIdx.x; f < f_end; f += blockDim.x) {
-            if (!frame_bit(a.done, f) && !frame_bit(unsat_prev, f)) {
+            if (frame_bit(a.done, f)) continue;
+            const bool zero = !frame_bit(unsat_prev, f);
+            const int32_t own = cont ? a.pass - a.base[f] : a.pass;
+            if (exit_test && zero) {
                 atomicOr(a.done + (f >> 5), 1u << (f & 31));
-                a.stop_iter[f] = a.pass - 1;
+                a.stop_iter[f] = own - 1;
+            } else if (cont && own > a.max_iter) {
+                atomicOr(a.done + (f >> 5), 1u << (f & 31));
+                a.stop_iter[f] = a.max_iter | (zero ? 0 : kStopFailed);
             }
         }
+        // the row the next check pass writes starts clear
+        if (cont && a.unsat_ring)
+            for (int w = threadIdx.x; w < a.Fp / 32; w += blockDim.x) unsat_row(a, a.pass)[w] = 0u;
     }
 
     bool live[V];
@@ -1585,6 +1737,7 @@ __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         live[v] = !frame_bit(a.done, f0 + v) && (!exit_test || frame_bit(unsat_prev, f0 + v));
+        if (cont) live[v] = live[v] && a.pass - a.base[f0 + v] <= a.max_iter;
         all_live &= live[v];
         any_live |= live[v];
     }
@@ -1594,6 +1747,7 @@ __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
     for (int j = blockIdx.x * (kThreads / 32) + warp; j < a.n; j += gridDim.x * (kThreads / 32)) {
         const int e0 = a.col_ptr[j];
         const int e1 = a.col_ptr[j + 1];
+        if (e1 - e0 > kWideVarDegree) continue;  // k_bit_wide
         float acc[V];
         load_v_hint<V, float>(a.lamT + (size_t)j * Fp + f0, acc, pol_stream);
 #pragma unroll 4
@@ -1620,6 +1774,76 @@ __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
             for (int v = 0; v < V; ++v) bits[v] = acc[v] > 0.0f;
             store_frame_bits<V>(a.dec + (size_t)j * (Fp / 32), g, lane, bits);
         }
+    }
+}
+
+// Variables of degree above kWideVarDegree: one CTA per (variable, group of
+// 32 V frames), its eight warps summing every eighth edge; the eight partial
+// sums are added to lambda in warp order (a fixed order, so every frame
+// layout gives the same posterior). Runs after k_bit on the same stream; the
+// live frames are those k_bit updates.
+template <int V, typename M>
+__global__ void __launch_bounds__(kThreads) k_bit_wide(PassArgs a) {
+    pdl_wait();
+    constexpr int W = kThreads / 32;
+    __shared__ float part[W][32 * V];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
+    const int f0 = g * 32 * V + lane * V;
+    const size_t Fp = (size_t)a.Fp;
+    const M *r = reinterpret_cast<const M *>(a.r);
+    const uint32_t *unsat_prev = a.pass > 0 ? unsat_row(a, a.pass - 1) : nullptr;
+    const bool exit_test = a.early_exit && a.pass > 0;
+    const bool cont = a.base != nullptr && a.pass > 0;
+    bool live[V];
+    bool all_live = true, any_live = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        live[v] = !frame_bit(a.done, f0 + v) && (!exit_test || frame_bit(unsat_prev, f0 + v));
+        if (cont) live[v] = live[v] && a.pass - a.base[f0 + v] <= a.max_iter;
+        all_live &= live[v];
+        any_live |= live[v];
+    }
+    if (!__syncthreads_or(any_live)) return;  // the whole CTA leaves together
+    const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
+    for (int w = blockIdx.x; w < a.n_wide_vars; w += gridDim.x) {
+        const int j = a.wide_vars[w];
+        const int e0 = a.col_ptr[j], e1 = a.col_ptr[j + 1];
+        float acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+#pragma unroll 2
+        for (int e = e0 + warp; e < e1; e += W) {
+            float rv[V];
+            load_v_hint<V, M>(r + (size_t)a.edge_slot[e] * Fp + f0, rv, pol_stream);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += rv[v];
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) part[warp][lane * V + v] = acc[v];
+        __syncthreads();
+        if (warp == 0) {
+            load_v_hint<V, float>(a.lamT + (size_t)j * Fp + f0, acc, pol_stream);
+            for (int u = 0; u < W; ++u)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] += part[u][lane * V + v];
+            float *dst = a.app + (size_t)j * Fp + f0;
+            if (all_live) {
+                store_v_hint<V>(dst, acc, pol_keep);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (live[v]) dst[v] = acc[v];
+            }
+            if (a.dec) {
+                bool bits[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) bits[v] = acc[v] > 0.0f;
+                store_frame_bits<V>(a.dec + (size_t)j * (Fp / 32), g, lane, bits);
+            }
+        }
+        __syncthreads();  // the partials are read before the next variable overwrites them
     }
 }
 
@@ -1751,6 +1975,31 @@ static cudaError_t launch_bulk(const PassArgs &a, const int2 *desc, int32_t coun
     return launch_bulk_mode<D, V, M, S, 1, RULE>(a, desc, count, s);
 }
 
+// The staged product-form kernel: shared memory for the bin's largest degree,
+// the grid sized to the CTAs that fit on the GPU at once.
+template <int V, typename M>
+static cudaError_t launch_prod(const PassArgs &a, const int32_t *checks, int32_t count, cudaStream_t s) {
+    const size_t smem = (size_t)(kThreads / 32) * ProdShape<V, M>::warp_bytes(a.bin_degree);
+    static std::atomic<int> resident_by[64][33];  // per device and staged degree
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int> &resident = resident_by[dev & 63][std::min(a.bin_degree, 32)];
+    int nres = resident.load(std::memory_order_acquire);
+    if (nres == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_check_prod<V, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(kThreads / 32 * ProdShape<V, M>::warp_bytes(32)));
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_prod<V, M>, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        nres = nb > 0 ? nb : 1;
+        resident.store(nres, std::memory_order_release);
+    }
+    PassArgs b = a;
+    b.grid_ctas = a.sm_count * nres;
+    return launch_pdl(k_check_prod<V, M>, pass_grid(b, count, V), dim3(kThreads), smem, s, a, checks, count);
+}
+
 // One CTA per check and group of 32 V frames, as many checks at once as the
 // CTA budget of a pass allows.
 template <int V, typename M, int RULE>
@@ -1792,6 +2041,10 @@ static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *
     // kernel, whose loads of one check are all in flight at once. The choice
     // depends on the code only, never on the batch, so a frame's result does
     // not depend on the frames decoded with it.
+    if (bin == 4 && count >= kWideBinAnyKernel && RULE == 0) {
+        if (a.V >= 2 && a.f_count % 64 == 0 && a.f_begin % 64 == 0) return launch_prod<2, M>(a, checks, count, s);
+        return launch_prod<1, M>(a, checks, count, s);
+    }
     if (bin == 4 && count >= kWideBinAnyKernel) {
         if (a.V >= 4 && a.f_count % 128 == 0 && a.f_begin % 128 == 0)
             return launch_pdl(k_check_any<4, M, RULE>, pass_grid(a, count, 4), dim3(kThreads), 0, s, a, checks,
@@ -1838,22 +2091,28 @@ cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, 
     return launch_check_rule<M, 0>(a, bin, checks, desc, count, s);
 }
 
-template <typename M>
-cudaError_t launch_bit(const PassArgs &a, cudaStream_t s) {
+template <int V, typename M>
+static cudaError_t launch_bit_v(const PassArgs &a, cudaStream_t s) {
     // The bit kernel is bound by row gathers: 8 CTAs per SM (64 warps) keep
     // more rows in flight than the default 4.
     PassArgs b = a;
     b.grid_ctas = a.sm_count * 8;
-    dim3 grid = pass_grid(b, a.n, a.V);
-    if (a.V == 8)
-        return launch_pdl(k_bit<8, M>, grid, dim3(kThreads), 0, s, a);
-    else if (a.V == 4)
-        return launch_pdl(k_bit<4, M>, grid, dim3(kThreads), 0, s, a);
-    else if (a.V == 2)
-        return launch_pdl(k_bit<2, M>, grid, dim3(kThreads), 0, s, a);
-    else
-        return launch_pdl(k_bit<1, M>, grid, dim3(kThreads), 0, s, a);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_bit<V, M>, pass_grid(b, a.n, V), dim3(kThreads), 0, s, a);
+    if (e == cudaSuccess && a.n_wide_vars > 0) {
+        const int groups = a.f_count / (32 * V);
+        const int64_t cap = std::max<int64_t>(1, (int64_t)a.sm_count * 8 / groups);
+        const dim3 grid((unsigned)std::min<int64_t>(a.n_wide_vars, cap), (unsigned)groups, 1);
+        e = launch_pdl(k_bit_wide<V, M>, grid, dim3(kThreads), 0, s, a);
+    }
+    return e;
+}
+
+template <typename M>
+cudaError_t launch_bit(const PassArgs &a, cudaStream_t s) {
+    if (a.V == 8) return launch_bit_v<8, M>(a, s);
+    if (a.V == 4) return launch_bit_v<4, M>(a, s);
+    if (a.V == 2) return launch_bit_v<2, M>(a, s);
+    return launch_bit_v<1, M>(a, s);
 }
 
 template <typename M>

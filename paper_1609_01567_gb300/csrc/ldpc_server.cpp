@@ -1,19 +1,30 @@
-// Decode server: continuous request batching over device-resident codes.
+// Decode server: continuous batching at the frame level over device-resident
+// codes.
 //
 // Requests (code, frames, caller-owned device buffers) queue per code. A
-// dispatcher thread hands the oldest queued requests of one code, up to a
-// batch size, to a free slot -- a decode workspace with its own stream --
-// gathers their LLRs into the slot's batch buffer, decodes, scatters the
-// results back, and a host callback on the slot's stream completes the
-// requests and frees the slot. Several slots are in flight at once, so
-// requests arriving while others run are admitted as soon as a slot frees,
-// and their decodes overlap on the device. The number of slots follows a
-// device-memory budget (admission by free memory); submits beyond a bound on
-// queued frames are refused with LDPC_EBUSY (back-pressure).
+// slot -- a frame set of up to max_batch_frames frames with its workspace and
+// stream -- serves one code at a time and decodes in chunks of a few
+// flooding passes. Frames enter and leave a running slot independently:
+//   * after each chunk, every frame that has stopped (zero syndrome) or used
+//     up its max_iter iterations has its results written to its request's
+//     buffers, and the live frames are packed to the front of the slot;
+//   * queued requests of the slot's code are then admitted into the free
+//     frame groups at the back: their LLRs are interleaved into the slot, the
+//     new groups run their first check and bit pass (Algorithm 2's pass before
+//     the loop), and from the next chunk on they share every pass with the
+//     frames already running, each frame counting its own iterations.
+// A request completes when its last frame has been written out. Several slots
+// run at once on their own streams, so the device overlaps their work while
+// the dispatcher thread handles another slot between chunks; a slot whose
+// frames are all done takes the code with the oldest waiting request. Slots
+// are sized by a device-memory budget; submits beyond a bound on queued
+// frames are refused with LDPC_EBUSY (back-pressure).
 //
-// A frame's result does not depend on the other frames of its batch (the
-// kernels treat frames independently and deterministically), so a request
-// decodes to the same bits, iterations and posteriors alone or in the mix.
+// A frame's decode does not depend on the other frames of its slot or on when
+// it was admitted (the kernels treat frames independently and
+// deterministically, and every frame runs its first pass and then its own
+// count of later passes), so a request decodes to the same bits, iterations
+// and posteriors alone or in the mix.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -23,19 +34,31 @@
 #include <unordered_map>
 
 #include "ldpc_internal.h"
+#include "ldpc_launch.cuh"
 
 using namespace ldpc;
 
 namespace {
+
+constexpr int32_t kChunkPasses = 4;  // flooding passes between two admission points
 
 double now_ms() {
     using namespace std::chrono;
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
+// Where a frame's results go.
+struct Dest {
+    uint8_t *bits;  // [n]
+    float *post;    // [n] or null
+    int32_t *iters;
+    uint8_t *ok;
+};
+
 struct Request {
     int32_t code = 0;
     int32_t F = 0;
+    int32_t left = 0;  // frames not yet written out
     const float *llr = nullptr;
     uint8_t *bits = nullptr;
     int32_t *iters = nullptr;
@@ -45,23 +68,32 @@ struct Request {
     int status = 1;  // 1 queued, 2 running, 0 done, < 0 error
 };
 
-struct Slot;
-
 struct SlotCallback {
     ldpc_server *server;
     int slot;
 };
 
 struct Slot {
-    Workspace ws;
+    Workspace ws;                 // frame-interleaved state of the frame set
+    int32_t *base = nullptr;      // [cap] pass before each frame's own first pass
+    Dest *dest = nullptr;         // [2 cap] destination of each frame token
+    uint8_t *emitted = nullptr;   // [2 cap] token written out by the last chunk
+    const float **adm_src = nullptr;  // [cap] admission staging: LLR row of each new frame
+    int32_t *adm_token = nullptr;     // [cap] its token
+    Dest *adm_dest = nullptr;         // [cap] its destination
+    // pinned host mirrors
+    const float **h_src = nullptr;
+    int32_t *h_token = nullptr;
+    Dest *h_dest = nullptr;
+    uint8_t *h_emitted = nullptr;
+    int2 *h_count = nullptr;          // (moves, live frames) after the last chunk
     cudaStream_t stream = nullptr;
-    float *llr = nullptr;
-    uint8_t *bits = nullptr;
-    int32_t *iters = nullptr;
-    uint8_t *ok = nullptr;
-    float *post = nullptr;
-    bool busy = false;
-    std::vector<uint64_t> reqs;
+    int code = -1;                // code served, -1 when idle
+    int32_t t = 1;                // the slot's next later pass (never reset)
+    int32_t live = 0;             // live frames, packed at the front
+    bool in_flight = false, status_ready = false;
+    std::vector<uint64_t> token_req;     // request of each token (0 = free)
+    std::vector<int32_t> free_tokens;
     SlotCallback cb{};
 };
 
@@ -73,7 +105,9 @@ struct ldpc_server {
     ldpc_decode_opts_t opts{};
     float l_max = 20.0f;
     int32_t max_iter = 50;
-    int32_t max_batch = 1024;
+    int32_t max_batch = 1024;  // largest request
+    int32_t cap = 1024;        // frames of a slot
+    int32_t V = 4, group = 128;
     int64_t max_pending = 1 << 20;
     std::vector<Slot> slots;
     std::mutex mu;
@@ -91,119 +125,297 @@ struct ldpc_server {
 
 namespace {
 
-void CUDART_CB slot_done(void *arg) {
+// Interleave the LLR rows of n_new new frames into slots [a, a + count) (the
+// rest of that range is padding), and set their state: frame token, pass
+// base, not stopped, destination.
+__global__ void __launch_bounds__(256) ks_admit(float *__restrict__ lamT, int32_t n, int32_t Fp, int32_t a,
+                                                int32_t n_new, const float *const *__restrict__ src,
+                                                const int32_t *__restrict__ token, const Dest *__restrict__ adm_dest,
+                                                int32_t *__restrict__ slot_frame, int32_t *__restrict__ base,
+                                                uint32_t *__restrict__ done, Dest *__restrict__ dest,
+                                                uint8_t *__restrict__ emitted, int32_t t_base) {
+    pdl_wait();
+    __shared__ float tile[32][129];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t j0 = blockIdx.x * 128;
+    const int32_t i0 = blockIdx.y * 32;
+    for (int fi = warp; fi < 32; fi += 8) {
+        const int32_t i = i0 + fi;
+        const float *row = i < n_new ? src[i] : nullptr;
+        for (int q = lane; q < 128; q += 32) {
+            const int32_t j = j0 + q;
+            tile[fi][q] = (row && j < n) ? row[j] : 0.0f;
+        }
+    }
+    __syncthreads();
+    for (int q = warp; q < 128; q += 8) {
+        const int32_t j = j0 + q;
+        if (j < n) lamT[(size_t)j * Fp + a + i0 + lane] = tile[lane][q];
+    }
+    if (blockIdx.x == 0 && warp == 0) {
+        const int32_t i = i0 + lane, s = a + i;
+        const bool real = i < n_new;
+        slot_frame[s] = real ? token[i] : -1;
+        base[s] = t_base;
+        if (real) {
+            dest[token[i]] = adm_dest[i];
+            emitted[token[i]] = 0;
+        }
+        const uint32_t pad = __ballot_sync(0xffffffffu, !real);
+        if (lane == 0) done[s >> 5] = pad;  // s is a multiple of 32 here
+    }
+}
+
+// Results of the stopped frames that still hold a token: decisions (and
+// posteriors) from their APP columns, iterations and syndrome flag from their
+// stop record. CTA (x, y): 128 variables of 32 slots.
+__global__ void __launch_bounds__(256) ks_emit(const float *__restrict__ app, int32_t n, int32_t Fp,
+                                               const uint32_t *__restrict__ done, const uint32_t *__restrict__ status,
+                                               const int32_t *__restrict__ slot_frame,
+                                               const int32_t *__restrict__ stop_iter, const Dest *__restrict__ dest,
+                                               uint8_t *__restrict__ emitted) {
+    pdl_wait();
+    __shared__ float tile[32][129];
+    __shared__ int32_t s_tok[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t s0 = blockIdx.y * 32;
+    if (warp == 0) {
+        const int32_t s = s0 + lane;
+        const int32_t tok = frame_bit(done, s) ? slot_frame[s] : -1;
+        s_tok[lane] = tok;
+        if (blockIdx.x == 0 && tok >= 0) {
+            const Dest d = dest[tok];
+            const int32_t st = stop_iter[s];
+            const bool gave_up = *status != 0u;
+            *d.iters = gave_up ? -1 : (st & ~kStopFailed);
+            *d.ok = (gave_up || (st & kStopFailed)) ? 0 : 1;
+            emitted[tok] = 1;
+        }
+    }
+    __syncthreads();
+    if (!__syncthreads_or(s_tok[lane] >= 0)) return;
+    const int32_t j0 = blockIdx.x * 128;
+    for (int q = warp; q < 128; q += 8) {
+        const int32_t j = j0 + q;
+        tile[lane][q] = (j < n && s_tok[lane] >= 0) ? app[(size_t)j * Fp + s0 + lane] : 0.0f;
+    }
+    __syncthreads();
+    for (int fi = warp; fi < 32; fi += 8) {
+        const int32_t tok = s_tok[fi];
+        if (tok < 0) continue;
+        const Dest d = dest[tok];
+        for (int q = lane; q < 128; q += 32) {
+            const int32_t j = j0 + q;
+            if (j >= n) break;
+            const float x = tile[fi][q];
+            d.bits[j] = x > 0.0f ? 1 : 0;
+            if (d.post) d.post[j] = x;
+        }
+    }
+}
+
+void CUDART_CB chunk_done(void *arg) {
     auto *cb = static_cast<SlotCallback *>(arg);
     ldpc_server *s = cb->server;
     std::lock_guard<std::mutex> lock(s->mu);
     Slot &sl = s->slots[cb->slot];
-    const double t = now_ms();
-    for (uint64_t id : sl.reqs) {
-        auto it = s->reqs.find(id);
-        if (it == s->reqs.end()) continue;
-        it->second.status = 0;
-        it->second.t_done = t;
-        s->completed += 1;
-        s->frames_done += it->second.F;
-    }
-    sl.reqs.clear();
-    sl.busy = false;
-    s->cv_done.notify_all();
+    sl.in_flight = false;
+    sl.status_ready = true;
     s->cv_work.notify_all();
 }
 
-// Gather, decode and scatter one batch on a slot (no lock held).
-cudaError_t launch_batch(ldpc_server *s, int si, int32_t code, const std::vector<Request> &batch) {
+struct Admission {
+    int32_t a = 0, count = 0, n_new = 0;  // slot range [a, a + count) of n_new new frames
+};
+
+// Enqueue one chunk of a slot (no lock held): admission of the staged new
+// frames with their first pass, kChunkPasses later passes over the occupied
+// groups, results of the stopped frames, packing, the status copy and the
+// callback.
+cudaError_t enqueue_chunk(ldpc_server *s, int si, const Admission &adm, int32_t range) {
     Slot &sl = s->slots[si];
-    ldpc_code *c = s->codes[code];
-    const size_t n = (size_t)c->n;
+    ldpc_code *c = s->codes[sl.code];
+    const cudaStream_t st = sl.stream;
+    Workspace &w = sl.ws;
+    const int32_t Fp = s->cap;
+    const int32_t words = Fp / 32;
+    PassArgs a = make_pass_args(c, s->opts, s->l_max, Fp, s->V, Fp, w.lamT, w.app, w.r, w.done, w.done + words,
+                                w.unsat, w.stop_iter);
+    a.base = sl.base;
+    a.max_iter = s->max_iter;
+    a.unsat_ring = 1;
     cudaError_t e = cudaSuccess;
-    int32_t off = 0;
-    for (const Request &r : batch) {
-        if (e == cudaSuccess && n)
-            e = cudaMemcpyAsync(sl.llr + (size_t)off * n, r.llr, sizeof(float) * n * r.F, cudaMemcpyDeviceToDevice,
-                                sl.stream);
-        off += r.F;
+    auto passes = [&](int32_t f_begin, int32_t f_count, int32_t t) {
+        PassArgs at = a;
+        at.f_begin = f_begin;
+        at.f_count = f_count;
+        at.pass = t;
+        at.syndrome = t > 0 ? 1 : 0;  // later passes test every frame's previous decision
+        return with_msg_type(s->opts.msg_dtype, [&](auto tag) {
+            using M = typename decltype(tag)::type;
+            cudaError_t ee = cudaSuccess;
+            for (int b = 0; b < kNumCheckBins && ee == cudaSuccess; ++b) {
+                const int32_t count = c->bin_off[b + 1] - c->bin_off[b];
+                if (count == 0) continue;
+                at.bin_degree = c->bin_max_degree[b];
+                ee = launch_check_bin<M>(at, b, c->d.bin_checks + c->bin_off[b], c->d.bin_desc + c->bin_off[b], count,
+                                         st);
+            }
+            if (ee == cudaSuccess && c->n > 0) ee = launch_bit<M>(at, st);
+            return ee;
+        });
+    };
+    if (adm.n_new > 0) {
+        const size_t k = (size_t)adm.n_new;
+        if ((e = cudaMemcpyAsync(sl.adm_src, sl.h_src, sizeof(float *) * k, cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(sl.adm_token, sl.h_token, sizeof(int32_t) * k, cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(sl.adm_dest, sl.h_dest, sizeof(Dest) * k, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return e;
+        const dim3 grid((unsigned)std::max<int32_t>(1, (c->n + 127) / 128), (unsigned)(adm.count / 32), 1);
+        e = launch_pdl(ks_admit, grid, dim3(256), 0, st, w.lamT, c->n, Fp, adm.a, adm.n_new,
+                       static_cast<const float *const *>(sl.adm_src), static_cast<const int32_t *>(sl.adm_token),
+                       static_cast<const Dest *>(sl.adm_dest), w.slot_frame, sl.base, w.done, sl.dest, sl.emitted,
+                       sl.t - 1);
+        if (e == cudaSuccess) e = passes(adm.a, adm.count, 0);  // the new frames' first pass
+        if (e != cudaSuccess) return e;
     }
-    const int32_t F = off;
+    for (int32_t t = sl.t; t < sl.t + kChunkPasses && e == cudaSuccess; ++t) e = passes(0, range, t);
+    if (e != cudaSuccess) return e;
+    sl.t += kChunkPasses;
+    if (c->n > 0) {
+        const dim3 grid((unsigned)((c->n + 127) / 128), (unsigned)(range / 32), 1);
+        e = launch_pdl(ks_emit, grid, dim3(256), 0, st, static_cast<const float *>(w.app), c->n, Fp,
+                       static_cast<const uint32_t *>(w.done), static_cast<const uint32_t *>(w.done + words),
+                       static_cast<const int32_t *>(w.slot_frame), static_cast<const int32_t *>(w.stop_iter),
+                       static_cast<const Dest *>(sl.dest), sl.emitted);
+    }
+    if (e == cudaSuccess) e = launch_continuous_pack(a, s->opts.msg_dtype, s->group, w.slot_frame, w.moves, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_count, w.moves, sizeof(int2), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
-        e = enqueue_decode(c, sl.ws, sl.llr, F, s->max_iter, s->opts, s->l_max, sl.bits, sl.iters, sl.ok, sl.post,
-                           sl.stream);
-    off = 0;
-    for (const Request &r : batch) {
-        if (e == cudaSuccess && n)
-            e = cudaMemcpyAsync(r.bits, sl.bits + (size_t)off * n, n * r.F, cudaMemcpyDeviceToDevice, sl.stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(r.iters, sl.iters + off, sizeof(int32_t) * r.F, cudaMemcpyDeviceToDevice, sl.stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(r.ok, sl.ok + off, r.F, cudaMemcpyDeviceToDevice, sl.stream);
-        if (e == cudaSuccess && r.post && n)
-            e = cudaMemcpyAsync(r.post, sl.post + (size_t)off * n, sizeof(float) * n * r.F, cudaMemcpyDeviceToDevice,
-                                sl.stream);
-        off += r.F;
-    }
-    if (e == cudaSuccess) e = cudaLaunchHostFunc(sl.stream, slot_done, &sl.cb);
+        e = cudaMemcpyAsync(sl.h_emitted, sl.emitted, (size_t)2 * s->cap, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaLaunchHostFunc(st, chunk_done, &sl.cb);
     return e;
+}
+
+// After a chunk (lock held): frames written out complete their requests.
+void take_status(ldpc_server *s, Slot &sl) {
+    const double t = now_ms();
+    for (size_t tok = 0; tok < sl.token_req.size(); ++tok) {
+        const uint64_t id = sl.token_req[tok];
+        if (!id || !sl.h_emitted[tok]) continue;
+        sl.token_req[tok] = 0;
+        sl.free_tokens.push_back((int32_t)tok);
+        auto it = s->reqs.find(id);
+        if (it == s->reqs.end()) continue;
+        Request &r = it->second;
+        if (--r.left == 0 && r.status == 2) {
+            r.status = 0;
+            r.t_done = t;
+            s->completed += 1;
+            s->frames_done += r.F;
+        }
+    }
+    sl.live = sl.h_count->y;
+    s->cv_done.notify_all();
+}
+
+int oldest_code(ldpc_server *s) {
+    int code = -1;
+    double oldest = 0.0;
+    for (size_t ci = 0; ci < s->pending.size(); ++ci) {
+        if (s->pending[ci].empty()) continue;
+        const double t = s->reqs[s->pending[ci].front()].t_submit;
+        if (code < 0 || t < oldest) {
+            code = (int)ci;
+            oldest = t;
+        }
+    }
+    return code;
+}
+
+void fail_slot(ldpc_server *s, Slot &sl, int status) {
+    s->error = status;
+    for (uint64_t id : sl.token_req)
+        if (id && s->reqs.count(id)) s->reqs[id].status = status;
+    s->cv_done.notify_all();
 }
 
 void dispatcher(ldpc_server *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lock(s->mu);
     while (true) {
-        // a free slot and the code whose oldest request waits longest
-        int si = -1;
-        for (size_t i = 0; i < s->slots.size(); ++i)
-            if (!s->slots[i].busy) {
-                si = (int)i;
-                break;
+        bool launched = false, busy = false;
+        for (size_t si = 0; si < s->slots.size(); ++si) {
+            Slot &sl = s->slots[si];
+            if (sl.in_flight) {
+                busy = true;
+                continue;
             }
-        int code = -1;
-        double oldest = 0.0;
-        for (size_t ci = 0; ci < s->pending.size(); ++ci) {
-            if (s->pending[ci].empty()) continue;
-            double t = s->reqs[s->pending[ci].front()].t_submit;
-            if (code < 0 || t < oldest) {
-                code = (int)ci;
-                oldest = t;
+            if (sl.status_ready) {
+                take_status(s, sl);
+                sl.status_ready = false;
+            }
+            if (s->error != LDPC_OK) continue;
+            // an idle slot (or one whose code has run dry) takes the code
+            // with the oldest waiting request
+            if (sl.live == 0 && (sl.code < 0 || s->pending[sl.code].empty())) sl.code = oldest_code(s);
+            if (sl.code < 0) continue;
+            // admit whole requests of the slot's code into the free groups
+            const int32_t a = (sl.live + s->group - 1) / s->group * s->group;
+            Admission adm;
+            adm.a = a;
+            auto &q = s->pending[sl.code];
+            std::vector<uint64_t> taken;
+            while (!q.empty()) {
+                Request &r = s->reqs[q.front()];
+                if (a + adm.n_new + r.F > s->cap) break;
+                for (int32_t f = 0; f < r.F; ++f) {
+                    const int32_t i = adm.n_new + f;
+                    const int32_t tok = sl.free_tokens.back();
+                    sl.free_tokens.pop_back();
+                    sl.token_req[tok] = q.front();
+                    const size_t n = (size_t)s->codes[sl.code]->n;
+                    sl.h_src[i] = r.llr + (size_t)f * n;
+                    sl.h_token[i] = tok;
+                    sl.h_dest[i] = Dest{r.bits + (size_t)f * n, r.post ? r.post + (size_t)f * n : nullptr,
+                                        r.iters + f, r.ok + f};
+                }
+                adm.n_new += r.F;
+                r.status = 2;
+                r.left = r.F;
+                s->pending_frames -= r.F;
+                s->info_bits += (int64_t)r.F * (s->codes[sl.code]->n - s->codes[sl.code]->m);
+                taken.push_back(q.front());
+                q.pop_front();
+            }
+            if (sl.live == 0 && adm.n_new == 0) {
+                sl.code = -1;
+                continue;
+            }
+            if (adm.n_new > 0) s->batches += 1;
+            adm.count = (adm.n_new + s->group - 1) / s->group * s->group;
+            const int32_t range = adm.n_new > 0 ? a + adm.count : a;
+            sl.in_flight = true;
+            launched = true;
+            lock.unlock();
+            const cudaError_t e = enqueue_chunk(s, (int)si, adm, range);
+            lock.lock();
+            if (e != cudaSuccess) {
+                sl.in_flight = false;
+                fail_slot(s, sl, cuda_error(e, "ldpc_server: chunk launch"));
             }
         }
-        if (si < 0 || code < 0) {
-            bool idle = code < 0;
-            bool any_busy = false;
-            for (auto &sl : s->slots) any_busy |= sl.busy;
-            if (s->stop && idle && !any_busy) break;
-            s->cv_work.wait(lock);
-            continue;
+        if (launched) continue;
+        if (s->stop && !busy) {
+            bool queued = false;
+            for (auto &q : s->pending) queued |= !q.empty();
+            bool running = false;
+            for (auto &sl : s->slots) running |= sl.live > 0;
+            if ((!queued && !running) || s->error != LDPC_OK) break;
         }
-        // take requests of that code, oldest first, up to the batch size
-        std::vector<Request> batch;
-        std::vector<uint64_t> ids;
-        int32_t frames = 0;
-        auto &q = s->pending[code];
-        while (!q.empty()) {
-            Request &r = s->reqs[q.front()];
-            if (!ids.empty() && frames + r.F > s->max_batch) break;
-            frames += r.F;
-            r.status = 2;
-            ids.push_back(q.front());
-            batch.push_back(r);
-            q.pop_front();
-        }
-        s->pending_frames -= frames;
-        Slot &sl = s->slots[si];
-        sl.busy = true;
-        sl.reqs = ids;
-        s->batches += 1;
-        s->info_bits += (int64_t)frames * (s->codes[code]->n - s->codes[code]->m);
-        lock.unlock();
-        cudaError_t e = launch_batch(s, si, code, batch);
-        lock.lock();
-        if (e != cudaSuccess) {
-            s->error = cuda_error(e, "ldpc_server: batch launch");
-            for (uint64_t id : ids) s->reqs[id].status = LDPC_ECUDA;
-            sl.reqs.clear();
-            sl.busy = false;
-            s->cv_done.notify_all();
-        }
+        s->cv_work.wait(lock);
     }
 }
 
@@ -222,15 +434,56 @@ void server_free(ldpc_server *s) {
     for (auto &sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         free_workspace(sl.ws);
-        cudaFree(sl.llr);
-        cudaFree(sl.bits);
-        cudaFree(sl.iters);
-        cudaFree(sl.ok);
-        cudaFree(sl.post);
+        cudaFree(sl.base);
+        cudaFree(sl.dest);
+        cudaFree(sl.emitted);
+        cudaFree(sl.adm_src);
+        cudaFree(sl.adm_token);
+        cudaFree(sl.adm_dest);
+        cudaFreeHost(sl.h_src);
+        cudaFreeHost(sl.h_token);
+        cudaFreeHost(sl.h_dest);
+        cudaFreeHost(sl.h_emitted);
+        cudaFreeHost(sl.h_count);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
     if (prev >= 0) cudaSetDevice(prev);
     delete s;
+}
+
+// Device and pinned buffers of one slot, its initial state (no frame, every
+// slot stopped, syndrome rows clear).
+cudaError_t make_slot(ldpc_server *s, Slot &sl, int32_t n_max, int64_t e_max, int mb, int *st) {
+    const int32_t cap = s->cap;
+    cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ws.last_use, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    *st = workspace_reserve(sl.ws, n_max, e_max, cap, 1, mb);  // two syndrome rows
+    if (*st != LDPC_OK) return cudaSuccess;
+    if ((e = cudaMalloc(&sl.base, sizeof(int32_t) * cap)) != cudaSuccess ||
+        (e = cudaMalloc(&sl.dest, sizeof(Dest) * 2 * cap)) != cudaSuccess ||
+        (e = cudaMalloc(&sl.emitted, (size_t)2 * cap)) != cudaSuccess ||
+        (e = cudaMalloc(&sl.adm_src, sizeof(float *) * cap)) != cudaSuccess ||
+        (e = cudaMalloc(&sl.adm_token, sizeof(int32_t) * cap)) != cudaSuccess ||
+        (e = cudaMalloc(&sl.adm_dest, sizeof(Dest) * cap)) != cudaSuccess ||
+        (e = cudaMallocHost(&sl.h_src, sizeof(float *) * cap)) != cudaSuccess ||
+        (e = cudaMallocHost(&sl.h_token, sizeof(int32_t) * cap)) != cudaSuccess ||
+        (e = cudaMallocHost(&sl.h_dest, sizeof(Dest) * cap)) != cudaSuccess ||
+        (e = cudaMallocHost(&sl.h_emitted, (size_t)2 * cap)) != cudaSuccess ||
+        (e = cudaMallocHost(&sl.h_count, sizeof(int2))) != cudaSuccess)
+        return e;
+    const int32_t words = cap / 32;
+    if ((e = cudaMemset(sl.ws.done, 0xFF, sizeof(uint32_t) * words)) != cudaSuccess ||
+        (e = cudaMemset(sl.ws.done + words, 0, sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMemset(sl.ws.unsat, 0, sizeof(uint32_t) * 2 * words)) != cudaSuccess ||
+        (e = cudaMemset(sl.ws.slot_frame, 0xFF, sizeof(int32_t) * cap)) != cudaSuccess ||
+        (e = cudaMemset(sl.base, 0, sizeof(int32_t) * cap)) != cudaSuccess ||
+        (e = cudaMemset(sl.emitted, 0, (size_t)2 * cap)) != cudaSuccess)
+        return e;
+    std::memset(sl.h_emitted, 0, (size_t)2 * cap);
+    sl.token_req.assign((size_t)2 * cap, 0);
+    for (int32_t tok = 2 * cap - 1; tok >= 0; --tok) sl.free_tokens.push_back(tok);
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -274,6 +527,10 @@ extern "C" int ldpc_server_create(int32_t n_codes, ldpc_code_t *const *codes, co
     s->l_max = l_max;
     s->max_iter = max_iter;
     s->max_batch = max_batch;
+    // a slot of max_batch frames in whole groups of 32 V (the frame layout of
+    // ldpc_decode for that batch size)
+    frames_layout(max_batch, 0, &s->V, &s->cap);
+    s->group = 32 * s->V;
     s->max_pending = o.max_pending_frames > 0 ? o.max_pending_frames : (1 << 20);
     s->pending.resize(n_codes);
 
@@ -281,10 +538,9 @@ extern "C" int ldpc_server_create(int32_t n_codes, ldpc_code_t *const *codes, co
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
     // slots: as many as the memory budget allows (at least one)
-    const int32_t Fp = (max_batch + 255) / 256 * 256;
+    const int32_t Fp = s->cap;
     const int mb = msg_bytes(d.msg_dtype);
-    const int64_t per_slot = (int64_t)Fp * (8 * (int64_t)n_max + mb * e_max) +
-                             (int64_t)max_batch * (5 * (int64_t)n_max + 5) + (int64_t)(max_iter + 1) * Fp / 8;
+    const int64_t per_slot = (int64_t)Fp * (8 * (int64_t)n_max + mb * e_max + 64) + 2 * (int64_t)Fp / 8;
     int64_t budget = o.memory_budget;
     if (budget <= 0) {
         size_t free_b = 0, total_b = 0;
@@ -297,16 +553,8 @@ extern "C" int ldpc_server_create(int32_t n_codes, ldpc_code_t *const *codes, co
     cudaError_t e = cudaSuccess;
     int st = LDPC_OK;
     for (int32_t i = 0; i < n_slots && e == cudaSuccess && st == LDPC_OK; ++i) {
-        Slot &sl = s->slots[i];
-        sl.cb = SlotCallback{s, i};
-        e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ws.last_use, cudaEventDisableTiming);
-        if (e == cudaSuccess) st = workspace_reserve(sl.ws, n_max, e_max, Fp, max_iter, mb);
-        if (e == cudaSuccess && st == LDPC_OK) e = cudaMalloc(&sl.llr, sizeof(float) * (size_t)max_batch * n_max);
-        if (e == cudaSuccess && st == LDPC_OK) e = cudaMalloc(&sl.bits, (size_t)max_batch * n_max);
-        if (e == cudaSuccess && st == LDPC_OK) e = cudaMalloc(&sl.iters, sizeof(int32_t) * max_batch);
-        if (e == cudaSuccess && st == LDPC_OK) e = cudaMalloc(&sl.ok, (size_t)max_batch);
-        if (e == cudaSuccess && st == LDPC_OK) e = cudaMalloc(&sl.post, sizeof(float) * (size_t)max_batch * n_max);
+        s->slots[i].cb = SlotCallback{s, i};
+        e = make_slot(s, s->slots[i], n_max, e_max, mb, &st);
     }
     if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess || st != LDPC_OK) {

@@ -93,3 +93,36 @@ def test_fer_of_every_format_within_the_oracle_interval(ldpc, point):
     print(f"n64800 {point['ebn0_db']} dB, {n} frames: oracle {len(ref)} errors (FER {len(ref) / n:.4g}, "
           f"95% [{lo:.4g}, {hi:.4g}]); " + "; ".join(f"{m} {v[0]} ({v[1]:.4g})" for m, v in rows.items() if isinstance(v, tuple))
           + f"; FP32 and oracle differ on {rows['f32_vs_oracle_frames']} frames")
+
+
+@pytest.mark.parametrize("point", [p for p in points() if p["frames"] >= 1000][:1], ids=lambda p: f"{p['ebn0_db']}dB")
+def test_served_fp16_fer_within_the_oracle_interval(ldpc, point):
+    """The same frames decoded through the decode server (FP16 messages,
+    requests of 1-512 frames, log-uniform, all submitted at once so that
+    frames are admitted into running slots): the FER lies inside the FP64
+    oracle's 95% Wilson interval, and every request equals the direct FP16
+    decode of its frames."""
+    code = I.large_code_n64800()
+    h = ldpc.code_from_inputs(code)
+    n = point["frames"]
+    ref = np.array(point["error_frames"], dtype=np.int64)
+    lo, hi = wilson(len(ref), n)
+    llr = ldpc.ldpc_gen_awgn(1, 0, n, code.n, I.sigma2_from_ebn0(point["ebn0_db"], code.rate))
+    rng = np.random.default_rng(3)
+    cuts, f = [], 0
+    while f < n:
+        k = int(min(n - f, max(1, np.floor(np.exp(rng.uniform(0.0, np.log(513)))))))
+        cuts.append((f, k))
+        f += k
+    srv = ldpc.ldpc_server_create([h], max_batch_frames=1024, max_slots=4, msg_dtype="f16", max_iter=50)
+    subs = [ldpc.ldpc_server_submit(srv, 0, llr[f0:f0 + k]) for f0, k in cuts]
+    for rid, _ in subs:
+        ldpc.ldpc_server_wait(srv, rid, timeout_ms=300000)
+    srv.close()
+    bad = np.concatenate([f0 + np.flatnonzero(o["bits"].any(dim=1).cpu().numpy()) for (f0, k), (_, o) in zip(cuts, subs)])
+    fer = len(bad) / n
+    assert lo <= fer <= hi, (fer, (lo, hi))
+    direct = gpu_frame_errors(ldpc, h, code, point["ebn0_db"], n, "f16")
+    np.testing.assert_array_equal(np.sort(bad), np.sort(direct))
+    print(f"served FP16 at {point['ebn0_db']} dB: {len(bad)} of {n} frames in error (oracle {len(ref)}, "
+          f"95% [{lo:.4g}, {hi:.4g}]), {len(cuts)} requests")
