@@ -1298,11 +1298,14 @@ __global__ void __launch_bounds__(kThreads) k_check_prod(PassArgs a, const int32
         uint32_t sb[V], z[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) sb[v] = z[v] = 0u;
+        // the check's column indices in one warp load (d <= 32), then each
+        // input's row loads need no dependent index load
+        const int jl = lane < d ? a.col_idx[b + lane] : 0;
         // inputs: t and sign bits (input k at bit d - 1 - k)
 #pragma unroll 4
         for (int k = 0; k < d; ++k) {
             float av[V], rv[V];
-            load_v_hint<V, float>(qsrc + (size_t)a.col_idx[b + k] * Fp + f0, av, pol_keep);
+            load_v_hint<V, float>(qsrc + (size_t)__shfl_sync(kFull, jl, k) * Fp + f0, av, pol_keep);
             if (!first) load_v_hint<V, M>(r + (size_t)(b + k) * Fp + f0, rv, pol_stream);
             float x[V];
 #pragma unroll

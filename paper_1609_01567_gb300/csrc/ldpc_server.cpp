@@ -41,6 +41,7 @@ using namespace ldpc;
 namespace {
 
 constexpr int32_t kChunkPasses = 4;  // flooding passes between two admission points
+constexpr double kFairMs = 20.0;     // waiting-time lead that makes a busy slot drain for another code
 
 double now_ms() {
     using namespace std::chrono;
@@ -92,6 +93,7 @@ struct Slot {
     int32_t t = 1;                // the slot's next later pass (never reset)
     int32_t live = 0;             // live frames, packed at the front
     bool in_flight = false, status_ready = false;
+    bool draining = false;        // admits nothing until its frames are done
     std::vector<uint64_t> token_req;     // request of each token (0 = free)
     std::vector<int32_t> free_tokens;
     SlotCallback cb{};
@@ -360,15 +362,31 @@ void dispatcher(ldpc_server *s) {
             if (s->error != LDPC_OK) continue;
             // an idle slot (or one whose code has run dry) takes the code
             // with the oldest waiting request
-            if (sl.live == 0 && (sl.code < 0 || s->pending[sl.code].empty())) sl.code = oldest_code(s);
+            if (sl.live == 0 && (sl.code < 0 || s->pending[sl.code].empty() || sl.draining)) {
+                sl.code = oldest_code(s);
+                sl.draining = false;
+            }
             if (sl.code < 0) continue;
-            // admit whole requests of the slot's code into the free groups
+            // admit whole requests of the slot's code into the free groups,
+            // unless an older request of a code no slot serves is waiting:
+            // then this slot drains and takes that code when it frees
             const int32_t a = (sl.live + s->group - 1) / s->group * s->group;
             Admission adm;
             adm.a = a;
             auto &q = s->pending[sl.code];
             std::vector<uint64_t> taken;
-            while (!q.empty()) {
+            bool drain = false;
+            const int oc = oldest_code(s);
+            if (sl.draining) {
+                drain = true;
+            } else if (oc >= 0 && oc != sl.code && !q.empty()) {
+                bool taken_care = false;  // served, or another slot drains for it already
+                for (auto &other : s->slots) taken_care |= other.code == oc || other.draining;
+                drain = !taken_care &&
+                        s->reqs[q.front()].t_submit - s->reqs[s->pending[oc].front()].t_submit > kFairMs;
+            }
+            sl.draining = drain;
+            while (!q.empty() && !drain) {
                 Request &r = s->reqs[q.front()];
                 if (a + adm.n_new + r.F > s->cap) break;
                 for (int32_t f = 0; f < r.F; ++f) {
@@ -392,6 +410,7 @@ void dispatcher(ldpc_server *s) {
             }
             if (sl.live == 0 && adm.n_new == 0) {
                 sl.code = -1;
+                sl.draining = false;
                 continue;
             }
             if (adm.n_new > 0) s->batches += 1;
