@@ -166,14 +166,18 @@ typedef struct {
                            bit-node kernel (1, 2, 4 or 8); 0 picks by batch
                            size                                              */
     int32_t check_schedule;  /* tuning: check-node kernel schedule for checks
-                           of degree <= 16; 0 = auto, 1 = inputs loaded
-                           straight from global memory, 2 = rows staged
-                           through a shared-memory ring by bulk copies (when
-                           the batch allows: frame groups of 64 or 128).
-                           Wider checks have kernels chosen by the code: the
-                           register kernel, the any-degree kernel (a code
-                           with >= 2048 checks of degree 17-32) or one CTA
-                           per check (degree > 32)                           */
+                           of degree <= 16, and of degree 17-18 in a code
+                           with >= 2048 checks of degree 17-32 that are all
+                           of degree <= 18; 0 = auto, 1 = inputs loaded
+                           straight from global memory (degree 17-18: the
+                           staged product-form kernel), 2 = rows staged
+                           through a shared-memory ring by tensor copies
+                           (when the batch allows: frame groups of 64 or
+                           128). Other wide checks have kernels chosen by the
+                           code: the register kernel, the staged product-form
+                           or any-degree kernel (a code with >= 2048 checks
+                           of degree 17-32) or one CTA per check (degree >
+                           32)                                               */
     int32_t streams;    /* tuning: 1 = all passes on `stream`; 2 = the two
                            halves of the batch on two library streams, half a
                            pass apart, so that the check pass of one half

@@ -1077,8 +1077,17 @@ struct BulkShape {
     static constexpr int kSmem = kBarBytes + (kThreads / 32) * S * PipeShape<D, V, M>::kStage;
 };
 
+// Three CTAs per SM for int8 messages and checks of degree <= 8, whose ring
+// is small enough for that: the register budget it sets (85 a thread) keeps
+// the syndrome form at 24 warps per SM. For 16-bit messages the same bound
+// measured no faster, and wider checks would spill under it.
+template <int D, typename M>
+constexpr int bulk_min_ctas() {
+    return sizeof(M) == 1 && D <= 8 ? 3 : 1;
+}
+
 template <int D, int V, typename M, int S, int MODE, int RULE>
-__global__ void __launch_bounds__(kThreads) k_check_bulk(const __grid_constant__ PassArgs a,
+__global__ void __launch_bounds__(kThreads, bulk_min_ctas<D, M>()) k_check_bulk(const __grid_constant__ PassArgs a,
                                                          const int2 *__restrict__ desc, int32_t count) {
     pdl_wait();
     using P = PipeShape<D, V, M>;
@@ -2036,14 +2045,19 @@ static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *
             return launch_bulk<16, 2, M, 2, RULE>(a, desc, count, s);
         }
     }
-    // Degrees 17-32 in a code with many such checks: the any-degree kernel
-    // (phi sums, constant state per frame, inputs read twice) at four frames
-    // per lane; the register kernel pads every check to 32 slots at one frame
-    // per lane (n = 64800 rate 5/6, 256 frames, 10 iterations: 5.28 -> 2.75
-    // ms). A few such checks (a short high-rate code) keep the register
-    // kernel, whose loads of one check are all in flight at once. The choice
-    // depends on the code only, never on the batch, so a frame's result does
-    // not depend on the frames decoded with it.
+    // Degrees 17-32 in a code with many such checks. Up to degree 18 (the
+    // rate-5/6 codes), batches of 64-frame groups run the pipelined kernel
+    // with 18 slots, its rows brought in by tensor copies; other batches and
+    // wider checks run the staged product-form kernel (the same operations in
+    // the same order, so a frame's result does not depend on which one ran),
+    // min-sum the any-degree kernel. The register kernel, which pads every
+    // check to 32 slots at one frame per lane, took 5.28 ms on n = 64800 rate
+    // 5/6 (256 frames, 10 iterations); it stays for a code with few such
+    // checks (a short high-rate code), whose loads of one check are all in
+    // flight at once. The choice depends on the code, never on the batch.
+    if (a.check_schedule != 1 && bin == 4 && a.bin_degree <= 18 && count >= kWideBinAnyKernel &&
+        a.f_count % 64 == 0 && a.f_begin % 64 == 0)
+        return launch_bulk<18, 2, M, 2, RULE>(a, desc, count, s);
     if (bin == 4 && count >= kWideBinAnyKernel && RULE == 0) {
         if (a.V >= 2 && a.f_count % 64 == 0 && a.f_begin % 64 == 0) return launch_prod<2, M>(a, checks, count, s);
         return launch_prod<1, M>(a, checks, count, s);

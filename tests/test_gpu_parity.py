@@ -299,7 +299,7 @@ def n64800_r56():
 @pytest.mark.parametrize("rule", ["sum_product", "min_sum"])
 def test_high_rate_checks_lock_step(ldpc, oracle_mod, n64800_r56, rule):
     """Checks of degree 17-18 in a code with many of them run in the
-    any-degree kernel: three passes at 256 frames, sampled frames against the
+    pipelined kernel with 18 slots: three passes at 256 frames, sampled frames against the
     oracle from the GPU's own messages (sum-product and offset/normalised
     min-sum)."""
     code, llr = n64800_r56
@@ -319,9 +319,12 @@ def test_high_rate_checks_lock_step(ldpc, oracle_mod, n64800_r56, rule):
 
 
 def test_high_rate_results_do_not_depend_on_layout_or_batch(ldpc, n64800_r56):
-    """The any-degree kernel's results are the same at four, two and one
+    """The degree-18 checks' results are the same at four, two and one
     frames per lane, on one or two streams, and for a frame decoded alone or
-    in a batch of 256."""
+    in a batch of 256. Batches of 64-frame groups run the pipelined kernel
+    with 18 slots; a batch of 20 frames (one 32-frame group) runs the staged
+    product-form kernel at one frame per lane, the same operations in the
+    same order, so its frames equal the batch's bit for bit."""
     code, llr = n64800_r56
     h = ldpc.code_from_inputs(code)
     base = gpu_decode(ldpc, h, llr, 8, early_exit=False)
@@ -329,9 +332,10 @@ def test_high_rate_results_do_not_depend_on_layout_or_batch(ldpc, n64800_r56):
         other = gpu_decode(ldpc, h, llr, 8, early_exit=False, **kw)
         for k in ("bits", "iters", "ok", "post"):
             np.testing.assert_array_equal(other[k], base[k], err_msg=f"{kw} {k}")
-    part = gpu_decode(ldpc, h, llr[:37], 8, early_exit=False)
-    for k in ("bits", "iters", "ok", "post"):
-        np.testing.assert_array_equal(part[k], base[k][:37], err_msg=f"37 frames {k}")
+    for nf in (37, 20):
+        part = gpu_decode(ldpc, h, llr[:nf], 8, early_exit=False)
+        for k in ("bits", "iters", "ok", "post"):
+            np.testing.assert_array_equal(part[k], base[k][:nf], err_msg=f"{nf} frames {k}")
 
 
 @pytest.mark.parametrize("rule", ["sum_product", "min_sum"])
