@@ -244,11 +244,13 @@ constexpr int kPlanThreads = 1024;  // one thread per 32-slot word: Fp <= 32768
 
 // moves[0] = (M, L); moves[1 + i] = (source, destination) slot of move i.
 // `always`: pack the live frames to the front even when no group is freed.
+// `narrow` (> 0): also pack when at most `narrow` frames live and one of them
+// sits at or beyond slot `narrow`, so that a narrow tail finds them all below.
 // `release` (continuous decoding): stopped slots, whose results have been
 // written out, give up their frame (slot_frame = -1).
 __global__ void __launch_bounds__(kPlanThreads) k_compact_plan(const uint32_t *__restrict__ done, int32_t Fp,
                                                                int32_t group, int2 *__restrict__ moves, int32_t always,
-                                                               int32_t *__restrict__ release) {
+                                                               int32_t narrow, int32_t *__restrict__ release) {
     pdl_wait();
     __shared__ int32_t s_a[kPlanThreads], s_b[kPlanThreads];
     const int t = threadIdx.x;
@@ -275,8 +277,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_compact_plan(const uint32_t *_
     int32_t busy = 0;
     for (int g = 0; g < (W + wpg - 1) / wpg; ++g) busy += s_b[g];
     const int32_t after = (L + group - 1) / group;
-    __syncthreads();
-    if (after >= busy && !always) {
+    const bool spread = __syncthreads_or(narrow > 0 && L <= narrow && t < W && t * 32 >= narrow && live != 0u);
+    if (after >= busy && !always && !spread) {
         if (t == 0) moves[0] = make_int2(0, L);
         return;
     }
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(256) k_compact_move(float *__restrict__ lamT, 
 template <typename M>
 static cudaError_t launch_pack(const PassArgs &a, int32_t group, int32_t *slot_frame, int2 *moves, cudaStream_t s) {
     cudaError_t e = launch_pdl(k_compact_plan, dim3(1), dim3(kPlanThreads), 0, s, a.done, a.Fp, group, moves, 1,
-                               slot_frame);
+                               0, slot_frame);
     if (e == cudaSuccess)
         e = launch_pdl(k_compact_move<M>, dim3((unsigned)std::max(1, a.sm_count) * 8), dim3(256), 0, s,
                        const_cast<float *>(a.lamT), a.app, reinterpret_cast<M *>(a.r), a.n, a.E, a.Fp,
@@ -561,6 +563,8 @@ PassArgs make_pass_args(const ldpc_code *c, const ldpc_decode_opts_t &o, float l
     a.ms_beta = o.rule_beta;
     a.ms_table = o.check_rule == LDPC_RULE_MIN_SUM_ADAPTIVE ? c->d.ms_table : nullptr;
     a.giveup_cta = -1;
+    a.gate = nullptr;
+    a.gate_narrow = 0;
     a.base = nullptr;
     a.max_iter = 0;
     a.unsat_ring = 0;
@@ -640,6 +644,15 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     // Segments of passes; between two segments the streams join and the
     // compaction kernels run on `s`.
     static constexpr int32_t kCuts[] = {6, 10, 15, 21, 28, 36, 46, 60, 80};
+    // Narrow tail (four frames per lane, two 128-frame halves or more): from
+    // the segment after pass kNarrowFrom on, stream 0 launches every pass in
+    // two forms, its 128-frame groups and one 64-frame group at two frames
+    // per lane, and the device runs the second once the last compaction left
+    // at most 64 live frames (then all in slots [0, 64); the other groups
+    // return at once). One pass of 64 frames costs about half the 128-frame
+    // pass that the last few frames of a batch would otherwise keep running.
+    static constexpr int32_t kNarrowFrom = 15;
+    const bool narrow = compact && V == 4 && nstreams == 2 && ntiles == 2 && Fp % 256 == 0;
     std::vector<int32_t> bounds{0};
     if (compact)
         for (int32_t t : kCuts)
@@ -657,29 +670,45 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
             PassArgs at = a;
             at.f_begin = ti * tile;
             at.f_count = tile;
+            // the narrow form of stream 0's passes in this segment
+            const bool two_forms = narrow && ti == 0 && t0 >= kNarrowFrom;
+            PassArgs an = at;
+            if (two_forms) {
+                at.gate = an.gate = w.moves;
+                an.gate_narrow = 1;
+                an.V = 2;
+                an.f_begin = 0;
+                an.f_count = kNarrowFrames;
+            }
             Launcher Lh{c, hs[h], per_kernel};
             for (int32_t t = t0; t < t1; ++t) {
-                at.pass = t;
-                at.syndrome = (t > 0 && at.early_exit) ? 1 : 0;
-                at.dec = t == max_iter ? w.dec : nullptr;
+                at.pass = an.pass = t;
+                at.syndrome = an.syndrome = (t > 0 && at.early_exit) ? 1 : 0;
+                at.dec = an.dec = t == max_iter ? w.dec : nullptr;
                 at.giveup_cta = (t == 1 && ti == 0) ? giveup : -1;
-                for (int b = 0; b < kNumCheckBins; ++b) {
-                    int32_t count = c->bin_off[b + 1] - c->bin_off[b];
-                    if (count == 0) continue;
-                    at.bin_degree = c->bin_max_degree[b];
-                    e = Lh(LDPC_K_CHECK, 1, [&] {
-                        return launch_check_bin<M>(at, b, c->d.bin_checks + c->bin_off[b],
-                                                   c->d.bin_desc + c->bin_off[b], count, hs[h]);
-                    });
-                    if (e != cudaSuccess) return e;
+                for (int form = 0; form < (two_forms ? 2 : 1); ++form) {
+                    PassArgs &ap = form == 0 ? at : an;
+                    for (int b = 0; b < kNumCheckBins; ++b) {
+                        int32_t count = c->bin_off[b + 1] - c->bin_off[b];
+                        if (count == 0) continue;
+                        ap.bin_degree = c->bin_max_degree[b];
+                        e = Lh(LDPC_K_CHECK, 1, [&] {
+                            return launch_check_bin<M>(ap, b, c->d.bin_checks + c->bin_off[b],
+                                                       c->d.bin_desc + c->bin_off[b], count, hs[h]);
+                        });
+                        if (e != cudaSuccess) return e;
+                    }
                 }
                 if (nstreams == 2 && ti == 0 && t == t0) {
                     if ((e = cudaEventRecord(w.phase, hs[0])) != cudaSuccess) return e;
                     if ((e = cudaStreamWaitEvent(hs[1], w.phase, 0)) != cudaSuccess) return e;
                 }
                 if (c->n > 0) {
-                    e = Lh(LDPC_K_BIT, c->wide_vars.empty() ? 1 : 2, [&] { return launch_bit<M>(at, hs[h]); });
-                    if (e != cudaSuccess) return e;
+                    for (int form = 0; form < (two_forms ? 2 : 1); ++form) {
+                        const PassArgs &ap = form == 0 ? at : an;
+                        e = Lh(LDPC_K_BIT, c->wide_vars.empty() ? 1 : 2, [&] { return launch_bit<M>(ap, hs[h]); });
+                        if (e != cudaSuccess) return e;
+                    }
                 }
             }
         }
@@ -692,7 +721,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
         if (sg + 2 < bounds.size()) {
             e = L(LDPC_K_OTHER, 3, [&] {
                 cudaError_t ee = launch_pdl(k_compact_plan, dim3(1), dim3(kPlanThreads), 0, s, w.done, Fp, group,
-                                            w.moves, 0, static_cast<int32_t *>(nullptr));
+                                            w.moves, 0, narrow ? kNarrowFrames : 0, static_cast<int32_t *>(nullptr));
                 const FrameResults fr{w.done, a.status, w.stop_iter, nullptr, F, max_iter, iters, ok, w.slot_frame};
                 if (ee == cudaSuccess)
                     ee = launch_pdl(k_compact_emit, dim3((unsigned)((c->n + kFinVars - 1) / kFinVars),

@@ -33,6 +33,7 @@ constexpr int kBinMaxDegree[kNumCheckBins] = {4, 6, 8, 16, 32, INT32_MAX};
 constexpr int kMaxRegisterDegree = 32;
 
 constexpr int kThreads = 256;  // threads per CTA of the pass kernels (8 warps)
+constexpr int32_t kNarrowFrames = 64;  // frames of an early-exit decode's narrow tail group
 // checks of degree 17-32 in one code from which the any-degree kernel serves them
 constexpr int32_t kWideBinAnyKernel = 2048;
 
@@ -138,6 +139,14 @@ struct PassArgs {
     int32_t n_wide_vars;
     int32_t giveup_cta;  // test hook (ldpc_debug_giveup): this CTA of the launch treats its first
                          // completed bounded wait as run out; -1 = off
+    // Early-exit tail: once a compaction has left at most kNarrowFrames live
+    // frames (all in the first slots), they run as one group of two frames
+    // per lane instead of a group of four. Both forms of a pass are launched
+    // and the device picks one: with gate set, the kernel runs only when
+    // (live frames <= kNarrowFrames) equals gate_narrow; gate->y holds the
+    // live count the last compaction left. Null gate: always runs.
+    const int2 *gate;
+    int32_t gate_narrow;
     // Tensor maps of the pipelined check kernel, filled by its launcher: the
     // rows the check inputs are read from (lamT on the first pass, else app;
     // float, box {32 V frames, 1 row}, gathered four rows at a time) and the
@@ -145,6 +154,13 @@ struct PassArgs {
     CUtensorMap tm_q;
     CUtensorMap tm_r;
 };
+
+// A pass kernel whose form the device did not pick for this pass returns at
+// once (after its programmatic wait, so the compaction's count is visible).
+__device__ __forceinline__ bool gated_off(const PassArgs &a) {
+    if (a.gate == nullptr) return false;
+    return (a.gate->y <= kNarrowFrames) != (a.gate_narrow != 0);
+}
 
 // A 2-D tensor map (TMA descriptor) over a row-major buffer of `rows` rows
 // of `cols` elements (CUtensorMapDataType dtype), rows `row_bytes` apart,

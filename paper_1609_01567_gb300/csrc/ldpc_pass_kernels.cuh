@@ -948,6 +948,7 @@ template <int D, int V, typename M, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_reg(PassArgs a, const int32_t *__restrict__ checks,
                                                         int32_t count) {
     pdl_wait();
+    if (gated_off(a)) return;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
@@ -1077,19 +1078,22 @@ struct BulkShape {
     static constexpr int kSmem = kBarBytes + (kThreads / 32) * S * PipeShape<D, V, M>::kStage;
 };
 
-// Three CTAs per SM for int8 messages and checks of degree <= 8, whose ring
-// is small enough for that: the register budget it sets (85 a thread) keeps
-// the syndrome form at 24 warps per SM. For 16-bit messages the same bound
-// measured no faster, and wider checks would spill under it.
-template <int D, typename M>
+// CTAs per SM the register budget is set for. Three for int8 messages and
+// checks of degree <= 8, whose ring is small enough for that (85 registers a
+// thread; for 16-bit messages the same bound measured no faster, and wider
+// checks would spill under it). Two for the syndrome form of the other
+// narrow bins, which would otherwise take 136 registers and run one CTA of
+// 8 warps per SM.
+template <int D, typename M, int MODE>
 constexpr int bulk_min_ctas() {
-    return sizeof(M) == 1 && D <= 8 ? 3 : 1;
+    return D > 8 ? 1 : (sizeof(M) == 1 ? 3 : (MODE == 2 ? 2 : 1));
 }
 
 template <int D, int V, typename M, int S, int MODE, int RULE>
-__global__ void __launch_bounds__(kThreads, bulk_min_ctas<D, M>()) k_check_bulk(const __grid_constant__ PassArgs a,
+__global__ void __launch_bounds__(kThreads, bulk_min_ctas<D, M, MODE>()) k_check_bulk(const __grid_constant__ PassArgs a,
                                                          const int2 *__restrict__ desc, int32_t count) {
     pdl_wait();
+    if (gated_off(a)) return;
     using P = PipeShape<D, V, M>;
     using B = BulkShape<D, V, M, S>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1266,6 +1270,7 @@ __global__ void __launch_bounds__(kThreads) k_check_prod(PassArgs a, const int32
                                                          int32_t count) {
     static_assert(V == 1 || V == 2, "one or two frames per lane");
     pdl_wait();
+    if (gated_off(a)) return;
     extern __shared__ __align__(128) unsigned char smem[];
     using T = typename std::conditional<V == 1, float, float2>::type;
     const int lane = threadIdx.x & 31;
@@ -1383,6 +1388,7 @@ template <int V, typename M, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_any(PassArgs a, const int32_t *__restrict__ checks,
                                                         int32_t count) {
     pdl_wait();
+    if (gated_off(a)) return;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
@@ -1537,6 +1543,7 @@ template <int V, typename M, int RULE>
 __global__ void __launch_bounds__(kThreads) k_check_wide(PassArgs a, const int32_t *__restrict__ checks,
                                                          int32_t count) {
     pdl_wait();
+    if (gated_off(a)) return;
     constexpr int W = kThreads / 32;
     __shared__ float s_hi[W][32 * V], s_lo[W][32 * V];
     __shared__ int s_idx[W][32 * V];
@@ -1710,6 +1717,7 @@ __global__ void __launch_bounds__(kThreads) k_check_wide(PassArgs a, const int32
 template <int V, typename M>
 __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
     pdl_wait();
+    if (gated_off(a)) return;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
@@ -1797,6 +1805,7 @@ __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
 template <int V, typename M>
 __global__ void __launch_bounds__(kThreads) k_bit_wide(PassArgs a) {
     pdl_wait();
+    if (gated_off(a)) return;
     constexpr int W = kThreads / 32;
     __shared__ float part[W][32 * V];
     const int lane = threadIdx.x & 31;

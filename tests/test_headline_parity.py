@@ -125,3 +125,27 @@ def test_early_exit_max_iter_50_matches_oracle(ldpc, oracle_mod, code, ebn0):
     print(f"n64800 early exit {ebn0} dB: {sample.size} frames, iterations {int(ref['iters'].min())}-"
           f"{int(ref['iters'].max())} (mean {ref['iters'].mean():.1f}), {int(exempt.sum())} exempt, "
           f"worst |dpost| beyond 20 iterations {drift:.2e}")
+
+
+@pytest.mark.parametrize("msg", ["f32", "bf16"])
+def test_early_exit_narrow_tail_is_bit_exact(ldpc, oracle_mod, code, msg):
+    """The early-exit form on the benchmark's 256 frames at 1.6 dB: after
+    about 20 passes at most 64 frames are still decoding, and from the next
+    compaction on the library runs them as one 64-frame group at two frames
+    per lane (the narrow tail, picked on the device). That decode equals,
+    bit for bit, the one-stream decode and the two-frames-per-lane decode
+    (neither has a narrow tail; the second compacts 64-frame groups
+    throughout): bits, iterations, flags and posteriors."""
+    F = BENCH_FRAMES
+    _, llr = philox_llr(oracle_mod, code, F, 1.6, EARLY_NOISE_SEED)
+    h = ldpc.code_from_inputs(code)
+    dev = torch.from_numpy(llr).cuda()
+    got = to_host(ldpc.ldpc_decode(h, dev, 50, early_exit=True, want_post=True, msg_dtype=msg))
+    late = int((got["iters"] > 21).sum())
+    assert 1 <= late <= 64, late  # the tail runs narrow after the compaction at pass 21
+    one = to_host(ldpc.ldpc_decode(h, dev, 50, early_exit=True, want_post=True, msg_dtype=msg, streams=1))
+    two = to_host(ldpc.ldpc_decode(h, dev, 50, early_exit=True, want_post=True, msg_dtype=msg, frames_per_lane=2))
+    for other, name in ((one, "one stream"), (two, "two frames per lane")):
+        for k in ("bits", "iters", "ok", "post"):
+            np.testing.assert_array_equal(other[k], got[k], err_msg=f"{name} {k}")
+    print(f"n64800 1.6 dB {msg}: {late} frames beyond 21 iterations, iterations up to {int(got['iters'].max())}")
