@@ -72,7 +72,8 @@ __global__ void k_init_done(uint32_t *done, uint32_t *status, uint32_t *unsat, i
 
 // Syndrome of the final hard decisions (Algorithm 6) from their bit words
 // dec [n][G] (G = Fp / 32 words per variable): thread (check i, word group)
-// xors the words of the check's variables, and each warp ors its checks'
+// xors the words of the check's variables (a check of degree above 32 by its
+// whole warp, lanes striding its edges), and each warp ors its checks'
 // unsatisfied-frame words into `row` with one atomic per word.
 template <int W>
 __global__ void k_syndrome_words(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, int32_t m,
@@ -83,20 +84,40 @@ __global__ void k_syndrome_words(const int32_t *__restrict__ row_ptr, const int3
     uint32_t z[W];
 #pragma unroll
     for (int q = 0; q < W; ++q) z[q] = 0u;
+    auto add = [&](uint32_t(&acc)[W], int32_t e) {
+        const uint32_t *p = dec + (size_t)col_idx[e] * G + w0;
+        if constexpr (W == 4) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(p);
+            acc[0] ^= v.x;
+            acc[1] ^= v.y;
+            acc[2] ^= v.z;
+            acc[3] ^= v.w;
+        } else {
+            acc[0] ^= p[0];
+        }
+    };
+    int32_t e0 = 0, e1 = 0;
     if (i < m) {
-        const int32_t e1 = row_ptr[i + 1];
+        e0 = row_ptr[i];
+        e1 = row_ptr[i + 1];
+    }
+    if (e1 - e0 <= 32) {
 #pragma unroll 4
-        for (int32_t e = row_ptr[i]; e < e1; ++e) {
-            const uint32_t *p = dec + (size_t)col_idx[e] * G + w0;
-            if constexpr (W == 4) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(p);
-                z[0] ^= v.x;
-                z[1] ^= v.y;
-                z[2] ^= v.z;
-                z[3] ^= v.w;
-            } else {
-                z[0] ^= p[0];
-            }
+        for (int32_t e = e0; e < e1; ++e) add(z, e);
+    }
+    // checks of degree above 32: the whole warp walks the check's edges and
+    // xor-reduces across its lanes
+    for (uint32_t wide = __ballot_sync(0xffffffffu, e1 - e0 > 32); wide; wide &= wide - 1) {
+        const int src = __ffs(wide) - 1;
+        const int32_t ws = __shfl_sync(0xffffffffu, e0, src), we = __shfl_sync(0xffffffffu, e1, src);
+        uint32_t zz[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) zz[q] = 0u;
+        for (int32_t e = ws + (int32_t)(threadIdx.x & 31); e < we; e += 32) add(zz, e);
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            zz[q] = __reduce_xor_sync(0xffffffffu, zz[q]);
+            if ((int)(threadIdx.x & 31) == src) z[q] ^= zz[q];
         }
     }
 #pragma unroll
@@ -504,6 +525,17 @@ static cudaError_t ensure_half_streams(Workspace &w) {
     return e;
 }
 
+// The side streams (non-blocking) of the two pass streams and their events.
+static cudaError_t ensure_side_streams(Workspace &w) {
+    cudaError_t e = cudaSuccess;
+    for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
+        if (!w.side_stream[h]) e = cudaStreamCreateWithFlags(&w.side_stream[h], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !w.side_fork[h]) e = cudaEventCreateWithFlags(&w.side_fork[h], cudaEventDisableTiming);
+        if (e == cudaSuccess && !w.side_join[h]) e = cudaEventCreateWithFlags(&w.side_join[h], cudaEventDisableTiming);
+    }
+    return e;
+}
+
 // Launch wrapper: optional CUDA-event timing of each launch on the stream.
 struct Launcher {
     ldpc_code *c;
@@ -570,6 +602,7 @@ PassArgs make_pass_args(const ldpc_code *c, const ldpc_decode_opts_t &o, float l
     a.unsat_ring = 0;
     a.wide_vars = c->d.wide_vars;
     a.n_wide_vars = (int32_t)c->wide_vars.size();
+    a.bit_wide_ctas = 0;
     return a;
 }
 
@@ -653,6 +686,12 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     // pass that the last few frames of a batch would otherwise keep running.
     static constexpr int32_t kNarrowFrom = 15;
     const bool narrow = compact && V == 4 && nstreams == 2 && ntiles == 2 && Fp % 256 == 0;
+    // Checks of degree above 32 (a CTA per check; a code has few of them)
+    // run on a side stream of each pass stream, beside the kernel of the
+    // other checks, which would otherwise wait for them.
+    const int32_t wide_bin = kNumCheckBins - 1;
+    const bool side = c->bin_off[wide_bin + 1] > c->bin_off[wide_bin] && c->bin_off[wide_bin] > 0;
+    if (side && (e = ensure_side_streams(w)) != cudaSuccess) return e;
     std::vector<int32_t> bounds{0};
     if (compact)
         for (int32_t t : kCuts)
@@ -688,9 +727,24 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
                 at.giveup_cta = (t == 1 && ti == 0) ? giveup : -1;
                 for (int form = 0; form < (two_forms ? 2 : 1); ++form) {
                     PassArgs &ap = form == 0 ? at : an;
+                    if (side) {
+                        const cudaStream_t ss = w.side_stream[h];
+                        if ((e = cudaEventRecord(w.side_fork[h], hs[h])) != cudaSuccess) return e;
+                        if ((e = cudaStreamWaitEvent(ss, w.side_fork[h], 0)) != cudaSuccess) return e;
+                        PassArgs aw = ap;
+                        aw.bin_degree = c->bin_max_degree[wide_bin];
+                        Launcher Ls{c, ss, per_kernel};
+                        e = Ls(LDPC_K_CHECK, 1, [&] {
+                            return launch_check_bin<M>(aw, wide_bin, c->d.bin_checks + c->bin_off[wide_bin],
+                                                       c->d.bin_desc + c->bin_off[wide_bin],
+                                                       c->bin_off[wide_bin + 1] - c->bin_off[wide_bin], ss);
+                        });
+                        if (e != cudaSuccess) return e;
+                        if ((e = cudaEventRecord(w.side_join[h], ss)) != cudaSuccess) return e;
+                    }
                     for (int b = 0; b < kNumCheckBins; ++b) {
                         int32_t count = c->bin_off[b + 1] - c->bin_off[b];
-                        if (count == 0) continue;
+                        if (count == 0 || (side && b == wide_bin)) continue;
                         ap.bin_degree = c->bin_max_degree[b];
                         e = Lh(LDPC_K_CHECK, 1, [&] {
                             return launch_check_bin<M>(ap, b, c->d.bin_checks + c->bin_off[b],
@@ -698,6 +752,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
                         });
                         if (e != cudaSuccess) return e;
                     }
+                    if (side && (e = cudaStreamWaitEvent(hs[h], w.side_join[h], 0)) != cudaSuccess) return e;
                 }
                 if (nstreams == 2 && ti == 0 && t == t0) {
                     if ((e = cudaEventRecord(w.phase, hs[0])) != cudaSuccess) return e;
@@ -706,7 +761,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
                 if (c->n > 0) {
                     for (int form = 0; form < (two_forms ? 2 : 1); ++form) {
                         const PassArgs &ap = form == 0 ? at : an;
-                        e = Lh(LDPC_K_BIT, c->wide_vars.empty() ? 1 : 2, [&] { return launch_bit<M>(ap, hs[h]); });
+                        e = Lh(LDPC_K_BIT, 1, [&] { return launch_bit<M>(ap, hs[h]); });
                         if (e != cudaSuccess) return e;
                     }
                 }
@@ -863,6 +918,7 @@ static int decode_graph(ldpc_code *c, const GraphKey &key, int32_t chunk, cudaSt
     cudaError_t e = cudaSuccess;
     if (!c->capture_stream) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = ensure_half_streams(c->ws);
+    if (e == cudaSuccess) e = ensure_side_streams(c->ws);
     if (e != cudaSuccess) return cuda_error(e, "ldpc_decode: graph set-up");
     cudaStream_t cap = c->capture_stream;
     const int64_t k0 = c->kernels_launched;
@@ -1087,6 +1143,9 @@ void free_workspace(Workspace &w) {
     for (int h = 0; h < 2; ++h) {
         if (w.half_stream[h]) cudaStreamDestroy(w.half_stream[h]);
         if (w.join[h]) cudaEventDestroy(w.join[h]);
+        if (w.side_stream[h]) cudaStreamDestroy(w.side_stream[h]);
+        if (w.side_fork[h]) cudaEventDestroy(w.side_fork[h]);
+        if (w.side_join[h]) cudaEventDestroy(w.side_join[h]);
     }
     if (w.fork) cudaEventDestroy(w.fork);
     if (w.phase) cudaEventDestroy(w.phase);

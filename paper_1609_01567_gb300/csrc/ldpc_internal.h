@@ -40,6 +40,9 @@ struct Workspace {
     // two library streams that run the two halves of a batch half a pass apart
     cudaStream_t half_stream[2] = {nullptr, nullptr};
     cudaEvent_t fork = nullptr, phase = nullptr, join[2] = {nullptr, nullptr};
+    // a side stream per pass stream for the checks of degree above 32
+    cudaStream_t side_stream[2] = {nullptr, nullptr};
+    cudaEvent_t side_fork[2] = {nullptr, nullptr}, side_join[2] = {nullptr, nullptr};
 };
 
 struct ProfRecord {

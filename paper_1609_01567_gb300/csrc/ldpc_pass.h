@@ -79,8 +79,8 @@ __device__ __forceinline__ bool frame_bit(const uint32_t *words, int f) { return
 // with a nonzero syndrome (the low bits hold max_iter)
 constexpr int32_t kStopFailed = 0x40000000;
 
-// Variables of higher degree are summed by a CTA (k_bit_wide), its warps
-// splitting the edges; the others by one warp each.
+// Variables of higher degree are summed by a CTA (trailing CTAs of the bit
+// kernel's grid), its warps splitting the edges; the others by one warp each.
 constexpr int kWideVarDegree = 16;
 
 // Tabulated phi: bucket key = float bits >> 17 (64 buckets per octave) over
@@ -137,6 +137,7 @@ struct PassArgs {
     int32_t unsat_ring;
     const int32_t *wide_vars;  // variables of degree above kWideVarDegree
     int32_t n_wide_vars;
+    int32_t bit_wide_ctas;     // bit kernel: its last CTAs sum the wide variables (set by its launcher)
     int32_t giveup_cta;  // test hook (ldpc_debug_giveup): this CTA of the launch treats its first
                          // completed bounded wait as run out; -1 = off
     // Early-exit tail: once a compaction has left at most kNarrowFrames live

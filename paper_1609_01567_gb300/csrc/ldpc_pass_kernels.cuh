@@ -659,45 +659,45 @@ __device__ __forceinline__ void check_node(int d, bool first, bool syn, Load &&l
         float tt[D][V];    // t_k = e^-min(|q_k|, L); 0 (a no-op) for slots k >= d
         uint32_t ones[V];  // bit k: input k says "bit 1" (q > 0)
         uint32_t z[V];
-    #pragma unroll
+#pragma unroll
         for (int v = 0; v < V; ++v) ones[v] = z[v] = 0u;
-    #pragma unroll
+#pragma unroll
         for (int k = 0; k < D; ++k) {
             if (k < d) {
                 float av[V], rv[V];
                 load(k, av, rv);
                 if (syn) {
-    #pragma unroll
+#pragma unroll
                     for (int v = 0; v < V; ++v) z[v] ^= av[v] > 0.0f ? 1u : 0u;
                 }
                 if (!first) {
-    #pragma unroll
+#pragma unroll
                     for (int v = 0; v < V; ++v) av[v] = extrinsic(av[v], rv[v]);
                 }
-    #pragma unroll
+#pragma unroll
                 for (int v = 0; v < V; ++v) {
                     ones[v] |= (av[v] > 0.0f ? 1u : 0u) << k;
                     tt[k][v] = exp_neg(fminf(fabsf(av[v]), a.l_max));
                 }
             } else {
-    #pragma unroll
+#pragma unroll
                 for (int v = 0; v < V; ++v) tt[k][v] = 0.0f;
             }
         }
-    #pragma unroll
+#pragma unroll
         for (int v = 0; v < V; ++v) unsat[v] |= z[v] != 0u;
         // (A2, D) of the inputs after k, then a running prefix
         float sa[D][V], sd[D][V];
         {
             float ca[V], cd[V];
-    #pragma unroll
+#pragma unroll
             for (int v = 0; v < V; ++v) {
                 ca[v] = 2.0f;
                 cd[v] = 0.0f;
             }
-    #pragma unroll
+#pragma unroll
             for (int k = D - 1; k >= 0; --k) {
-    #pragma unroll
+#pragma unroll
                 for (int v = 0; v < V; ++v) {
                     sa[k][v] = ca[v];
                     sd[k][v] = cd[v];
@@ -709,17 +709,17 @@ __device__ __forceinline__ void check_node(int d, bool first, bool syn, Load &&l
         // number of ones, i.e. iff input k's bit equals the total parity
         float pa[V], pd[V];
         uint32_t neg[V];
-    #pragma unroll
+#pragma unroll
         for (int v = 0; v < V; ++v) {
             pa[v] = 2.0f;
             pd[v] = 0.0f;
             neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
         }
-    #pragma unroll
+#pragma unroll
         for (int k = 0; k < D; ++k) {
             if (k < d) {
                 float o[V];
-    #pragma unroll
+#pragma unroll
                 for (int v = 0; v < V; ++v) {
                     o[v] = pf_out<true>(pa[v], pd[v], sa[k][v], sd[k][v], a.r_max);
                     o[v] = with_sign(o[v], neg[v] << (31 - k));
@@ -766,14 +766,14 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
         float2 tt[D][P];       // t_k, two frames per entry; 0 for slots k >= d
         uint32_t ones[2 * P];  // bit k: input k says "bit 1" (q > 0)
         uint32_t z[2 * P];
-    #pragma unroll
+#pragma unroll
         for (int v = 0; v < 2 * P; ++v) ones[v] = z[v] = 0u;
-    #pragma unroll
+#pragma unroll
         for (int k = 0; k < D; ++k) {
             if (k < d) {
                 float2 av[P], rv[P];
                 load(k, av, rv);
-    #pragma unroll
+#pragma unroll
                 for (int q = 0; q < P; ++q) {
                     if (syn) {
                         z[2 * q] ^= av[q].x > 0.0f ? 1u : 0u;
@@ -785,23 +785,23 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
                     tt[k][q] = exp_neg2(sat_abs2(av[q], a.l_max));
                 }
             } else {
-    #pragma unroll
+#pragma unroll
                 for (int q = 0; q < P; ++q) tt[k][q] = f2(0.0f);
             }
         }
-    #pragma unroll
+#pragma unroll
         for (int v = 0; v < 2 * P; ++v) unsat[v] |= z[v] != 0u;
         float2 sa[D][P], sd[D][P];
         {
             float2 ca[P], cd[P];
-    #pragma unroll
+#pragma unroll
             for (int q = 0; q < P; ++q) {
                 ca[q] = f2(2.0f);
                 cd[q] = f2(0.0f);
             }
-    #pragma unroll
+#pragma unroll
             for (int k = D - 1; k >= 0; --k) {
-    #pragma unroll
+#pragma unroll
                 for (int q = 0; q < P; ++q) {
                     sa[k][q] = ca[q];
                     sd[k][q] = cd[q];
@@ -811,18 +811,18 @@ __device__ __forceinline__ void check_node_pairs(int d, bool first, bool syn, Lo
         }
         float2 pa[P], pd[P];
         uint32_t neg[2 * P];
-    #pragma unroll
+#pragma unroll
         for (int q = 0; q < P; ++q) {
             pa[q] = f2(2.0f);
             pd[q] = f2(0.0f);
         }
-    #pragma unroll
+#pragma unroll
         for (int v = 0; v < 2 * P; ++v) neg[v] = (__popc(ones[v]) & 1u) ? ones[v] : ~ones[v];
-    #pragma unroll
+#pragma unroll
         for (int k = 0; k < D; ++k) {
             if (k < d) {
                 float2 o[P];
-    #pragma unroll
+#pragma unroll
                 for (int q = 0; q < P; ++q) {
                     o[q] = pf_out2<true>(pa[q], pd[q], sa[k][q], sd[k][q], a.r_max);
                     o[q].x = with_sign(o[q].x, neg[2 * q] << (31 - k));
@@ -1588,42 +1588,52 @@ __global__ void __launch_bounds__(kThreads) k_check_wide(PassArgs a, const int32
             idx[v] = -1;
             par[v] = z[v] = 0u;
         }
-        for (int k = warp; k < d; k += W) {
-            const int slot = b + k;
-            float av[V], qv[V];
-            load_v<V, float>(qsrc + (size_t)a.col_idx[slot] * Fp + f0, av);
-            if (first) {
+        // this warp's inputs k = warp + W u, u < nk; their column indices
+        // are fetched 32 at a time (lane u holds input u of the chunk), so the
+        // row loads of several inputs are in flight at once
+        const int nk = (d - warp + W - 1) / W;
+        for (int uc = 0; uc < nk; uc += 32) {
+            const int jl = uc + lane < nk ? a.col_idx[b + warp + W * (uc + lane)] : 0;
+            const int ue = min(32, nk - uc);
+#pragma unroll 4
+            for (int u = 0; u < ue; ++u) {
+                const int k = warp + W * (uc + u);
+                const int slot = b + k;
+                float av[V], qv[V];
+                load_v<V, float>(qsrc + (size_t)__shfl_sync(kFull, jl, u) * Fp + f0, av);
+                if (first) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) qv[v] = av[v];
-            } else {
-                float rv[V];
-                load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
+                    for (int v = 0; v < V; ++v) qv[v] = av[v];
+                } else {
+                    float rv[V];
+                    load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        // sum-product outputs next to a zero input are tiny, not
+                        // zero, so that input takes the sign of APP (min-sum
+                        // makes them exactly zero)
+                        qv[v] = RULE == 1 ? av[v] - rv[v] : extrinsic(av[v], rv[v]);
+                        z[v] ^= av[v] > 0.0f ? 1u : 0u;
+                    }
+                }
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    // sum-product outputs next to a zero input are tiny, not
-                    // zero, so that input takes the sign of APP (min-sum
-                    // makes them exactly zero)
-                    qv[v] = RULE == 1 ? av[v] - rv[v] : extrinsic(av[v], rv[v]);
-                    z[v] ^= av[v] > 0.0f ? 1u : 0u;
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if constexpr (RULE == 1) {
-                    const float x = fminf(fabsf(qv[v]), a.l_max);
-                    if (x < hi[v]) {
-                        lo[v] = hi[v];
-                        hi[v] = x;
-                        idx[v] = k;
-                    } else if (x < lo[v]) {
-                        lo[v] = x;
+                    if constexpr (RULE == 1) {
+                        const float x = fminf(fabsf(qv[v]), a.l_max);
+                        if (x < hi[v]) {
+                            lo[v] = hi[v];
+                            hi[v] = x;
+                            idx[v] = k;
+                        } else if (x < lo[v]) {
+                            lo[v] = x;
+                        }
+                    } else {
+                        float err;
+                        hi[v] = two_sum(hi[v], phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax), err);
+                        lo[v] += err;
                     }
-                } else {
-                    float err;
-                    hi[v] = two_sum(hi[v], phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax), err);
-                    lo[v] += err;
+                    par[v] ^= qv[v] > 0.0f ? 1u : 0u;
                 }
-                par[v] ^= qv[v] > 0.0f ? 1u : 0u;
             }
         }
 #pragma unroll
@@ -1670,36 +1680,42 @@ __global__ void __launch_bounds__(kThreads) k_check_wide(PassArgs a, const int32
             unsat[v] |= Z != 0u;
         }
         __syncthreads();  // the partials are read before the next check overwrites them
-        for (int k = warp; k < d; k += W) {
-            const int slot = b + k;
-            float av[V], qv[V];
-            load_v<V, float>(qsrc + (size_t)a.col_idx[slot] * Fp + f0, av);
-            if (first) {
+        for (int uc = 0; uc < nk; uc += 32) {
+            const int jl = uc + lane < nk ? a.col_idx[b + warp + W * (uc + lane)] : 0;
+            const int ue = min(32, nk - uc);
+#pragma unroll 4
+            for (int u = 0; u < ue; ++u) {
+                const int k = warp + W * (uc + u);
+                const int slot = b + k;
+                float av[V], qv[V];
+                load_v<V, float>(qsrc + (size_t)__shfl_sync(kFull, jl, u) * Fp + f0, av);
+                if (first) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) qv[v] = av[v];
-            } else {
-                float rv[V];
-                load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
-#pragma unroll
-                for (int v = 0; v < V; ++v) qv[v] = RULE == 1 ? av[v] - rv[v] : extrinsic(av[v], rv[v]);
-            }
-            float out[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                float mm;
-                if constexpr (RULE == 1) {
-                    const float m = idx[v] == k ? lo[v] : hi[v];
-                    mm = fminf(fmaxf(fmaf(alpha, m, -beta), 0.0f), a.l_max);
+                    for (int v = 0; v < V; ++v) qv[v] = av[v];
                 } else {
-                    const float own = phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax);
-                    float err;
-                    const float s2 = two_sum(hi[v], -own, err);
-                    mm = phi_hat(s2 + (err + lo[v]), a.l_max, a.phi_lmax);
+                    float rv[V];
+                    load_v<V, M>(r + (size_t)slot * Fp + f0, rv);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) qv[v] = RULE == 1 ? av[v] - rv[v] : extrinsic(av[v], rv[v]);
                 }
-                const uint32_t others = par[v] ^ (qv[v] > 0.0f ? 1u : 0u);
-                out[v] = others ? mm : -mm;
+                float out[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    float mm;
+                    if constexpr (RULE == 1) {
+                        const float m = idx[v] == k ? lo[v] : hi[v];
+                        mm = fminf(fmaxf(fmaf(alpha, m, -beta), 0.0f), a.l_max);
+                    } else {
+                        const float own = phi_hat(fabsf(qv[v]), a.l_max, a.phi_lmax);
+                        float err;
+                        const float s2 = two_sum(hi[v], -own, err);
+                        mm = phi_hat(s2 + (err + lo[v]), a.l_max, a.phi_lmax);
+                    }
+                    const uint32_t others = par[v] ^ (qv[v] > 0.0f ? 1u : 0u);
+                    out[v] = others ? mm : -mm;
+                }
+                store_v<V, M>(r + (size_t)slot * Fp + f0, out);
             }
-            store_v<V, M>(r + (size_t)slot * Fp + f0, out);
         }
     }
     if (a.syndrome && warp == 0) {
@@ -1714,7 +1730,68 @@ __global__ void __launch_bounds__(kThreads) k_check_wide(PassArgs a, const int32
 // Bit-node kernel: APP_j = lambda_j + sum_{i in M_j} r_ij
 // ---------------------------------------------------------------------------
 
+// Variables of degree above kWideVarDegree: the last bit_wide_ctas CTAs of
+// the bit kernel's grid, one CTA per (variable, group of 32 V frames) at a
+// time, its eight warps summing every eighth edge; the eight partial sums
+// (dynamic shared memory) are added to lambda in warp order (a fixed order,
+// so every frame layout gives the same posterior). They run beside the other
+// CTAs, which skip these variables, and see the same live frames.
 template <int V, typename M>
+__device__ __forceinline__ void bit_wide_ctas(const PassArgs &a, int cta, int ctas, int g, const bool (&live)[V],
+                                              bool all_live) {
+    constexpr int W = kThreads / 32;
+    extern __shared__ __align__(16) float part_smem[];
+    float(*part)[32 * V] = reinterpret_cast<float(*)[32 * V]>(part_smem);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int f0 = g * 32 * V + lane * V;
+    const size_t Fp = (size_t)a.Fp;
+    const M *r = reinterpret_cast<const M *>(a.r);
+    const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
+    for (int w = cta; w < a.n_wide_vars; w += ctas) {
+        const int j = a.wide_vars[w];
+        const int e0 = a.col_ptr[j], e1 = a.col_ptr[j + 1];
+        float acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+#pragma unroll 2
+        for (int e = e0 + warp; e < e1; e += W) {
+            float rv[V];
+            load_v_hint<V, M>(r + (size_t)a.edge_slot[e] * Fp + f0, rv, pol_stream);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += rv[v];
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) part[warp][lane * V + v] = acc[v];
+        __syncthreads();
+        if (warp == 0) {
+            load_v_hint<V, float>(a.lamT + (size_t)j * Fp + f0, acc, pol_stream);
+            for (int u = 0; u < W; ++u)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] += part[u][lane * V + v];
+            float *dst = a.app + (size_t)j * Fp + f0;
+            if (all_live) {
+                store_v_hint<V>(dst, acc, pol_keep);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (live[v]) dst[v] = acc[v];
+            }
+            if (a.dec) {
+                bool bits[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) bits[v] = acc[v] > 0.0f;
+                store_frame_bits<V>(a.dec + (size_t)j * (Fp / 32), g, lane, bits);
+            }
+        }
+        __syncthreads();  // the partials are read before the next variable overwrites them
+    }
+}
+
+// kWide: the grid ends in CTAs for the variables of degree above
+// kWideVarDegree (a separate instance, so that the common one keeps its
+// 32 registers and 8 CTAs per SM).
+template <int V, typename M, bool kWide>
 __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
     pdl_wait();
     if (gated_off(a)) return;
@@ -1761,13 +1838,21 @@ __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
         all_live &= live[v];
         any_live |= live[v];
     }
+    const int main_ctas = kWide ? (int)gridDim.x - a.bit_wide_ctas : (int)gridDim.x;
+    if constexpr (kWide) {
+        if ((int)blockIdx.x >= main_ctas) {
+            if (__syncthreads_or(any_live))  // the whole CTA stays or leaves together
+                bit_wide_ctas<V, M>(a, (int)blockIdx.x - main_ctas, a.bit_wide_ctas, g, live, all_live);
+            return;
+        }
+    }
     if (!__any_sync(kFull, any_live)) return;
 
     const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
-    for (int j = blockIdx.x * (kThreads / 32) + warp; j < a.n; j += gridDim.x * (kThreads / 32)) {
+    for (int j = blockIdx.x * (kThreads / 32) + warp; j < a.n; j += main_ctas * (kThreads / 32)) {
         const int e0 = a.col_ptr[j];
         const int e1 = a.col_ptr[j + 1];
-        if (e1 - e0 > kWideVarDegree) continue;  // k_bit_wide
+        if (kWide && e1 - e0 > kWideVarDegree) continue;  // the trailing CTAs
         float acc[V];
         load_v_hint<V, float>(a.lamT + (size_t)j * Fp + f0, acc, pol_stream);
 #pragma unroll 4
@@ -1794,77 +1879,6 @@ __global__ void __launch_bounds__(kThreads) k_bit(PassArgs a) {
             for (int v = 0; v < V; ++v) bits[v] = acc[v] > 0.0f;
             store_frame_bits<V>(a.dec + (size_t)j * (Fp / 32), g, lane, bits);
         }
-    }
-}
-
-// Variables of degree above kWideVarDegree: one CTA per (variable, group of
-// 32 V frames), its eight warps summing every eighth edge; the eight partial
-// sums are added to lambda in warp order (a fixed order, so every frame
-// layout gives the same posterior). Runs after k_bit on the same stream; the
-// live frames are those k_bit updates.
-template <int V, typename M>
-__global__ void __launch_bounds__(kThreads) k_bit_wide(PassArgs a) {
-    pdl_wait();
-    if (gated_off(a)) return;
-    constexpr int W = kThreads / 32;
-    __shared__ float part[W][32 * V];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int g = a.f_begin / (32 * V) + (int)blockIdx.y;
-    const int f0 = g * 32 * V + lane * V;
-    const size_t Fp = (size_t)a.Fp;
-    const M *r = reinterpret_cast<const M *>(a.r);
-    const uint32_t *unsat_prev = a.pass > 0 ? unsat_row(a, a.pass - 1) : nullptr;
-    const bool exit_test = a.early_exit && a.pass > 0;
-    const bool cont = a.base != nullptr && a.pass > 0;
-    bool live[V];
-    bool all_live = true, any_live = false;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        live[v] = !frame_bit(a.done, f0 + v) && (!exit_test || frame_bit(unsat_prev, f0 + v));
-        if (cont) live[v] = live[v] && a.pass - a.base[f0 + v] <= a.max_iter;
-        all_live &= live[v];
-        any_live |= live[v];
-    }
-    if (!__syncthreads_or(any_live)) return;  // the whole CTA leaves together
-    const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
-    for (int w = blockIdx.x; w < a.n_wide_vars; w += gridDim.x) {
-        const int j = a.wide_vars[w];
-        const int e0 = a.col_ptr[j], e1 = a.col_ptr[j + 1];
-        float acc[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = 0.0f;
-#pragma unroll 2
-        for (int e = e0 + warp; e < e1; e += W) {
-            float rv[V];
-            load_v_hint<V, M>(r + (size_t)a.edge_slot[e] * Fp + f0, rv, pol_stream);
-#pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] += rv[v];
-        }
-#pragma unroll
-        for (int v = 0; v < V; ++v) part[warp][lane * V + v] = acc[v];
-        __syncthreads();
-        if (warp == 0) {
-            load_v_hint<V, float>(a.lamT + (size_t)j * Fp + f0, acc, pol_stream);
-            for (int u = 0; u < W; ++u)
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] += part[u][lane * V + v];
-            float *dst = a.app + (size_t)j * Fp + f0;
-            if (all_live) {
-                store_v_hint<V>(dst, acc, pol_keep);
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-                    if (live[v]) dst[v] = acc[v];
-            }
-            if (a.dec) {
-                bool bits[V];
-#pragma unroll
-                for (int v = 0; v < V; ++v) bits[v] = acc[v] > 0.0f;
-                store_frame_bits<V>(a.dec + (size_t)j * (Fp / 32), g, lane, bits);
-            }
-        }
-        __syncthreads();  // the partials are read before the next variable overwrites them
     }
 }
 
@@ -2080,10 +2094,16 @@ static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *
                               count);
         return launch_pdl(k_check_any<1, M, RULE>, pass_grid(a, count, 1), dim3(kThreads), 0, s, a, checks, count);
     }
-    // Degrees above 32: a CTA per check and frame group (k_check_wide).
+    // Degrees above 32: a CTA per check and frame group (k_check_wide). A
+    // few such checks (the usual case) take narrow frame groups, so that
+    // more CTAs share them: one check of degree 96 on 128 frames is four
+    // CTAs at one frame per lane instead of one at four. Every width gives
+    // the same results.
     if (bin == kNumCheckBins - 1) {
-        if (a.V >= 4 && a.f_count % 128 == 0 && a.f_begin % 128 == 0) return launch_wide<4, M, RULE>(a, checks, count, s);
-        if (a.V >= 2) return launch_wide<2, M, RULE>(a, checks, count, s);
+        const int64_t ctas4 = (int64_t)count * (a.f_count / 128);
+        if (a.V >= 4 && a.f_count % 128 == 0 && a.f_begin % 128 == 0 && ctas4 >= a.sm_count)
+            return launch_wide<4, M, RULE>(a, checks, count, s);
+        if (a.V >= 2 && 2 * ctas4 >= a.sm_count) return launch_wide<2, M, RULE>(a, checks, count, s);
         return launch_wide<1, M, RULE>(a, checks, count, s);
     }
     // The register kernel for the other layouts. Wider bins keep more
@@ -2120,17 +2140,18 @@ cudaError_t launch_check_bin(const PassArgs &a, int bin, const int32_t *checks, 
 template <int V, typename M>
 static cudaError_t launch_bit_v(const PassArgs &a, cudaStream_t s) {
     // The bit kernel is bound by row gathers: 8 CTAs per SM (64 warps) keep
-    // more rows in flight than the default 4.
+    // more rows in flight than the default 4. Variables of degree above
+    // kWideVarDegree get trailing CTAs of the same grid (a CTA per variable
+    // and frame group), with their partial sums in dynamic shared memory.
     PassArgs b = a;
     b.grid_ctas = a.sm_count * 8;
-    cudaError_t e = launch_pdl(k_bit<V, M>, pass_grid(b, a.n, V), dim3(kThreads), 0, s, a);
-    if (e == cudaSuccess && a.n_wide_vars > 0) {
-        const int groups = a.f_count / (32 * V);
-        const int64_t cap = std::max<int64_t>(1, (int64_t)a.sm_count * 8 / groups);
-        const dim3 grid((unsigned)std::min<int64_t>(a.n_wide_vars, cap), (unsigned)groups, 1);
-        e = launch_pdl(k_bit_wide<V, M>, grid, dim3(kThreads), 0, s, a);
-    }
-    return e;
+    dim3 grid = pass_grid(b, a.n, V);
+    b.bit_wide_ctas = 0;
+    if (a.n_wide_vars == 0) return launch_pdl(k_bit<V, M, false>, grid, dim3(kThreads), 0, s, b);
+    const int64_t cap = std::max<int64_t>(1, (int64_t)a.sm_count * 8 / grid.y);
+    b.bit_wide_ctas = (int32_t)std::min<int64_t>(a.n_wide_vars, cap);
+    grid.x += (unsigned)b.bit_wide_ctas;
+    return launch_pdl(k_bit<V, M, true>, grid, dim3(kThreads), sizeof(float) * (kThreads / 32) * 32 * V, s, b);
 }
 
 template <typename M>
