@@ -676,7 +676,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     c->debug_giveup_cta = -1;
     // Segments of passes; between two segments the streams join and the
     // compaction kernels run on `s`.
-    static constexpr int32_t kCuts[] = {6, 10, 15, 21, 28, 36, 46, 60, 80};
+    static constexpr int32_t kCuts[] = {6, 10, 15, 21, 25, 28, 32, 36, 44, 48, 60, 80};
     // Narrow tail (four frames per lane, two 128-frame halves or more): from
     // the segment after pass kNarrowFrom on, stream 0 launches every pass in
     // two forms, its 128-frame groups and one 64-frame group at two frames
