@@ -8,8 +8,13 @@ Philox generator), flooding sum-product with max_iter = 10 fixed (11 check
 passes), FP32 messages. One step = one ldpc_decode call on the batch
 (interleave, 11 check + 11 bit passes, final syndrome, results).
 
-Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
-on the same workload instead (bounded samples per step).
+Prints one JSON line (rank 0): the timed steps, the roofline of the pass,
+the same workload with FP16/BF16/int8 messages (`by_msg`), end to end from
+pinned host memory (`e2e`), the max_iter-50 early-exit form, the FP64
+oracle's throughput on the host cores, and (N = 1, outside the timed region)
+the mixed-code batch and the decode server beside the plain FP32 decoder.
+`--impl reference` times the FP64 CPU oracle on the same workload instead
+(bounded samples per step).
 """
 from __future__ import annotations
 
@@ -53,6 +58,9 @@ def parse_args():
     p.add_argument("--by-msg-steps", type=int, default=200, help="steps per message format in by_msg (0 = skip)")
     p.add_argument("--streams", type=int, default=0, help="decode tuning: 1 or 2 streams (0 = library choice)")
     p.add_argument("--frames-per-lane", type=int, default=0, help="decode tuning (0 = library choice)")
+    p.add_argument("--no-context", action="store_true",
+                   help="skip the mixed-code batch and decode-server records (N = 1 only, outside the timed region)")
+    p.add_argument("--serve-requests", type=int, default=2000, help="requests per offered rate in the serving record")
     return p.parse_args()
 
 
@@ -459,6 +467,24 @@ def run_ours(args):
             early[f"{eb} dB"] = {"value": world * F * K_BITS / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                                  "mean_iters": sum(its) / len(its)}
         line["early_exit_max_iter_50"] = early
+
+    # context, N = 1 only and outside the timed region: the mixed-code batch
+    # (4096 frames over eight codes, one CUDA graph) and the decode server
+    # under Poisson traces of 2k / 10k / 50k requests per second, each beside
+    # the plain per-code (per-request) FP32 decoder on the same GPU
+    if world == 1 and not args.no_context:
+        from paper_1609_01567_gb300 import mixed, serve
+        mb = mixed.bench(reps=10, device=local)
+        line["mixed_batch"] = {
+            "workload": f"{sum(mb['frames'])} frames over {len(mb['codes'])} codes (Zipf 1.1), max_iter 50, early exit, "
+                        "each code at its FER ~1e-2 point",
+            **{k: {"ms": v["ms"], "gbps": v["gbps"], "frame_errors": v["frame_errors"]}
+               for k, v in mb.items() if isinstance(v, dict)}}
+        line["serving"] = [
+            {"rate_req_s": r["rate_req_s"], "requests": r["requests"], "frames": r["frames"],
+             "server_f16": {k: r["server"][k] for k in ("p50_ms", "p99_ms", "gbps", "slots")},
+             "plain_f32_per_request": {k: r["plain_f32"][k] for k in ("p50_ms", "p99_ms", "gbps")}}
+            for r in serve.measure([2000.0, 10000.0, 50000.0], args.serve_requests, device=local)]
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         frames, threads, wall, t_frame = oracle_sample(code, cw_host, args, args.cpu_seconds, F)

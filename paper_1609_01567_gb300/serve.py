@@ -140,22 +140,31 @@ def main(argv=None):
 
     from . import ldpc
 
+    for line in measure(args.rate, args.requests, msg=args.msg, slots=args.slots, plain=not args.no_plain):
+        print(json.dumps(line), flush=True)
+
+
+def measure(rates, requests, msg="f16", slots=4, plain=True, device=0):
+    """One Poisson trace per offered rate through the server, and (plain)
+    through the per-request FP32 decoder; yields one record per rate."""
+    from . import ldpc
+
     codes, ebn0 = serving_codes()
-    handles = [ldpc.code_from_inputs(c) for c in codes]
-    pools = make_pools(codes, ebn0)
-    for rate in args.rate:
-        tr = trace(args.requests, rate, len(codes))
+    handles = [ldpc.code_from_inputs(c, device=device) for c in codes]
+    pools = make_pools(codes, ebn0, device=device)
+    for rate in rates:
+        tr = trace(requests, rate, len(codes))
         info_bits = int(sum(codes[c].k * f for c, f in zip(tr[1], tr[2])))
-        lat, span, stats = run_server(handles, pools, tr, msg=args.msg, max_slots=args.slots)
-        line = {"rate_req_s": rate, "requests": args.requests, "frames": int(tr[2].sum()), "info_bits": info_bits,
-                "server": {"msg_dtype": args.msg, "slots": stats["slots"], "batches": stats["batches"],
+        lat, span, stats = run_server(handles, pools, tr, msg=msg, max_slots=slots)
+        line = {"rate_req_s": rate, "requests": requests, "frames": int(tr[2].sum()), "info_bits": info_bits,
+                "server": {"msg_dtype": msg, "slots": stats["slots"], "batches": stats["batches"],
                            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "gbps": info_bits / span / 1e9,
                            "seconds": span}}
-        if not args.no_plain:
+        if plain:
             lat_p, span_p = run_plain(handles, pools, tr)
             line["plain_f32"] = {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99), "gbps": info_bits / span_p / 1e9,
                                  "seconds": span_p}
-        print(json.dumps(line), flush=True)
+        yield line
 
 
 if __name__ == "__main__":
