@@ -34,7 +34,8 @@ constexpr int kMaxRegisterDegree = 32;
 
 constexpr int kThreads = 256;  // threads per CTA of the pass kernels (8 warps)
 constexpr int32_t kNarrowFrames = 64;  // frames of an early-exit decode's narrow tail group
-// checks of degree 17-32 in one code from which the any-degree kernel serves them
+// checks of degree 17-32 in one code from which the wide-bin kernels (18-slot ring, staged
+// product form, any-degree) serve them instead of the padded register kernel
 constexpr int32_t kWideBinAnyKernel = 2048;
 
 // int8 messages: uniform step 20/127, saturating at +-127 steps (= 20).

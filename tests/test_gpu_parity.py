@@ -385,10 +385,11 @@ def test_checks_of_degree_9_to_12_in_twelve_slots(ldpc, oracle_mod):
 
 @pytest.mark.parametrize("msg", ["f16", "bf16", "i8"])
 def test_new_check_paths_in_every_message_format(ldpc, msg):
-    """The 12-slot, high-rate (any-degree) and wide-check paths with 16-bit
-    and int8 messages: the same results at one frame per lane with direct
-    loads on one stream as in the default layout, and the same codeword as
-    the FP32 decode on nearly every frame that FP32 corrects."""
+    """The 12-slot, 18-slot (high-rate) and wide-check paths with 16-bit
+    and int8 messages: the same results as the direct-load kernels (the
+    staged product form for the high-rate checks) at one frame per lane on
+    one stream, and the same codeword as the FP32 decode on nearly every
+    frame that FP32 corrects."""
     for idx, ebn0 in ((1, 3.6), (4, 2.8), (7, 3.1)):  # n = 1152 r 3/4, n = 8192 with a degree-96 check, n = 64800 r 5/6
         code = I.mixed_code(idx)
         h = ldpc.code_from_inputs(code)
