@@ -182,7 +182,8 @@ typedef struct {
                            halves of the batch on two library streams, half a
                            pass apart, so that the check pass of one half
                            overlaps the bit pass of the other; 0 = 2 when the
-                           batch splits evenly                              */
+                           batch splits evenly into halves of at least 128
+                           frames and n x (padded frames) >= 2^20, else 1   */
     int32_t tile_frames; /* tuning: run all passes of tile_frames frames at a
                            time (rounded up to the kernels' frame group; tiles
                            alternate between the two streams), so that one

@@ -656,8 +656,14 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     // (messages, posteriors, LLRs) within L2 while it iterates. With two
     // streams, consecutive tiles alternate between them and the second stream
     // starts when the first has finished its first check pass.
+    // By default a batch splits when each half still fills the GPU: at least
+    // 256 frames and n * Fp >= 2^20 (n = 4096 at 256 frames; shorter codes'
+    // passes are launch- and latency-bound, and one stream is faster there:
+    // n = 576 / 1152 / 2304 at 256 frames 0.099 / 0.095 / 0.143 ms on two
+    // streams, 0.093 / 0.085 / 0.132 ms on one).
     const int32_t unit = 32 * std::max(V, 2);
-    const bool split = o.streams != 1 && Fp % (2 * unit) == 0 && (o.streams == 2 || Fp >= 256);
+    const bool split = o.streams != 1 && Fp % (2 * unit) == 0 &&
+                       (o.streams == 2 || (Fp >= 256 && (int64_t)c->n * Fp >= (int64_t)1 << 20));
     int32_t tile = o.tile_frames > 0 ? (o.tile_frames + unit - 1) / unit * unit : 0;
     if (tile <= 0 || tile >= Fp || Fp % tile != 0) tile = split ? Fp / 2 : Fp;
     const int32_t ntiles = Fp / tile;

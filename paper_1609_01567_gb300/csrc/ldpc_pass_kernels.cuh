@@ -2068,18 +2068,17 @@ static cudaError_t launch_check_rule(const PassArgs &a, int bin, const int32_t *
             return launch_bulk<16, 2, M, 2, RULE>(a, desc, count, s);
         }
     }
-    // Degrees 17-32 in a code with many such checks. Up to degree 18 (the
-    // rate-5/6 codes), batches of 64-frame groups run the pipelined kernel
-    // with 18 slots, its rows brought in by tensor copies; other batches and
-    // wider checks run the staged product-form kernel (the same operations in
-    // the same order, so a frame's result does not depend on which one ran),
-    // min-sum the any-degree kernel. The register kernel, which pads every
-    // check to 32 slots at one frame per lane, took 5.28 ms on n = 64800 rate
-    // 5/6 (256 frames, 10 iterations); it stays for a code with few such
-    // checks (a short high-rate code), whose loads of one check are all in
-    // flight at once. The choice depends on the code, never on the batch.
-    if (a.check_schedule != 1 && bin == 4 && a.bin_degree <= 18 && count >= kWideBinAnyKernel &&
-        a.f_count % 64 == 0 && a.f_begin % 64 == 0)
+    // Degrees 17-32. Up to degree 18 (the rate-5/6 codes), batches of 64-frame
+    // groups run the pipelined kernel with 18 slots, its rows brought in by
+    // tensor copies (n = 576 rate 5/6, 256 frames, 10 iterations: 0.156 ->
+    // 0.099 ms against the register kernel). Other batches and wider checks:
+    // in a code with many such checks the staged product-form kernel (the
+    // same operations in the same order, so a frame's result does not depend
+    // on which one ran), min-sum the any-degree kernel; in a code with few,
+    // the register kernel, which pads every check to 32 slots at one frame
+    // per lane (5.28 ms on n = 64800 rate 5/6, where it would be the only
+    // choice), whose loads of one check are all in flight at once.
+    if (a.check_schedule != 1 && bin == 4 && a.bin_degree <= 18 && a.f_count % 64 == 0 && a.f_begin % 64 == 0)
         return launch_bulk<18, 2, M, 2, RULE>(a, desc, count, s);
     if (bin == 4 && count >= kWideBinAnyKernel && RULE == 0) {
         if (a.V >= 2 && a.f_count % 64 == 0 && a.f_begin % 64 == 0) return launch_prod<2, M>(a, checks, count, s);

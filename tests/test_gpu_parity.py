@@ -365,6 +365,31 @@ def test_wide_check_lock_step_and_layouts(ldpc, oracle_mod, rule):
             np.testing.assert_array_equal(other[k], base[k], err_msg=f"{lay} {k}")
 
 
+@pytest.mark.parametrize("rule", ["sum_product", "min_sum"])
+def test_short_high_rate_code_ring_and_register_kernels(ldpc, oracle_mod, rule):
+    """A short rate-5/6 code (95 checks of degree 17-18): batches of 64-frame
+    groups run the 18-slot ring kernel, a 20-frame batch and check_schedule 1
+    the register kernel (32 slots, one frame per lane, direct loads). Same
+    results bit for bit, and the oracle's on every frame that stops within
+    12 iterations (min-sum: the offset/normalised rule)."""
+    code = I.mixed_code(0)  # n = 576, rate 5/6
+    h = ldpc.code_from_inputs(code)
+    assert ldpc.ldpc_code_info(h)["check_bin_count"][4] == code.m
+    kw = dict(rule=rule, rule_alpha=0.85, rule_beta=0.1) if rule == "min_sum" else {}
+    okw = dict(rule="min_sum", alpha=0.85, beta=0.1) if rule == "min_sum" else {}
+    llr = I.gaussian_llr(np.zeros((256, code.n), np.uint8), I.sigma2_from_ebn0(4.0, code.rate), seed=576)
+    base = gpu_decode(ldpc, h, llr, 20, **kw)
+    reg = gpu_decode(ldpc, h, llr, 20, check_schedule=1, **kw)
+    part = gpu_decode(ldpc, h, llr[:20], 20, **kw)
+    for k in ("bits", "iters", "ok", "post"):
+        np.testing.assert_array_equal(reg[k], base[k], err_msg=f"register kernel {k}")
+        np.testing.assert_array_equal(part[k], base[k][:20], err_msg=f"20 frames {k}")
+    ref = oracle_mod.decode(code, llr.astype(np.float64), 20, n_threads=8, **okw)
+    bad, exempt = compare_decodes(base, ref)
+    short = ref["iters"] <= 12
+    assert short.mean() > 0.5 and not np.isin(bad, np.flatnonzero(short)).any(), bad
+
+
 def test_checks_of_degree_9_to_12_in_twelve_slots(ldpc, oracle_mod):
     """A bin of checks of degree 9-16 whose largest degree is 12 runs in 12
     slots instead of 16; padding slots are exact no-ops, so the results equal
