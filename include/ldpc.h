@@ -312,14 +312,16 @@ int ldpc_batch_run(ldpc_batch_t *batch, const float *const *llr, uint8_t *const 
                    uint8_t *const *syndrome_ok, float *const *post_llr, void *stream);
 
 /* Autotune each item's kernel schedule (frames per lane in {1, 2, 4, 8} with
- * padding at most a quarter of the frames, direct or pipelined check
- * kernel) by timing decodes of the given device LLRs; keeps the fastest.
- * Synchronous; allocates temporary outputs. */
+ * padding at most the item's own frame count, direct or pipelined check
+ * kernel, the item's frames on one stream or split over two) by timing
+ * decodes of the given device LLRs; keeps the fastest. Synchronous;
+ * allocates temporary outputs. */
 int ldpc_batch_tune(ldpc_batch_t *batch, const float *const *llr, void *stream);
 
-/* The schedule picked for one item and the kernels one graph replay runs. */
+/* The schedule picked for one item (frames per lane, check schedule,
+ * streams) and the kernels one graph replay runs. NULL outputs are skipped. */
 int ldpc_batch_info(const ldpc_batch_t *batch, int32_t item, int32_t *frames_per_lane, int32_t *check_schedule,
-                    int64_t *kernels_per_run);
+                    int32_t *streams, int64_t *kernels_per_run);
 
 /* Waits for the batch's pending work and releases it. NULL is ignored. */
 void ldpc_batch_destroy(ldpc_batch_t *batch);

@@ -660,13 +660,14 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
     // 256 frames and n * Fp >= 2^20 (n = 4096 at 256 frames; shorter codes'
     // passes are launch- and latency-bound, and one stream is faster there:
     // n = 576 / 1152 / 2304 at 256 frames 0.099 / 0.095 / 0.143 ms on two
-    // streams, 0.093 / 0.085 / 0.132 ms on one).
+    // streams, 0.093 / 0.085 / 0.132 ms on one). An odd number of frame
+    // groups splits unevenly (192 frames at two per lane: 128 + 64).
     const int32_t unit = 32 * std::max(V, 2);
-    const bool split = o.streams != 1 && Fp % (2 * unit) == 0 &&
+    const bool split = o.streams != 1 && Fp >= 2 * unit &&
                        (o.streams == 2 || (Fp >= 256 && (int64_t)c->n * Fp >= (int64_t)1 << 20));
     int32_t tile = o.tile_frames > 0 ? (o.tile_frames + unit - 1) / unit * unit : 0;
-    if (tile <= 0 || tile >= Fp || Fp % tile != 0) tile = split ? Fp / 2 : Fp;
-    const int32_t ntiles = Fp / tile;
+    if (tile <= 0 || tile >= Fp || Fp % tile != 0) tile = split ? (Fp / 2 + unit - 1) / unit * unit : Fp;
+    const int32_t ntiles = (Fp + tile - 1) / tile;  // the last tile may be shorter
     const int nstreams = split && ntiles >= 2 ? 2 : 1;
     cudaStream_t hs[2] = {s, s};
     if (nstreams == 2) {
@@ -714,7 +715,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
             const int h = ti % nstreams;
             PassArgs at = a;
             at.f_begin = ti * tile;
-            at.f_count = tile;
+            at.f_count = std::min(tile, Fp - ti * tile);
             // the narrow form of stream 0's passes in this segment
             const bool two_forms = narrow && ti == 0 && t0 >= kNarrowFrom;
             PassArgs an = at;
@@ -1379,10 +1380,16 @@ extern "C" int ldpc_batch_tune(ldpc_batch_t *b, const float *const *llr, void *s
         for (int li = 0; li < 4 && status == LDPC_OK; ++li) {
             int32_t v = lanes[li];
             int32_t Fp = (it.F + 32 * v - 1) / (32 * v) * (32 * v);
-            if (v > 1 && Fp - it.F > it.F / 4) continue;  // padding wider than a quarter of the batch
-            for (int32_t sched = 1; sched <= 2 && status == LDPC_OK; ++sched) {
+            if (v > 1 && Fp - it.F > it.F) continue;  // padding larger than the batch itself
+            for (int32_t trial = 0; trial < 4 && status == LDPC_OK; ++trial) {
+                const int32_t sched = 1 + trial % 2, nst = 1 + trial / 2;
+                // two streams only for items that fill the GPU by themselves
+                // (in the graph the items already overlap one another)
+                if (nst == 2 && (Fp < 2 * 32 * std::max(v, 2) || (int64_t)it.code->n * Fp < ((int64_t)1 << 22)))
+                    continue;
                 it.opts.frames_per_lane = v;
                 it.opts.check_schedule = sched;
+                it.opts.streams = nst;
                 float ms = 0.0f;
                 for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
                     if (rep == 1) e = cudaEventRecord(t0, it.stream);
@@ -1396,7 +1403,7 @@ extern "C" int ldpc_batch_tune(ldpc_batch_t *b, const float *const *llr, void *s
                     status = cuda_error(e, "ldpc_batch_tune: trial");
                     break;
                 }
-                if (ms < best) {
+                if (ms < (nst == 2 ? 0.9f : 1.0f) * best) {  // a split must win clearly
                     best = ms;
                     best_opts = it.opts;
                 }
@@ -1418,10 +1425,11 @@ extern "C" int ldpc_batch_tune(ldpc_batch_t *b, const float *const *llr, void *s
 }
 
 extern "C" int ldpc_batch_info(const ldpc_batch_t *b, int32_t item, int32_t *frames_per_lane, int32_t *check_schedule,
-                               int64_t *kernels_per_run) {
+                               int32_t *streams, int64_t *kernels_per_run) {
     if (!b || item < 0 || item >= (int32_t)b->items.size()) return set_error(LDPC_EINVAL, "ldpc_batch_info: bad item");
     if (frames_per_lane) *frames_per_lane = b->items[item].opts.frames_per_lane;
     if (check_schedule) *check_schedule = b->items[item].opts.check_schedule;
+    if (streams) *streams = b->items[item].opts.streams;
     if (kernels_per_run) *kernels_per_run = b->kernels_per_run;
     return LDPC_OK;
 }

@@ -104,7 +104,7 @@ def library():
             lib.ldpc_batch_create.argtypes = [i32, vp, vp, i32, ctypes.POINTER(ldpc_decode_opts_t), ctypes.POINTER(vp)]
             lib.ldpc_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             lib.ldpc_batch_tune.argtypes = [vp, vp, vp]
-            lib.ldpc_batch_info.argtypes = [vp, i32, vp, vp, vp]
+            lib.ldpc_batch_info.argtypes = [vp, i32, vp, vp, vp, vp]
             lib.ldpc_batch_destroy.argtypes = [vp]
             lib.ldpc_batch_destroy.restype = None
             lib.ldpc_server_create.argtypes = [i32, vp, ctypes.POINTER(ldpc_server_opts_t), ctypes.POINTER(vp)]
@@ -557,9 +557,10 @@ def ldpc_batch_tune(batch: Batch, llrs, stream=None) -> None:
 
 
 def ldpc_batch_info(batch: Batch, item: int) -> dict:
-    v, s, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
-    _check(library().ldpc_batch_info(batch.handle, item, ctypes.byref(v), ctypes.byref(s), ctypes.byref(k)))
-    return {"frames_per_lane": v.value, "check_schedule": s.value, "kernels_per_run": k.value}
+    v, s, st, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(library().ldpc_batch_info(batch.handle, item, ctypes.byref(v), ctypes.byref(s), ctypes.byref(st),
+                                     ctypes.byref(k)))
+    return {"frames_per_lane": v.value, "check_schedule": s.value, "streams": st.value, "kernels_per_run": k.value}
 
 
 class Server:

@@ -111,7 +111,7 @@ def bench(reps: int = 20, device: int = 0) -> dict:
         fe = [int((o["bits"] != s).any(dim=1).sum()) for o, s in zip(bouts, sent)]
         sched = [ldpc.ldpc_batch_info(b, i) for i in range(len(codes))]
         result[f"batch_graph_{msg}"] = {"ms": ms, "gbps": info_bits / (ms * 1e-3) / 1e9, "frame_errors": fe,
-                                        "schedules": [(s["frames_per_lane"], s["check_schedule"]) for s in sched],
+                                        "schedules": [(s["frames_per_lane"], s["check_schedule"], s["streams"]) for s in sched],
                                         "kernels_per_run": sched[0]["kernels_per_run"]}
         b.close()
     return result
