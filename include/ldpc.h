@@ -469,6 +469,31 @@ int ldpc_gen_bits(uint64_t seed, int64_t frame_offset, int32_t n_frames, int32_t
 int ldpc_encode_ira(ldpc_code_t *code, const uint8_t *info, int32_t n_frames, uint8_t *codeword, void *stream);
 
 /*
+ * A systematic encoder for any code, lifted (quasi-cyclic) codes without a
+ * staircase included. H is brought to reduced row echelon form over GF(2)
+ * on the host, pivots taken column by column from the last column down (an
+ * IRA code keeps its staircase columns as parity positions); rank r of H,
+ * k = n - r information positions (the non-pivot columns, in increasing
+ * order), and per pivot row the information bits whose xor sets its pivot
+ * column. Built once and kept with the code (device: r * ceil(k / 32) words
+ * and n indices); *k_out (optional) receives k. A host-only code gets k only.
+ * Synchronous. Errors: LDPC_EINVAL for a NULL code or m * n > 2^26 (the dense
+ * elimination), LDPC_ECUDA/LDPC_ENOMEM on device failures.
+ */
+int ldpc_code_build_encoder(ldpc_code_t *code, int32_t *k_out);
+
+/*
+ * Encoding with that encoder: information words info [n_frames][k] (device
+ * uint8, bit 0 of each byte used, k from ldpc_code_build_encoder) to
+ * codewords [n_frames][n] (device uint8): information bit t at the t-th
+ * information position, each pivot column the xor its row gives, so that
+ * H c = 0 for every frame. Stream-ordered scratch ((k + r) * ceil(n_frames /
+ * 32) words). Asynchronous. Errors: LDPC_EINVAL without an encoder, for
+ * n_frames < 0 or NULL buffers; LDPC_ENODEV for a host-only code.
+ */
+int ldpc_encode(ldpc_code_t *code, const uint8_t *info, int32_t n_frames, uint8_t *codeword, void *stream);
+
+/*
  * Error counts of the BER simulator (Section IV): for decoded words bits
  * [n_frames][n] and the transmitted words ref [n_frames][n] (NULL = the
  * all-zero word, enough by the code's linearity), adds to device counts[0]

@@ -41,8 +41,9 @@ def simulate(handle, code, ebn0_db: float, n_frames: int, *, batch: int = 1024, 
 
     codewords: None for the all-zero word, "random" for random codewords
     made on the device (information bits from Philox key (seed, 1), encoded
-    by the library's IRA encoder), else a CUDA uint8 tensor [n_frames, n] of
-    transmitted codewords.
+    by the library's IRA encoder, or by its dense systematic encoder for a
+    code without the staircase, a lifted code say), else a CUDA uint8 tensor
+    [n_frames, n] of transmitted codewords.
     """
     import torch
 
@@ -58,14 +59,16 @@ def simulate(handle, code, ebn0_db: float, n_frames: int, *, batch: int = 1024, 
     if rand:
         if codewords != "random":
             raise ValueError("codewords must be None, 'random' or a tensor")
-        k = code.n - code.m
+        ira = ldpc.ldpc_code_info(handle)["ira_k"] >= 0
+        k = code.n - code.m if ira else ldpc.ldpc_code_build_encoder(handle)
+        encode = ldpc.ldpc_encode_ira if ira else ldpc.ldpc_encode
         info = torch.empty((batch, k), dtype=torch.uint8, device=dev)
         cw_buf = torch.empty((batch, code.n), dtype=torch.uint8, device=dev)
     while done < n_frames:
         b = min(batch, n_frames - done)
         if rand:
             ldpc.ldpc_gen_bits(seed, frame_offset + done, b, k, out=info[:b], device=handle.device, stream=stream)
-            cw = ldpc.ldpc_encode_ira(handle, info[:b], out=cw_buf[:b], stream=stream)
+            cw = encode(handle, info[:b], out=cw_buf[:b], stream=stream)
         else:
             cw = None if codewords is None else codewords[done:done + b]
         lb = llr[:b]

@@ -51,6 +51,10 @@ static void free_device_tables(ldpc_code *c) {
     cudaFree(c->d.phi_table);
     cudaFree(c->d.ms_table);
     cudaFree(c->d.wide_vars);
+    cudaFree(c->enc_R);
+    cudaFree(c->enc_colmap);
+    c->enc_R = nullptr;
+    c->enc_colmap = nullptr;
     free_host_stream(c);
     free_decode_graphs(c);
     free_workspace(c->ws);

@@ -124,6 +124,14 @@ struct ldpc_code {
     uint64_t graph_tick = 0;
     cudaStream_t capture_stream = nullptr;
     int32_t debug_giveup_cta = -1;  // ldpc_debug_giveup: armed for the next decode, then cleared
+    // systematic encoder of any code (ldpc_code_build_encoder): enc_k
+    // information positions (-1: not built), enc_r = rank of H; on the device
+    // the parity rows over the information bits, enc_R [enc_r][ceil(enc_k / 32)]
+    // bit words, and enc_colmap [n] (information index j >= 0, or -1 - i for
+    // the column set by parity row i)
+    int32_t enc_k = -1, enc_r = 0;
+    uint32_t *enc_R = nullptr;
+    int32_t *enc_colmap = nullptr;
 };
 
 namespace ldpc {

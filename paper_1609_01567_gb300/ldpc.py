@@ -61,7 +61,8 @@ class ldpc_prof_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 7), ("total_ms", ctypes.c_double * 7), ("kernels", ctypes.c_int64)]
 
 
-EXPORTS = ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira", "ldpc_decode_host_stream",
+EXPORTS = ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira", "ldpc_code_build_encoder",
+           "ldpc_encode", "ldpc_decode_host_stream",
            "ldpc_code_destroy", "ldpc_code_info", "ldpc_code_set_rule_table", "ldpc_code_tables", "ldpc_decode",
            "ldpc_decode_host", "ldpc_decode_static", "ldpc_gen_awgn", "ldpc_count_errors", "ldpc_batch_create",
            "ldpc_batch_run", "ldpc_batch_tune", "ldpc_batch_info", "ldpc_batch_destroy", "ldpc_server_create",
@@ -89,6 +90,8 @@ def library():
             lib.ldpc_decode_host_stream.argtypes = [vp, i32, vp, i32, i32, ctypes.POINTER(ldpc_decode_opts_t), vp, vp,
                                                     vp, vp]
             lib.ldpc_encode_ira.argtypes = [vp, vp, i32, vp, vp]
+            lib.ldpc_code_build_encoder.argtypes = [vp, vp]
+            lib.ldpc_encode.argtypes = [vp, vp, i32, vp, vp]
             lib.ldpc_code_destroy.argtypes = [vp]
             lib.ldpc_code_destroy.restype = None
             lib.ldpc_code_info.argtypes = [vp, ctypes.POINTER(ldpc_code_info_t)]
@@ -118,6 +121,7 @@ def library():
             lib.ldpc_last_error.restype = ctypes.c_char_p
             lib.ldpc_version.restype = ctypes.c_char_p
             for name in ("ldpc_code_create", "ldpc_code_create_qc", "ldpc_gen_bits", "ldpc_encode_ira",
+                         "ldpc_code_build_encoder", "ldpc_encode",
                          "ldpc_decode_host_stream", "ldpc_code_info", "ldpc_code_set_rule_table", "ldpc_code_tables",
                          "ldpc_decode", "ldpc_decode_host",
                          "ldpc_decode_static",
@@ -434,6 +438,27 @@ def ldpc_encode_ira(code: Code, info, out=None, stream=None):
     _check(library().ldpc_encode_ira(code.handle, _dev_ptr(info, torch.uint8, (f, k), "info", code.device), f,
                                      _dev_ptr(out, torch.uint8, (f, code.n), "out", code.device),
                                      _stream_handle(stream)))
+    return out
+
+
+def ldpc_code_build_encoder(code: Code) -> int:
+    """Build the code's systematic encoder (any code; host GF(2) reduction of
+    H, kept with the code); returns k, its number of information bits."""
+    k = ctypes.c_int32()
+    _check(library().ldpc_code_build_encoder(code.handle, ctypes.byref(k)))
+    return k.value
+
+
+def ldpc_encode(code: Code, info, out=None, stream=None):
+    """Systematic encoding with the encoder ldpc_code_build_encoder built:
+    CUDA uint8 info [F, k] -> codewords [F, n]."""
+    import torch
+    k = ldpc_code_build_encoder(code)
+    f = int(info.shape[0])
+    if out is None:
+        out = torch.empty((f, code.n), dtype=torch.uint8, device=info.device)
+    _check(library().ldpc_encode(code.handle, _dev_ptr(info, torch.uint8, (f, k), "info", code.device), f,
+                                 _dev_ptr(out, torch.uint8, (f, code.n), "out", code.device), _stream_handle(stream)))
     return out
 
 

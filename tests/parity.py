@@ -38,3 +38,28 @@ def compare_decodes(gpu: dict, ref: dict, frames=None):
     bad = ~(post_ok & same) & ~exempt
     idx = np.arange(len(bad)) if frames is None else np.asarray(frames)
     return idx[bad], idx[exempt]
+
+
+def gf2_information_positions(m, n, rows, cols):
+    """Column j of H is an information position iff it lies in the span of
+    the columns to its right (GF(2)); independent of the library's
+    elimination: a column-by-column basis of those columns, numpy bool rows."""
+    H = np.zeros((m, n), dtype=bool)
+    H[np.asarray(rows), np.asarray(cols)] = True
+    basis = {}  # leading row -> reduced column vector
+    info = []
+    for j in range(n - 1, -1, -1):
+        v = H[:, j].copy()
+        for lead in sorted(basis):
+            if v[lead]:
+                v ^= basis[lead]
+        nz = np.flatnonzero(v)
+        if nz.size == 0:
+            info.append(j)
+        else:
+            lead = int(nz[0])
+            for key in list(basis):
+                if basis[key][lead]:
+                    basis[key] ^= v
+            basis[lead] = v
+    return sorted(info), len(basis)

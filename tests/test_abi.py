@@ -14,6 +14,7 @@ import pytest
 from paper_1609_01567_gb300 import build as lib_build
 from paper_1609_01567_gb300 import inputs as I
 from tests.paper_tables import table
+from tests.parity import gf2_information_positions
 
 ROOT = Path(__file__).resolve().parent.parent
 
@@ -191,3 +192,25 @@ def test_debug_giveup_hook_validation(ldpc):
     with pytest.raises(ldpc.LdpcError) as e:
         ldpc.ldpc_debug_giveup(h, -2)
     assert e.value.status == -1
+
+
+def test_dense_encoder_rank_and_positions(ldpc):
+    """ldpc_code_build_encoder on host-only codes: k = n - rank(H) as an
+    independent GF(2) basis computation gives it, for a lifted (4, 8) code
+    (rank-deficient: each block row of an all-ones protograph lift sums to the
+    same word) and an IRA code (full rank, k = n - m); bad sizes refused."""
+    code, ent = I.qc_stand_in_code(256)
+    h = ldpc.ldpc_code_create_qc(4, 8, 32, ent, device=-1)
+    info, rank = gf2_information_positions(code.m, code.n, code.rows, code.cols)
+    assert rank < code.m
+    assert ldpc.ldpc_code_build_encoder(h) == code.n - rank == len(info)
+    ira = I.mixed_codes()[0]
+    hi = ldpc.ldpc_code_create(ira.m, ira.n, ira.rows, ira.cols, device=-1)
+    info_i, rank_i = gf2_information_positions(ira.m, ira.n, ira.rows, ira.cols)
+    assert rank_i == ira.m and info_i == list(range(ira.k))
+    assert ldpc.ldpc_code_build_encoder(hi) == ira.k
+    big = I.large_code_n64800()
+    hb = ldpc.ldpc_code_create(big.m, big.n, big.rows, big.cols, device=-1)
+    with pytest.raises(ldpc.LdpcError) as e:
+        ldpc.ldpc_code_build_encoder(hb)
+    assert e.value.status == -1 and "2^26" in str(e.value)

@@ -11,7 +11,7 @@ import pytest
 
 from paper_1609_01567_gb300 import ber
 from paper_1609_01567_gb300 import inputs as I
-from tests.parity import close, near_zero_frames
+from tests.parity import close, gf2_information_positions, near_zero_frames
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -116,3 +116,49 @@ def test_random_codeword_simulation(ldpc, oracle_mod):
     cw = ldpc.ldpc_encode_ira(h, info).cpu().numpy()
     assert np.all(oracle_mod.syndrome_weight(code, cw) == 0)
     np.testing.assert_array_equal(cw[:, :code.k], expected_bits(oracle_mod, 3, 0, 50, code.k))
+
+
+def test_dense_encoder_on_a_lifted_code(ldpc, oracle_mod):
+    """The dense systematic encoder on a lifted (4, 8) code without a
+    staircase: every word satisfies H c = 0 (the oracle's syndrome) and holds
+    its information bits at the information positions that an independent
+    GF(2) basis computation finds (columns in the span of the columns to
+    their right); together these fix the codeword."""
+    code, ent = I.qc_stand_in_code(512)
+    h = ldpc.ldpc_code_create_qc(4, 8, 64, ent)
+    pos, rank = gf2_information_positions(code.m, code.n, code.rows, code.cols)
+    k = ldpc.ldpc_code_build_encoder(h)
+    assert k == len(pos) == code.n - rank
+    for F in (1, 33, 70):
+        info = I.random_info(F, k, seed=F)
+        cw = ldpc.ldpc_encode(h, torch.from_numpy(info).cuda()).cpu().numpy()
+        np.testing.assert_array_equal(cw[:, pos], info)
+        assert np.all(oracle_mod.syndrome_weight(code, cw) == 0), F
+
+
+def test_dense_encoder_equals_the_ira_encoder(ldpc):
+    """On an IRA code the dense encoder's parity positions are the staircase
+    columns, so its words are the IRA encoder's, bit for bit."""
+    for code in (I.small_code_n1008(), I.mixed_codes()[3]):
+        h = ldpc.code_from_inputs(code)
+        assert ldpc.ldpc_code_build_encoder(h) == code.k
+        info = torch.from_numpy(I.random_info(45, code.k, seed=9)).cuda()
+        np.testing.assert_array_equal(ldpc.ldpc_encode(h, info).cpu().numpy(),
+                                      ldpc.ldpc_encode_ira(h, info).cpu().numpy(), err_msg=code.name)
+
+
+def test_random_codewords_of_a_lifted_code(ldpc, oracle_mod):
+    """Random codewords of a lifted code (dense encoder) decode as well as the
+    all-zero word, and at high SNR nothing is miscounted."""
+    code, ent = I.qc_stand_in_code(2048)
+    h = ldpc.ldpc_code_create_qc(4, 8, 256, ent)
+    z = ber.simulate(h, code, 2.2, 3000, batch=1000, seed=5)
+    r = ber.simulate(h, code, 2.2, 3000, batch=1000, seed=5, codewords="random")
+    lo_z, hi_z = ber.wilson(z.frame_errors, 3000)
+    lo_r, hi_r = ber.wilson(r.frame_errors, 3000)
+    assert lo_z <= hi_r and lo_r <= hi_z, (z, r)
+    hi = ber.simulate(h, code, 6.0, 1000, batch=1000, seed=6, codewords="random")
+    assert hi.frame_errors == 0 and hi.bit_errors == 0 and hi.unsatisfied == 0
+    k = ldpc.ldpc_code_build_encoder(h)
+    cw = ldpc.ldpc_encode(h, ldpc.ldpc_gen_bits(6, 0, 40, k)).cpu().numpy()
+    assert np.all(oracle_mod.syndrome_weight(code, cw) == 0) and cw.any()
