@@ -11,6 +11,13 @@ runs split across batches or ranks see the same channel.
         --frames 1000000 --batch 1024 --msg f32 f16 bf16 i8
     python -m paper_1609_01567_gb300.ber --code n16200_r1/3 --ebn0 1.0 \
         --rule min_sum_adaptive --degree-alpha 1 1 1 0.94 0.88
+    python -m paper_1609_01567_gb300.ber --frames 10000000 --checkpoint run.json
+
+With --checkpoint, each point runs in chunks of --chunk-frames and its
+counts and next frame index are saved after every chunk; a run started
+again with the same file continues every point where it stopped. Frames are
+numbered globally, so a resumed run decodes exactly the frames (and noise) an
+uninterrupted one would, and gives the same counts.
 """
 from __future__ import annotations
 
@@ -18,6 +25,8 @@ import argparse
 import json
 import math
 import time
+
+import os
 
 from . import inputs
 from .shard import Counts
@@ -98,6 +107,39 @@ CODES = {"n1008": inputs.small_code_n1008, "n64800": inputs.large_code_n64800,
          **{name: (lambda i=i: inputs.mixed_code(i)) for i, (_, _, name) in enumerate(inputs.MIXED_SPECS)}}
 
 
+def load_checkpoint(path):
+    if path and os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def save_checkpoint(path, state):
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(state, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)  # a run killed mid-write keeps the previous file
+
+
+def simulate_resumable(handle, code, ebn0_db, n_frames, key, state, path, chunk_frames, **kw) -> Counts:
+    """simulate() over frames [0, n_frames) in chunks, continuing from the
+    counts and frame index stored under ``key`` in ``state`` and saving them
+    to ``path`` after every chunk (no path: plain simulate)."""
+    if not path:
+        return simulate(handle, code, ebn0_db, n_frames, **kw)
+    entry = state.get(key, {"next_frame": 0, "counts": Counts().as_list()})
+    c = Counts.from_list(entry["counts"])
+    done = int(entry["next_frame"])
+    while done < n_frames:
+        b = min(chunk_frames, n_frames - done)
+        part = simulate(handle, code, ebn0_db, b, frame_offset=done, **kw)
+        c = Counts.from_list([x + y for x, y in zip(c.as_list(), part.as_list())])
+        done += b
+        state[key] = {"next_frame": done, "counts": c.as_list()}
+        save_checkpoint(path, state)
+    return c
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description="GPU BER/FER simulation")
     p.add_argument("--code", choices=sorted(CODES), default="n64800")
@@ -112,6 +154,8 @@ def main(argv=None):
     p.add_argument("--beta", type=float, default=0.0, help="min-sum offset")
     p.add_argument("--degree-alpha", type=float, nargs="+", help="min_sum_adaptive: scale by check degree 0, 1, ...")
     p.add_argument("--degree-beta", type=float, nargs="+", help="min_sum_adaptive: offset by check degree 0, 1, ...")
+    p.add_argument("--checkpoint", help="JSON file of per-point counts; an interrupted run resumes from it")
+    p.add_argument("--chunk-frames", type=int, default=100000, help="frames between two checkpoint saves")
     args = p.parse_args(argv)
 
     from . import ldpc
@@ -127,11 +171,15 @@ def main(argv=None):
             raise SystemExit("min_sum_adaptive needs --degree-alpha")
         ldpc.ldpc_code_set_rule_table(h, args.degree_alpha, args.degree_beta)
         rule_desc.update(degree_alpha=args.degree_alpha, degree_beta=args.degree_beta)
+    state = load_checkpoint(args.checkpoint)
     for eb in args.ebn0:
         for msg in args.msg:
             t0 = time.perf_counter()
-            c = simulate(h, code, eb, args.frames, batch=args.batch, max_iter=args.max_iter, msg_dtype=msg,
-                         seed=args.seed, **rule_kw)
+            key = json.dumps({"code": args.code, "ebn0_db": eb, "msg": msg, "max_iter": args.max_iter,
+                              "seed": args.seed, "batch": args.batch, **rule_desc}, sort_keys=True)
+            c = simulate_resumable(h, code, eb, args.frames, key, state, args.checkpoint, args.chunk_frames,
+                                   batch=args.batch, max_iter=args.max_iter, msg_dtype=msg, seed=args.seed,
+                                   **rule_kw)
             line = {"code": args.code, "ebn0_db": eb, "msg_dtype": msg, "max_iter": args.max_iter, **rule_desc,
                     "seconds": time.perf_counter() - t0, **summary(c, code.n)}
             print(json.dumps(line), flush=True)

@@ -610,6 +610,7 @@ template <typename M>
 static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32_t F, int32_t max_iter,
                              const ldpc_decode_opts_t &o, float l_max, uint8_t *bits, int32_t *iters, uint8_t *ok,
                              float *post, float *r_out, cudaStream_t s) {
+    NvtxRange nvtx_decode("ldpc decode");
     int32_t V, Fp;
     frames_layout(F, o.frames_per_lane, &V, &Fp);
     // the status word follows the frame bits
@@ -728,6 +729,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
             }
             Launcher Lh{c, hs[h], per_kernel};
             for (int32_t t = t0; t < t1; ++t) {
+                NvtxRange nvtx_pass(ti == 0 ? "ldpc pass (first half)" : "ldpc pass (second half)");
                 at.pass = an.pass = t;
                 at.syndrome = an.syndrome = (t > 0 && at.early_exit) ? 1 : 0;
                 at.dec = an.dec = t == max_iter ? w.dec : nullptr;
@@ -781,6 +783,7 @@ static cudaError_t run_chunk(ldpc_code *c, Workspace &w, const float *llr, int32
             }
         }
         if (sg + 2 < bounds.size()) {
+            NvtxRange nvtx_compact("ldpc compaction");
             e = L(LDPC_K_OTHER, 3, [&] {
                 cudaError_t ee = launch_pdl(k_compact_plan, dim3(1), dim3(kPlanThreads), 0, s, w.done, Fp, group,
                                             w.moves, 0, narrow ? kNarrowFrames : 0, static_cast<int32_t *>(nullptr));

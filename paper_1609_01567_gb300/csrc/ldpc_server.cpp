@@ -235,6 +235,7 @@ struct Admission {
 // groups, results of the stopped frames, packing, the status copy and the
 // callback.
 cudaError_t enqueue_chunk(ldpc_server *s, int si, const Admission &adm, int32_t range) {
+    NvtxRange nvtx_chunk("ldpc server chunk");
     Slot &sl = s->slots[si];
     ldpc_code *c = s->codes[sl.code];
     const cudaStream_t st = sl.stream;
