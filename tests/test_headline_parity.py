@@ -149,3 +149,22 @@ def test_early_exit_narrow_tail_is_bit_exact(ldpc, oracle_mod, code, msg):
         for k in ("bits", "iters", "ok", "post"):
             np.testing.assert_array_equal(other[k], got[k], err_msg=f"{name} {k}")
     print(f"n64800 1.6 dB {msg}: {late} frames beyond 21 iterations, iterations up to {int(got['iters'].max())}")
+
+
+def test_uneven_stream_split_is_bit_exact(ldpc, oracle_mod, code):
+    """Padded frame counts that are an odd number of frame groups split
+    unevenly over the two pass streams: 300 frames (three 128-frame groups,
+    256 + 128 by default) and 165 frames at two per lane (three 64-frame
+    groups, 128 + 64 with streams=2). The early-exit decode, whose
+    compaction runs across the split, and a fixed-iteration decode each equal
+    the one-stream decode bit for bit."""
+    _, llr = philox_llr(oracle_mod, code, 300, 1.4, EARLY_NOISE_SEED)
+    h = ldpc.code_from_inputs(code)
+    for F, kw in ((300, {}), (165, {"frames_per_lane": 2, "streams": 2})):
+        dev = torch.from_numpy(llr[:F]).cuda()
+        for max_iter, early in ((30, True), (5, False)):
+            two = to_host(ldpc.ldpc_decode(h, dev, max_iter, early_exit=early, want_post=True, **kw))
+            one = to_host(ldpc.ldpc_decode(h, dev, max_iter, early_exit=early, want_post=True, streams=1,
+                                           frames_per_lane=kw.get("frames_per_lane", 0)))
+            for k in ("bits", "iters", "ok", "post"):
+                np.testing.assert_array_equal(two[k], one[k], err_msg=f"{F} frames, max_iter {max_iter} {k}")
