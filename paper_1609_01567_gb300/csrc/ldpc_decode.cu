@@ -1047,17 +1047,60 @@ extern "C" int ldpc_decode_host(ldpc_code_t *c, const float *llr_host, int32_t F
         w.host_cap = F;
     }
     if ((e = cudaStreamWaitEvent(s, w.last_use, 0)) != cudaSuccess) return cuda_error(e, "ldpc_decode_host: wait");
-    size_t nf = (size_t)F * c->n;
-    if (nf && (e = cudaMemcpyAsync(w.h_llr, llr_host, sizeof(float) * nf, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return cuda_error(e, "ldpc_decode_host: copy in");
-    st = decode_locked(c, w.h_llr, F, max_iter, o, l_max, w.h_bits, w.h_iters, w.h_ok, post_host ? w.h_post : nullptr, s);
-    if (st != LDPC_OK) return st;
-    if ((nf && (e = cudaMemcpyAsync(bits_host, w.h_bits, nf, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
-        (e = cudaMemcpyAsync(iters_host, w.h_iters, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(ok_host, w.h_ok, F, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (post_host && nf &&
-         (e = cudaMemcpyAsync(post_host, w.h_post, sizeof(float) * nf, cudaMemcpyDeviceToHost, s)) != cudaSuccess))
-        return cuda_error(e, "ldpc_decode_host: copy out");
+    // A large batch runs as two parts, its copies on a copy stream: the
+    // second part's LLRs arrive while the first decodes, and the first part's
+    // results leave while the second decodes (a frame's result does not
+    // depend on the frames decoded with it).
+    const int32_t part = (F / 2 + 127) / 128 * 128;
+    const bool pipe = F >= 256 && part < F && (int64_t)c->n * F >= ((int64_t)1 << 22);
+    if (pipe && !w.copy_stream) {
+        e = cudaStreamCreateWithFlags(&w.copy_stream, cudaStreamNonBlocking);
+        for (auto &ev : w.copy_ev)
+            if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_error(e, "ldpc_decode_host: copy stream");
+    }
+    const int32_t np = pipe ? 2 : 1;
+    const int32_t f0s[2] = {0, pipe ? part : F}, fns[2] = {pipe ? part : F, pipe ? F - part : 0};
+    const cudaStream_t cs = pipe ? w.copy_stream : s;
+    if (pipe && ((e = cudaEventRecord(w.copy_ev[0], s)) != cudaSuccess ||
+                 (e = cudaStreamWaitEvent(cs, w.copy_ev[0], 0)) != cudaSuccess))
+        return cuda_error(e, "ldpc_decode_host: fork");
+    for (int32_t p = 0; p < np; ++p) {  // copies in
+        const size_t off = (size_t)f0s[p] * c->n, cnt = (size_t)fns[p] * c->n;
+        if (cnt && (e = cudaMemcpyAsync(w.h_llr + off, llr_host + off, sizeof(float) * cnt, cudaMemcpyHostToDevice,
+                                        cs)) != cudaSuccess)
+            return cuda_error(e, "ldpc_decode_host: copy in");
+        if (pipe && (e = cudaEventRecord(w.copy_ev[1 + p], cs)) != cudaSuccess)
+            return cuda_error(e, "ldpc_decode_host: record");
+    }
+    for (int32_t p = 0; p < np; ++p) {  // decodes
+        const size_t off = (size_t)f0s[p] * c->n;
+        if (pipe && (e = cudaStreamWaitEvent(s, w.copy_ev[1 + p], 0)) != cudaSuccess)
+            return cuda_error(e, "ldpc_decode_host: wait");
+        st = decode_locked(c, w.h_llr + off, fns[p], max_iter, o, l_max, w.h_bits + off, w.h_iters + f0s[p],
+                           w.h_ok + f0s[p], post_host ? w.h_post + off : nullptr, s);
+        if (st != LDPC_OK) return st;
+        if (pipe && (e = cudaEventRecord(w.copy_ev[3 + p], s)) != cudaSuccess)
+            return cuda_error(e, "ldpc_decode_host: record");
+    }
+    for (int32_t p = 0; p < np; ++p) {  // copies out
+        const size_t off = (size_t)f0s[p] * c->n, cnt = (size_t)fns[p] * c->n;
+        const int32_t f0 = f0s[p], fn = fns[p];
+        if (pipe && (e = cudaStreamWaitEvent(cs, w.copy_ev[3 + p], 0)) != cudaSuccess)
+            return cuda_error(e, "ldpc_decode_host: wait");
+        if ((cnt && (e = cudaMemcpyAsync(bits_host + off, w.h_bits + off, cnt, cudaMemcpyDeviceToHost, cs)) !=
+                        cudaSuccess) ||
+            (e = cudaMemcpyAsync(iters_host + f0, w.h_iters + f0, sizeof(int32_t) * fn, cudaMemcpyDeviceToHost, cs)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(ok_host + f0, w.h_ok + f0, fn, cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
+            (post_host && cnt &&
+             (e = cudaMemcpyAsync(post_host + off, w.h_post + off, sizeof(float) * cnt, cudaMemcpyDeviceToHost, cs)) !=
+                 cudaSuccess))
+            return cuda_error(e, "ldpc_decode_host: copy out");
+    }
+    if (pipe && ((e = cudaEventRecord(w.copy_ev[5], cs)) != cudaSuccess ||
+                 (e = cudaStreamWaitEvent(s, w.copy_ev[5], 0)) != cudaSuccess))
+        return cuda_error(e, "ldpc_decode_host: join");
     if ((e = cudaEventRecord(w.last_use, s)) != cudaSuccess) return cuda_error(e, "ldpc_decode_host: record");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_error(e, "ldpc_decode_host: synchronize");
     return report_gave_up(iters_host, F, "ldpc_decode_host");
@@ -1150,6 +1193,9 @@ void free_workspace(Workspace &w) {
     cudaFree(w.h_ok);
     cudaFree(w.h_post);
     if (w.last_use) cudaEventDestroy(w.last_use);
+    if (w.copy_stream) cudaStreamDestroy(w.copy_stream);
+    for (auto ev : w.copy_ev)
+        if (ev) cudaEventDestroy(ev);
     for (int h = 0; h < 2; ++h) {
         if (w.half_stream[h]) cudaStreamDestroy(w.half_stream[h]);
         if (w.join[h]) cudaEventDestroy(w.join[h]);

@@ -39,6 +39,10 @@ struct Workspace {
     uint8_t *h_ok = nullptr;
     float *h_post = nullptr;
     cudaEvent_t last_use = nullptr;  // end of the last decode that used the buffers
+    // ldpc_decode_host's copy stream and its events (start, two copies in, two
+    // decodes, copies out done), for batches decoded as two halves
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // two library streams that run the two halves of a batch half a pass apart
     cudaStream_t half_stream[2] = {nullptr, nullptr};
     cudaEvent_t fork = nullptr, phase = nullptr, join[2] = {nullptr, nullptr};

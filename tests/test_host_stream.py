@@ -72,3 +72,22 @@ def test_stream_at_the_benchmark_configuration(ldpc, msg):
     one = ldpc.ldpc_decode_host(h, llrs[1], 10, early_exit=False, msg_dtype=msg)
     for k in ("bits", "iters", "ok"):
         np.testing.assert_array_equal(one[k].numpy(), refs[1][k], err_msg=f"one call {k}")
+
+
+def test_one_call_in_two_parts(ldpc):
+    """A large one-call host decode runs as two parts whose copies overlap
+    the other part's decode (here 300 frames: 256 + 44, and 256: 128 + 128),
+    with early exit and posteriors; repeated calls replay captured graphs.
+    Every call equals the device decode of the whole batch bit for bit."""
+    code = I.large_code_n64800()
+    h = ldpc.code_from_inputs(code)
+    s2 = I.sigma2_from_ebn0(1.4, code.rate)
+    for F in (300, 256):
+        llr = ldpc.ldpc_gen_awgn(90 + F, 0, F, code.n, s2).cpu().pin_memory()
+        ref = ldpc.ldpc_decode(h, llr.cuda(), 30, want_post=True)
+        torch.cuda.synchronize()
+        ref = {k: v.cpu().numpy() for k, v in ref.items()}
+        for rep in range(3):
+            got = ldpc.ldpc_decode_host(h, llr, 30, want_post=True)
+            for k in ("bits", "iters", "ok", "post"):
+                np.testing.assert_array_equal(np.asarray(got[k]), ref[k], err_msg=f"{F} frames, call {rep}, {k}")
