@@ -260,7 +260,10 @@ int ldpc_decode(ldpc_code_t *code, const float *llr, int32_t n_frames, int32_t m
  * ldpc_decode on HOST buffers (same shapes, host memory; pinned memory makes
  * the copies asynchronous). Copies llr to the device, decodes, copies bits,
  * iters, syndrome_ok (and post_llr when non-NULL) back, and synchronizes
- * `stream` before returning. opts->r_out must be NULL. Returns LDPC_ETIMEOUT
+ * `stream` before returning. A batch of at least 256 frames with
+ * n x n_frames >= 2^22 runs as two parts whose copies (on a library copy
+ * stream) overlap the other part's decode; results are those of one decode.
+ * opts->r_out must be NULL. Returns LDPC_ETIMEOUT
  * (results copied back, iters = -1) when a bounded device wait of the decode
  * gave up.
  */
